@@ -1,0 +1,275 @@
+"""Seeded synthetic inputs shaped after the paper's test problems (Section 4).
+
+This module holds only input generation: a SplitMix64 generator and the initial
+cell averages and interface point values of each workload.  It contains none of the
+scheme's arithmetic, so both the CUDA path and the oracle may use it.
+
+Workloads (all FP64 host arrays in the library's SoA layout):
+
+* ``density_wave_1d``  -- Section 4.1, rho = 1 + 0.2 sin(pi (x + phi)), U = 1, p = 1 on a
+  periodic [0, 2] line, laid out as an nx-by-1 periodic 2D grid (dy = dx).
+* ``smooth_wave_2d``   -- rho = 1 + 0.2 sin(pi (x + y) + phi), U = V = 1, p = 1 on the
+  periodic square [0, 2]^2 (the 2D analogue of Section 4.1).
+* ``riemann_2d``       -- four constant quadrants on [0, 1]^2 as in the 2D Riemann problems
+  of Section 4, with seeded rho ~ U[0.1, 1.5], p ~ U[0.03, 1.5], u, v ~ U[-1, 1].
+* ``cavity_2d``        -- lid-driven square cavity at rest (rho = 1, p = 1/gamma), lid speed
+  0.15 (lid Mach number 0.15), isothermal no-slip walls.
+* ``batch_grids``      -- 512 independent grids with seeded sizes, kinds, gamma and mu.
+
+Cell averages are exact averages of the initial data; interface values are the exact
+point values at the Gauss points (x-faces: y_j -/+ sqrt(3)/6 dy; y-faces: x_i -/+ sqrt(3)/6 dx).
+A point lying exactly on an initial discontinuity takes the mean of the two sides.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+MASK64 = (1 << 64) - 1
+GAUSS = math.sqrt(3.0) / 6.0
+
+
+class SplitMix64:
+    """SplitMix64 (Steele, Lea & Flood 2014); doubles are (x >> 11) * 2^-53."""
+
+    def __init__(self, seed: int):
+        self.state = seed & MASK64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        return z ^ (z >> 31)
+
+    def uniform(self, lo: float = 0.0, hi: float = 1.0) -> float:
+        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / 9007199254740992.0))
+
+
+BC_PERIODIC, BC_OUTFLOW, BC_SLIPWALL, BC_NOSLIP_ISOTHERMAL = 0, 1, 2, 3
+
+
+@dataclass
+class Problem:
+    """A 2D grid problem: geometry, gas, boundary conditions and the initial state."""
+    name: str
+    nx: int
+    ny: int
+    Lx: float
+    Ly: float
+    gamma: float
+    mu: float
+    Pr: float
+    bc: list  # 4 x (kind, u_wall, v_wall, T_wall): x-low, x-high, y-low, y-high
+    U: np.ndarray   # [4][ny][nx]
+    Wx: np.ndarray  # [4][2][ny][nx+1]
+    Wy: np.ndarray  # [4][2][ny+1][nx]
+    CFL: float = 0.5
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny
+
+
+def _cons(rho, u, v, p, gamma):
+    rho = np.asarray(rho, dtype=np.float64)
+    return np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
+
+
+def _gauss_points(nx, ny, Lx, Ly):
+    dx, dy = Lx / nx, Ly / ny
+    xc = (np.arange(nx) + 0.5) * dx
+    yc = (np.arange(ny) + 0.5) * dy
+    xf = np.arange(nx + 1) * dx
+    yf = np.arange(ny + 1) * dy
+    # x-faces: (x = xf[i], y = yc[j] -/+ g dy)
+    wx_pts = [(xf[None, :] + 0 * yc[:, None], yc[:, None] + s * GAUSS * dy + 0 * xf[None, :]) for s in (-1, 1)]
+    wy_pts = [(xc[None, :] + s * GAUSS * dx + 0 * yf[:, None], yf[:, None] + 0 * xc[None, :]) for s in (-1, 1)]
+    return xc, yc, wx_pts, wy_pts
+
+
+def _point_state(fn, pts):
+    return np.stack([fn(x, y) for (x, y) in pts], axis=1)  # [4][2][...]
+
+
+def sinc(z):
+    z = np.asarray(z, dtype=np.float64)
+    return np.where(z == 0.0, 1.0, np.sin(z) / np.where(z == 0.0, 1.0, z))
+
+
+def smooth_wave_2d(n: int, seed: int = 2, gamma: float = 1.4, L: float = 2.0, ny: int | None = None) -> Problem:
+    """Periodic smooth wave rho = 1 + 0.2 sin(pi (x + y) + phi), U = V = 1, p = 1."""
+    ny = n if ny is None else ny
+    rng = SplitMix64(seed)
+    phi = rng.uniform()
+    nx = n
+    Lx = Ly = L
+    dx, dy = Lx / nx, Ly / ny
+    xc, yc, wxp, wyp = _gauss_points(nx, ny, Lx, Ly)
+    X, Y = np.meshgrid(xc, yc)
+    rho_bar = 1.0 + 0.2 * np.sin(np.pi * (X + Y) + phi) * sinc(np.pi * dx / 2) * sinc(np.pi * dy / 2)
+    U = np.stack([rho_bar, rho_bar, rho_bar, 1.0 / (gamma - 1.0) + rho_bar])
+
+    def pt(x, y):
+        r = 1.0 + 0.2 * np.sin(np.pi * (x + y) + phi)
+        return _cons(r, 1.0, 1.0, 1.0, gamma)
+
+    Wx = _point_state(pt, wxp)
+    Wy = _point_state(pt, wyp)
+    bc = [(BC_PERIODIC, 0.0, 0.0, 1.0)] * 4
+    return Problem(f"smooth_wave_{nx}x{ny}", nx, ny, Lx, Ly, gamma, 0.0, 1.0, bc,
+                   np.ascontiguousarray(U), np.ascontiguousarray(Wx), np.ascontiguousarray(Wy),
+                   meta={"phi": phi, "seed": seed})
+
+
+def density_wave_1d(nx: int, seed: int = 1, gamma: float = 1.4, phi: float | None = None) -> Problem:
+    """Section 4.1 density wave on [0, 2] as an nx-by-1 periodic grid with dy = dx."""
+    if phi is None:
+        phi = SplitMix64(seed).uniform()
+    Lx = 2.0
+    dx = Lx / nx
+    Ly = dx
+    xc, yc, wxp, wyp = _gauss_points(nx, 1, Lx, Ly)
+    rho_bar = 1.0 + 0.2 * np.sin(np.pi * (xc + phi)) * sinc(np.pi * dx / 2)
+    U = np.stack([rho_bar, rho_bar, 0 * rho_bar, 1.0 / (gamma - 1.0) + 0.5 * rho_bar])[:, None, :]
+
+    def pt(x, y):
+        r = 1.0 + 0.2 * np.sin(np.pi * (x + phi))
+        return _cons(r, 1.0, 0.0, 1.0, gamma)
+
+    Wx = _point_state(pt, wxp)
+    Wy = _point_state(pt, wyp)
+    bc = [(BC_PERIODIC, 0.0, 0.0, 1.0)] * 4
+    return Problem(f"density_wave_{nx}", nx, 1, Lx, Ly, gamma, 0.0, 1.0, bc,
+                   np.ascontiguousarray(U), np.ascontiguousarray(Wx), np.ascontiguousarray(Wy),
+                   meta={"phi": phi, "seed": seed})
+
+
+def density_wave_exact_avg(nx: int, t: float, phi: float, gamma: float = 1.4):
+    """Exact cell averages of rho at time t for the translated density wave."""
+    dx = 2.0 / nx
+    xc = (np.arange(nx) + 0.5) * dx
+    return 1.0 + 0.2 * np.sin(np.pi * (xc - t + phi)) * sinc(np.pi * dx / 2)
+
+
+def density_wave_1d_layout(p: Problem):
+    """The same data in the 3-variable 1D layout U[3][nx], W[3][nx+1] (face-centre values)."""
+    U1 = np.ascontiguousarray(np.stack([p.U[0, 0], p.U[1, 0], p.U[3, 0]]))
+    # 1D face values are the point values at the face; with no y dependence both Gauss
+    # points carry the same value
+    W1 = np.ascontiguousarray(np.stack([p.Wx[0, 0, 0], p.Wx[1, 0, 0], p.Wx[3, 0, 0]]))
+    return U1, W1
+
+
+def riemann_draw(rng: SplitMix64):
+    """Quadrant states in the order NE, NW, SW, SE; per quadrant rho, p, u, v."""
+    q = []
+    for _ in range(4):
+        rho = rng.uniform(0.1, 1.5)
+        p = rng.uniform(0.03, 1.5)
+        u = rng.uniform(-1.0, 1.0)
+        v = rng.uniform(-1.0, 1.0)
+        q.append((rho, u, v, p))
+    return q
+
+
+def riemann_2d(nx: int, ny: int | None = None, seed: int = 3, gamma: float = 1.4, mu: float = 1e-4,
+               Pr: float = 0.72, quadrants=None) -> Problem:
+    """Four-quadrant Riemann data on [0, 1]^2 with outflow boundaries."""
+    ny = nx if ny is None else ny
+    if quadrants is None:
+        quadrants = riemann_draw(SplitMix64(seed))
+    Lx = Ly = 1.0
+    dx, dy = Lx / nx, Ly / ny
+    qs = [_cons(r, u, v, p, gamma) for (r, u, v, p) in quadrants]  # NE, NW, SW, SE
+
+    def state_at(x, y):
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64)
+        out = np.zeros((4,) + np.broadcast(x, y).shape)
+        east = np.where(x > 0.5, 1.0, np.where(x < 0.5, 0.0, 0.5))
+        north = np.where(y > 0.5, 1.0, np.where(y < 0.5, 0.0, 0.5))
+        w = [east * north, (1 - east) * north, (1 - east) * (1 - north), east * (1 - north)]
+        for k in range(4):
+            out += w[k][None] * qs[k].reshape(4, *([1] * x.ndim))
+        return out
+
+    # exact cell averages: area fractions of each quadrant
+    xl = np.arange(nx) * dx
+    yl = np.arange(ny) * dy
+    fe = np.clip((xl + dx - 0.5) / dx, 0.0, 1.0)  # fraction of the cell east of x = 0.5
+    fn = np.clip((yl + dy - 0.5) / dy, 0.0, 1.0)
+    FE, FN = np.meshgrid(fe, fn)
+    U = (qs[0].reshape(4, 1, 1) * FE * FN + qs[1].reshape(4, 1, 1) * (1 - FE) * FN +
+         qs[2].reshape(4, 1, 1) * (1 - FE) * (1 - FN) + qs[3].reshape(4, 1, 1) * FE * (1 - FN))
+    _, _, wxp, wyp = _gauss_points(nx, ny, Lx, Ly)
+    Wx = _point_state(state_at, wxp)
+    Wy = _point_state(state_at, wyp)
+    bc = [(BC_OUTFLOW, 0.0, 0.0, 1.0)] * 4
+    return Problem(f"riemann_{nx}x{ny}", nx, ny, Lx, Ly, gamma, mu, Pr, bc,
+                   np.ascontiguousarray(U), np.ascontiguousarray(Wx), np.ascontiguousarray(Wy),
+                   meta={"quadrants": quadrants, "seed": seed})
+
+
+def cavity_2d(n: int, gamma: float = 1.4, Re: float = 1000.0, lid: float = 0.15, Pr: float = 0.72) -> Problem:
+    """Lid-driven square cavity, rho = 1, p = 1/gamma (sound speed 1), at rest."""
+    nx = ny = n
+    Lx = Ly = 1.0
+    mu = 1.0 * lid * Lx / Re
+    Tw = 1.0 / gamma
+    U = np.ascontiguousarray(np.broadcast_to(_cons(1.0, 0.0, 0.0, 1.0 / gamma, gamma).reshape(4, 1, 1),
+                                             (4, ny, nx)).copy())
+    Wx = np.ascontiguousarray(np.broadcast_to(U[:, None, :, :1], (4, 2, ny, nx + 1)).copy())
+    Wy = np.ascontiguousarray(np.broadcast_to(U[:, None, :1, :], (4, 2, ny + 1, nx)).copy())
+    wall = (BC_NOSLIP_ISOTHERMAL, 0.0, 0.0, Tw)
+    bc = [wall, wall, wall, (BC_NOSLIP_ISOTHERMAL, lid, 0.0, Tw)]
+    return Problem(f"cavity_{n}", nx, ny, Lx, Ly, gamma, mu, Pr, bc, U, Wx, Wy,
+                   meta={"Re": Re, "lid": lid})
+
+
+BATCH_SIZES = [32 * k for k in range(1, 13)]
+
+
+def batch_specs(n_grids: int = 512, seed: int = 5):
+    """Per grid: (nx, ny, kind, gamma, mu, draws) with kind 'wave' for even g, 'riemann' for odd."""
+    rng = SplitMix64(seed)
+    specs = []
+    for g in range(n_grids):
+        nx = BATCH_SIZES[min(int(rng.uniform() * 12), 11)]
+        ny = BATCH_SIZES[min(int(rng.uniform() * 12), 11)]
+        gamma = 1.4 if rng.uniform() < 0.5 else 5.0 / 3.0
+        mu = 10.0 ** (-5.0 + 2.0 * rng.uniform())
+        if g % 2 == 0:
+            specs.append((nx, ny, "wave", gamma, mu, rng.uniform()))
+        else:
+            specs.append((nx, ny, "riemann", gamma, mu, riemann_draw(rng)))
+    return specs
+
+
+def batch_problem(spec) -> Problem:
+    nx, ny, kind, gamma, mu, draw = spec
+    if kind == "wave":
+        p = smooth_wave_2d(nx, ny=ny, gamma=gamma)
+        # replace the phase by the batch draw
+        return _rephase(p, draw, gamma, mu)
+    return riemann_2d(nx, ny, gamma=gamma, mu=mu, Pr=0.72, quadrants=draw)
+
+
+def _rephase(p: Problem, phi: float, gamma: float, mu: float) -> Problem:
+    nx, ny, Lx, Ly = p.nx, p.ny, p.Lx, p.Ly
+    dx, dy = Lx / nx, Ly / ny
+    xc, yc, wxp, wyp = _gauss_points(nx, ny, Lx, Ly)
+    X, Y = np.meshgrid(xc, yc)
+    rho_bar = 1.0 + 0.2 * np.sin(np.pi * (X + Y) + phi) * sinc(np.pi * dx / 2) * sinc(np.pi * dy / 2)
+    U = np.stack([rho_bar, rho_bar, rho_bar, 1.0 / (gamma - 1.0) + rho_bar])
+
+    def pt(x, y):
+        r = 1.0 + 0.2 * np.sin(np.pi * (x + y) + phi)
+        return _cons(r, 1.0, 1.0, 1.0, gamma)
+
+    return Problem(f"wave_{nx}x{ny}", nx, ny, Lx, Ly, gamma, mu, 0.72, p.bc, np.ascontiguousarray(U),
+                   np.ascontiguousarray(_point_state(pt, wxp)), np.ascontiguousarray(_point_state(pt, wyp)),
+                   meta={"phi": phi})

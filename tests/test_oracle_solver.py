@@ -1,0 +1,227 @@
+"""Grid-level pins of the oracle: what the paper and the mathematics fix for whole steps.
+
+* free stream is preserved exactly (Eq. finite with identical face fluxes);
+* mass, momentum and energy are conserved to roundoff on periodic grids and in a box of
+  slip walls;
+* the scheme commutes with the transposition x <-> y and the reflection x -> -x;
+* data that do not depend on y reproduce the independent 1D scheme (one step, exactly);
+* the density wave of Section 4.1 converges at third order (Table 1), in 1D and 2D.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1412_4489_gb300 import workloads as wl
+
+G = math.sqrt(3.0) / 6.0
+PER = [oracle.BC_PERIODIC] * 4
+
+
+def _cons(rho, u, v, p, gamma):
+    return np.array([rho, rho * u, rho * v, p / (gamma - 1) + 0.5 * rho * (u * u + v * v)])
+
+
+def _state(p):
+    return oracle.State2D(p.nx, p.ny, p.Lx, p.Ly, p.U, p.Wx, p.Wy)
+
+
+def _perturbed(nx, ny, seed, gamma=1.4, amp=0.05):
+    """A smooth periodic state with random small perturbations on cells and faces."""
+    p = wl.smooth_wave_2d(nx, ny=ny, seed=seed, gamma=gamma)
+    rng = np.random.default_rng(seed)
+    st = _state(p)
+    st.U *= 1 + amp * rng.uniform(-1, 1, size=st.U.shape) * np.array([1, 1, 1, 0.2])[:, None, None]
+    st.Wx *= 1 + amp * rng.uniform(-1, 1, size=st.Wx.shape) * np.array([1, 1, 1, 0.2])[:, None, None, None]
+    st.Wy *= 1 + amp * rng.uniform(-1, 1, size=st.Wy.shape) * np.array([1, 1, 1, 0.2])[:, None, None, None]
+    # make periodic duplicate faces agree
+    st.Wx[..., -1] = st.Wx[..., 0]
+    st.Wy[:, :, -1, :] = st.Wy[:, :, 0, :]
+    return st
+
+
+@pytest.mark.parametrize("mu", [0.0, 1e-3])
+def test_free_stream(mu):
+    gamma = 1.4
+    w = _cons(0.8, 0.4, -0.7, 1.3, gamma)
+    nx, ny = 7, 5
+    U = np.broadcast_to(w[:, None, None], (4, ny, nx)).copy()
+    Wx = np.broadcast_to(w[:, None, None, None], (4, 2, ny, nx + 1)).copy()
+    Wy = np.broadcast_to(w[:, None, None, None], (4, 2, ny + 1, nx)).copy()
+    st = oracle.State2D(nx, ny, 1.0, 0.8, U, Wx, Wy)
+    P = oracle.params(gamma=gamma, mu=mu, Pr=0.72)
+    oracle.step2d(P, st, oracle.bcs(PER), 0.5)
+    assert np.array_equal(st.U, U)  # identical face fluxes cancel exactly
+    for _ in range(20):
+        oracle.step2d(P, st, oracle.bcs(PER), 0.5)
+    np.testing.assert_allclose(st.U, U, rtol=1e-13)
+    np.testing.assert_allclose(st.Wx, Wx, rtol=1e-13)
+    np.testing.assert_allclose(st.Wy, Wy, rtol=1e-13)
+
+
+@pytest.mark.parametrize("mu,Pr", [(0.0, 1.0), (2e-3, 0.72)])
+def test_conservation_periodic(mu, Pr):
+    st = _perturbed(12, 9, seed=4)
+    P = oracle.params(gamma=1.4, mu=mu, Pr=Pr)
+    tot0 = st.U.sum(axis=(1, 2))
+    for _ in range(15):
+        rc, _ = oracle.step2d(P, st, oracle.bcs(PER), 0.5)
+        assert rc == 0
+        np.testing.assert_allclose(st.U.sum(axis=(1, 2)), tot0, rtol=1e-13, atol=1e-13 * np.abs(tot0).max())
+
+
+def test_conservation_riemann_periodic():
+    p = wl.riemann_2d(16, 12, seed=3, mu=1e-3)
+    st = _state(p)
+    P = oracle.params(gamma=1.4, mu=1e-3, Pr=0.72)
+    tot0 = st.U.sum(axis=(1, 2))
+    for _ in range(10):
+        rc, _ = oracle.step2d(P, st, oracle.bcs(PER), 0.5)
+        assert rc == 0
+    np.testing.assert_allclose(st.U.sum(axis=(1, 2)), tot0, rtol=1e-13, atol=1e-13 * np.abs(tot0).max())
+
+
+def test_slip_wall_box_conserves_mass_and_energy():
+    p = wl.riemann_2d(10, 8, seed=9, mu=0.0)
+    st = _state(p)
+    P = oracle.params(gamma=1.4)
+    bc = oracle.bcs([oracle.BC_SLIPWALL] * 4)
+    tot0 = st.U.sum(axis=(1, 2))
+    for _ in range(10):
+        assert oracle.step2d(P, st, bc, 0.4)[0] == 0
+    tot = st.U.sum(axis=(1, 2))
+    assert tot[0] == pytest.approx(tot0[0], rel=1e-13)
+    assert tot[3] == pytest.approx(tot0[3], rel=1e-13)
+
+
+def test_cavity_at_rest_stays_at_rest():
+    p = wl.cavity_2d(8, lid=0.0)
+    st = _state(p)
+    P = oracle.params(gamma=p.gamma, mu=p.mu, Pr=p.Pr)
+    bc = oracle.bcs([b[0] for b in p.bc], [b[1:] for b in p.bc])
+    for _ in range(5):
+        assert oracle.step2d(P, st, bc, 0.5)[0] == 0
+    np.testing.assert_allclose(st.U, p.U, rtol=1e-13, atol=1e-14)
+
+
+def _transpose(st):
+    U = st.U.transpose(0, 2, 1)[[0, 2, 1, 3]]
+    Wx = st.Wy.transpose(0, 1, 3, 2)[[0, 2, 1, 3]]
+    Wy = st.Wx.transpose(0, 1, 3, 2)[[0, 2, 1, 3]]
+    return oracle.State2D(st.ny, st.nx, st.Ly, st.Lx, U, Wx, Wy)
+
+
+@pytest.mark.parametrize("mu", [0.0, 1e-3])
+def test_transpose_symmetry(mu):
+    st = _perturbed(10, 7, seed=6)
+    st.Ly = 1.5
+    tr = _transpose(st)
+    P = oracle.params(gamma=1.4, mu=mu, Pr=0.72)
+    for _ in range(4):
+        oracle.step2d(P, st, oracle.bcs(PER), 0.5)
+        oracle.step2d(P, tr, oracle.bcs(PER), 0.5)
+    back = _transpose(tr)
+    np.testing.assert_allclose(back.U, st.U, rtol=1e-12)
+    np.testing.assert_allclose(back.Wx, st.Wx, rtol=1e-12)
+    np.testing.assert_allclose(back.Wy, st.Wy, rtol=1e-12)
+
+
+def _reflect_x(st):
+    sgn = np.array([1, -1, 1, 1])[:, None, None]
+    U = st.U[:, :, ::-1] * sgn
+    Wx = st.Wx[:, :, :, ::-1] * sgn[:, None]
+    Wy = st.Wy[:, ::-1, :, ::-1] * sgn[:, None]  # x-Gauss points swap under x -> -x
+    return oracle.State2D(st.nx, st.ny, st.Lx, st.Ly, U.copy(), Wx.copy(), Wy.copy())
+
+
+@pytest.mark.parametrize("kinds", [PER, [oracle.BC_OUTFLOW] * 4])
+def test_reflection_symmetry(kinds):
+    st = _perturbed(9, 8, seed=2)
+    rf = _reflect_x(st)
+    P = oracle.params(gamma=1.4, mu=1e-3, Pr=0.72)
+    for _ in range(4):
+        oracle.step2d(P, st, oracle.bcs(kinds), 0.5)
+        oracle.step2d(P, rf, oracle.bcs(kinds), 0.5)
+    back = _reflect_x(rf)
+    np.testing.assert_allclose(back.U, st.U, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(back.Wx, st.Wx, rtol=1e-12, atol=1e-13)
+
+
+def _minmod(a, b):
+    return np.where(a * b > 0, np.where(np.abs(a) < np.abs(b), a, b), 0.0)
+
+
+@pytest.mark.parametrize("mu", [0.0, 1e-3])
+def test_y_uniform_data_reproduce_the_1d_scheme(mu):
+    """One step of the 2D oracle on an nx-by-1 periodic grid with V = 0 equals one step of the
+    independent 1D oracle (K1 = K + 1 absorbs v into the internal degrees of freedom).
+
+    The y-face point values are set to those of the cell's limited one-sided polynomial
+    U_1 (x) at x = -/+ sqrt(3)/6 dx, so that the 2D reconstruction has a3 = a5 = a6 = 0."""
+    nx, gamma = 24, 1.4
+    p = wl.density_wave_1d(nx, phi=0.37)
+    U1, W1 = wl.density_wave_1d_layout(p)
+    dx = p.Lx / nx
+    Um, Up = np.roll(U1, 1, axis=1), np.roll(U1, -1, axis=1)
+    Wm, Wp = W1[:, :-1], W1[:, 1:]
+    a3 = _minmod(3 * (U1 + Um - 2 * Wm) / dx ** 2, 3 * (U1 + Up - 2 * Wp) / dx ** 2)
+    a2 = _minmod(-2 * (Wm - U1) / dx + a3 * dx / 6, 2 * (Wp - U1) / dx - a3 * dx / 6)
+    st = _state(p)
+    for g, s in ((0, -1), (1, 1)):
+        for j in range(2):
+            st.Wy[[0, 1, 3], g, j, :] = U1 + s * G * dx * a2
+            st.Wy[2, g, j, :] = 0.0
+    P = oracle.params(gamma=gamma, mu=mu, Pr=0.72 if mu else 1.0)
+    rc2, dt2 = oracle.step2d(P, st, oracle.bcs(PER), 0.5)
+    rc1, dt1 = oracle.step1d(P, nx, p.Lx, U1, W1, 0.5)
+    assert rc1 == rc2 == 0
+    assert dt2 == pytest.approx(dt1, rel=1e-15)
+    np.testing.assert_allclose(st.U[[0, 1, 3], 0], U1, rtol=1e-13)
+    np.testing.assert_allclose(st.U[2], 0.0, atol=1e-15)
+    for g in range(2):
+        np.testing.assert_allclose(st.Wx[[0, 1, 3], g, 0], W1, rtol=1e-13)
+
+
+def _wave_errors_1d(P, cells, cfl=0.2):
+    out = []
+    for nx in cells:
+        p = wl.density_wave_1d(nx, phi=0.0)
+        U1, W1 = wl.density_wave_1d_layout(p)
+        oracle.run1d(P, nx, 2.0, U1, W1, cfl, 2.0)
+        ex = wl.density_wave_exact_avg(nx, 2.0, 0.0)
+        out.append((np.mean(np.abs(U1[0] - ex)), math.sqrt(np.mean((U1[0] - ex) ** 2))))
+    return np.array(out)
+
+
+def test_density_wave_third_order_1d():
+    """Section 4.1 / Table 1 in the Euler limit of the collision time (epsilon = 0)."""
+    e = _wave_errors_1d(oracle.params(tau_eps=0.0), [25, 50, 100, 200])
+    orders = np.log2(e[:-1, 0] / e[1:, 0])
+    assert np.all(orders > 2.9), orders
+    table = np.loadtxt(__file__.replace("test_oracle_solver.py", "golden/table1_density_wave.txt"))
+    paper_orders = table[1:, 2]
+    assert np.all(paper_orders > 2.8)  # the order the paper reports, which ours matches
+    # our error constant: within 20x of Table 1 at 50..200 cells (the paper's weights are unstated)
+    assert np.all(e[1:, 0] < 20 * table[:3, 1])
+
+
+def test_paper_inviscid_tau_limits_smooth_order():
+    """With the inviscid tau = 0.05 dt of Section 4 the epsilon dt collision time adds an O(dt)
+    heat conduction: the smooth wave converges at first order only.  This is why the accuracy
+    workloads use epsilon = 0 (a reading recorded with the design)."""
+    e = _wave_errors_1d(oracle.params(tau_eps=0.05), [50, 100, 200])
+    orders = np.log2(e[:-1, 0] / e[1:, 0])
+    assert np.all(orders < 1.8), orders
+
+
+def test_smooth_wave_2d_converges():
+    P = oracle.params(gamma=1.4, tau_eps=0.0)
+    errs = []
+    for n in (16, 32, 64):
+        p = wl.smooth_wave_2d(n, seed=2)
+        st = _state(p)
+        oracle.run2d(P, st, oracle.bcs(PER), 0.5, t_end=1.0)  # one period along x + y
+        errs.append(np.mean(np.abs(st.U[0] - p.U[0])))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders[0] > 2.5 and orders[1] > 2.7 and orders[1] > orders[0], orders
