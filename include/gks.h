@@ -1,0 +1,178 @@
+/*
+ * gks.h -- C ABI of the GB300 (sm_103a) implementation of the hot path of the
+ * compact third-order gas-kinetic scheme of Pan & Xu ("A compact third-order
+ * gas-kinetic scheme for compressible Euler and Navier-Stokes equations",
+ * arXiv:1412.4489) on 2D structured grids.
+ *
+ * One call of gks_step is one time step of the scheme:
+ *   (a) compact reconstruction of every cell from its cell average, the four
+ *       neighbouring averages and the tracked point values at the Gauss points
+ *       of its four faces (Section 3.2: Eq. over-sys, Eq. limiter, Eq. average);
+ *   (b) the third-order gas evolution model at every face centre (Section 2.2:
+ *       Eq. compatibility2 for g0, the equilibrium polynomial of Section 3.3,
+ *       the coefficient systems after Eq. dis3, the collision time of Section 4);
+ *   (c) the analytically time-integrated flux (Eq. dis1 + Eq. dis2 integrated in
+ *       time and along the face), the face point values W(t^{n+1}) (Eq. point),
+ *       the conservative update (Eq. finite) and the CFL time step reduction.
+ *
+ * Conventions
+ *   Grid: nx by ny cells on [0, Lx] x [0, Ly], cell (i, j) centred at
+ *   ((i+1/2) Lx/nx, (j+1/2) Ly/ny).  A 1D problem is nx by 1 with periodic y.
+ *   Conservative variables (rho, rho U, rho V, rho E), p = (gamma-1)(rho E - rho|U|^2/2).
+ *   Host state arrays are FP64, structure of arrays, x fastest:
+ *     U [4][ny][nx]           cell averages
+ *     Wx[4][2][ny][nx+1]      x-face point values at y_j - g dy (g index 0) and
+ *                             y_j + g dy (index 1), g = sqrt(3)/6
+ *     Wy[4][2][ny+1][nx]      y-face point values at x_i - g dx, x_i + g dx
+ *   Face i of Wx lies between cells i-1 and i; on a periodic side faces 0 and
+ *   nx (0 and ny) are the same face and must carry equal values.
+ *   Boundary sides are ordered x-low, x-high, y-low, y-high.
+ *
+ * Ownership: the library allocates and owns all device memory of a handle
+ * (cudaMalloc in gks_create, cudaFree in gks_destroy).  Host pointers passed in
+ * are read (set) or written (get) during the call only.  Device pointers passed
+ * to the *_device calls must hold FP64 arrays of the layouts above on the
+ * handle's device.
+ *
+ * Errors are returned as gks_status, never by aborting; gks_last_error gives a
+ * message.  A step whose new state is not physical (rho <= 0, p <= 0 or not
+ * finite in some cell) is not taken: the state stays the one before the step and
+ * GKS_ENONPHYSICAL is reported (by gks_step, or by the next gks_sync /
+ * gks_get_state after gks_advance).
+ */
+#ifndef GKS_H
+#define GKS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GKS_OK = 0,
+  GKS_EINVAL = 1,        /* invalid argument */
+  GKS_ENOMEM = 2,        /* device allocation failed */
+  GKS_ECUDA = 3,         /* a CUDA call failed (message in gks_last_error) */
+  GKS_ENONPHYSICAL = 4,  /* a step produced a non-physical state; state rolled back */
+  GKS_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+  GKS_EUNSUPPORTED = 6
+} gks_status;
+
+/* Boundary conditions.  The paper names its boundary conditions (periodic,
+ * non-reflecting / outflow, reflective, isothermal no-slip) without defining
+ * them; this library uses: periodic = index wrap; outflow = the inside
+ * polynomial continued across the boundary face (equal states and
+ * derivatives), ghost averages copied; slip wall = mirror image with the normal
+ * momentum negated; isothermal no-slip = mirror image with velocity
+ * 2 u_wall - u, temperature 2 T_wall - T and equal density (images of the
+ * derivatives by the chain rule of that map). */
+typedef enum {
+  GKS_BC_PERIODIC = 0,
+  GKS_BC_OUTFLOW = 1,
+  GKS_BC_SLIPWALL = 2,
+  GKS_BC_NOSLIP_ISOTHERMAL = 3
+} gks_bc_kind;
+
+typedef struct {
+  int kind;        /* gks_bc_kind */
+  double u_wall;   /* wall velocity (x component), no-slip only */
+  double v_wall;   /* wall velocity (y component), no-slip only */
+  double T_wall;   /* wall temperature p/rho, no-slip only */
+} gks_bc;
+
+typedef enum {
+  GKS_FP64 = 0,      /* every step in FP64 */
+  GKS_FP32_BULK = 1  /* reconstruction, face evolution and face values in FP32;
+                        cell averages, the update and dt in FP64 */
+} gks_precision;
+
+typedef struct {
+  int precision;     /* gks_precision */
+  double weno_eps;   /* epsilon of the nonlinear weights, Eq. average (paper: unstated; default 1e-6) */
+  double weno_C;     /* C of I(U1) = C dx dy, Section 3.1 (paper: unstated; default 1) */
+  double tau_eps;    /* epsilon of the inviscid collision time, Section 4 (default 0.05) */
+  double tau_C;      /* C of the inviscid collision time, Section 4 (default 1) */
+  int viscous_dt;    /* 1: also bound dt by CFL rho h^2 / (2 mu max(4/3, gamma/Pr)) */
+} gks_options;
+
+typedef struct gks_handle gks_handle;
+
+/* Fills *opt with the defaults listed above. */
+void gks_default_options(gks_options* opt);
+
+/* Creates a solver for an nx by ny grid on [0,Lx] x [0,Ly] (nx, ny >= 1;
+ * ny = 1 requires periodic y, and likewise nx = 1 periodic x).  gamma > 1 is
+ * the ratio of specific heats (K = (4-2 gamma)/(gamma-1) internal degrees of
+ * freedom, Section 2.1); mu >= 0 the dynamic viscosity (mu = 0 selects the
+ * Euler model f_G = g and the inviscid collision time, Section 2.2 / 4); Pr > 0
+ * the Prandtl number (the energy flux gets (1/Pr - 1) times the face heat flux
+ * when Pr != 1).  bc[4] may be NULL for all-periodic.  opt may be NULL for the
+ * defaults.  cuda_stream is a cudaStream_t (NULL = the legacy default stream)
+ * on which all work of the handle is queued.  The state is zero until
+ * gks_set_state.  Returns GKS_EINVAL, GKS_ENOMEM or GKS_ECUDA on failure and
+ * leaves *out NULL. */
+gks_status gks_create(int nx, int ny, double Lx, double Ly, double gamma, double Pr, double mu,
+                      const gks_bc* bc, const gks_options* opt, void* cuda_stream,
+                      gks_handle** out);
+
+/* Copies a state from host memory (layouts above; Wx/Wy may be NULL, which
+ * sets every face point value to the mean of the two adjacent cell averages, a
+ * second-order start).  t is the simulation time.  Computes the first CFL
+ * bound.  Synchronous.  Clears a pending GKS_ENONPHYSICAL. */
+gks_status gks_set_state(gks_handle* h, const double* U, const double* Wx, const double* Wy,
+                         double t);
+
+/* Same, from device memory of the handle's device (FP64 arrays). */
+gks_status gks_set_state_device(gks_handle* h, const double* dU, const double* dWx,
+                                const double* dWy, double t);
+
+/* One time step with dt = min(CFL * dt_cfl, dt_max) where dt_cfl =
+ * min over cells of min(dx/(|U|+c), dy/(|V|+c)) (and the viscous bound if
+ * enabled) of the current state.  Synchronous: returns the status of this step
+ * and, if dt_taken != NULL, the dt used (0 if no step was taken). */
+gks_status gks_step(gks_handle* h, double CFL, double dt_max, double* dt_taken);
+
+/* Queues nsteps steps on the handle's stream without synchronising, each with
+ * dt = min(CFL * dt_cfl, t_end - t); steps once t >= t_end are skipped.  The
+ * sequence is captured once into a CUDA graph and replayed.  Errors of the
+ * queued steps are reported by gks_sync or gks_get_state. */
+gks_status gks_advance(gks_handle* h, int nsteps, double CFL, double t_end);
+
+/* Waits for queued work; returns the pending status.  t and steps (either may
+ * be NULL) receive the simulation time and the number of steps taken. */
+gks_status gks_sync(gks_handle* h, double* t, long long* steps);
+
+/* Copies the state to host memory (any of U, Wx, Wy, t may be NULL).
+ * Synchronous; returns the pending status (the state is the last good one). */
+gks_status gks_get_state(gks_handle* h, double* U, double* Wx, double* Wy, double* t);
+
+/* Same, into device memory (FP64 arrays). */
+gks_status gks_get_state_device(gks_handle* h, double* dU, double* dWx, double* dWy, double* t);
+
+/* Frees the handle and its device memory.  NULL is ignored. */
+void gks_destroy(gks_handle* h);
+
+/* Message of the last failed call on h (h may be NULL for create failures). */
+const char* gks_last_error(const gks_handle* h);
+
+/* Number of kernel launches one step issues (for launch accounting). */
+int gks_launches_per_step(const gks_handle* h);
+
+/* ---- unit-level entry points used for per-kernel parity checks ---- */
+
+/* Runs only the reconstruction of the current state and copies the
+ * coefficients (Ubar, a2, a3, a4, a5, a6) of every cell to host memory in the
+ * layout coef[4][6][ny][nx] (FP64).  Synchronous. */
+gks_status gks_debug_recon(gks_handle* h, double* coef);
+
+/* Runs reconstruction and the face evolution of the current state with the
+ * given dt and copies the face fluxes Fx[4][ny][nx+1], Fy[4][ny+1][nx] and new
+ * face values (state layout) to host memory, without updating the state. */
+gks_status gks_debug_flux(gks_handle* h, double dt, double* Fx, double* Fy, double* Wx_new,
+                          double* Wy_new);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GKS_H */

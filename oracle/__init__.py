@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
         if os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(s) for s in srcs):
             return LIB_PATH
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-o", tmp]
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp", "-o", tmp]
     cmd += [os.path.join(HERE, s) for s in SOURCES] + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB_PATH)

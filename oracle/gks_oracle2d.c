@@ -602,7 +602,10 @@ static void recon_var(const orc_params* P, double Uc, double Ue, double Uw, doub
   const double a5 = minmod(a5s, a5n);
   const double a3 = minmod(-t3s + a5 * dy / 6.0, t3n - a5 * dy / 6.0);
   /* cross derivative of the four one-sided stencils with the limited a2, a3;
-   * keep the smallest in magnitude (first one on ties) */
+   * keep the smallest in magnitude.  The paper gives no tie rule, and piecewise
+   * constant data produce exact ties of opposite sign: magnitudes within a
+   * relative 1e-8 of the current choice count as ties, and the first stencil in
+   * the order (+,+), (-,+), (-,-), (+,-) is kept */
   const double dxe = ep - em, dxw = wp - wm, dyn = np - nm, dys = sp - sm;
   const double r3 = sqrt(3.0);
   const int sx[4] = {1, -1, -1, 1}, sy[4] = {1, 1, -1, -1};
@@ -610,7 +613,7 @@ static void recon_var(const orc_params* P, double Uc, double Ue, double Uw, doub
   for (int k = 0; k < 4; ++k) {
     const double Dx = sx[k] > 0 ? dxe : dxw, Dy = sy[k] > 0 ? dyn : dys;
     const double c = sx[k] * (r3 * Dx / (dx * dy) - a3 / dx) + sy[k] * (r3 * Dy / (dx * dy) - a2 / dy);
-    if (k == 0 || fabs(c) < fabs(a6)) a6 = c;
+    if (k == 0 || fabs(c) < fabs(a6) * (1.0 - 1e-8)) a6 = c;
   }
   const double U1[6] = {Uc, a2, a3, a4, a5, a6};
   /* central stencil */

@@ -1,0 +1,942 @@
+// GB300 (sm_103a) kernels and C ABI of the compact third-order gas-kinetic
+// scheme (Pan & Xu, arXiv:1412.4489).  See include/gks.h for the interface.
+//
+// One step = six launches on the handle's stream, all reading a device-resident
+// control block so that the sequence can be captured once in a CUDA graph:
+//   k_begin    dt = min(CFL * dt_cfl, dt_max, t_end - t) from the running min
+//   k_ghost    one-cell ghost ring of the cell averages (boundary conditions)
+//   k_recon    compact reconstruction of every cell (Section 3.2)
+//   k_flux<0>  gas evolution at every x-face (Section 2.2, 3.3, 4)
+//   k_flux<1>  gas evolution at every y-face (frame rotated: n = y, t = x)
+//   k_update   conservative update (Eq. finite) in FP64 + next CFL bound
+//              (warp-shuffle / block / atomic min) + physical-state check
+//   k_end      advance t and the step counter
+// Cell averages and face values are double-buffered; the buffer in use is the
+// parity of the device step counter, so a failed step leaves the last good
+// state in place.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/gks.h"
+#include "gks_device.cuh"
+
+using namespace gks;
+
+namespace {
+
+constexpr int kLaunchesPerStep = 7;
+
+struct Ctrl {
+  unsigned long long dtbits[2];  // running min of the CFL bound, per parity
+  double t;
+  double dt;
+  long long steps;
+  int status;
+  int skip;
+  long long fail_step;
+};
+
+struct BCs {
+  int kind[4];
+  double uw[4], vw[4], Tw[4];
+};
+
+struct Geo {
+  int nx, ny, pitch;   // pitch: row length of the padded cell arrays
+  size_t plane;        // (ny+2) * pitch
+  double dx, dy;
+  double gamma, mu, Pr;
+  double weno_eps, weno_C, tau_eps, tau_C;
+  int viscous_dt;
+  BCs bc;
+};
+
+__device__ __forceinline__ size_t ci(const Geo& g, int v, int i, int j) {
+  return (size_t)v * g.plane + (size_t)(j + 1) * g.pitch + (i + 1);
+}
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+template <class T> struct Store;
+template <> struct Store<double> { static __device__ __forceinline__ double to(double x) { return x; } };
+template <> struct Store<float> { static __device__ __forceinline__ float to(double x) { return (float)x; } };
+
+// ---------------------------------------------------------------------------
+// boundary images of cell averages (ghost ring)
+// ---------------------------------------------------------------------------
+__device__ void bc_value(int kind, double gamma, double uwt, double Tw, int axis, const double in[4],
+                         double out[4]) {
+  if (kind == GKS_BC_PERIODIC || kind == GKS_BC_OUTFLOW) {
+    for (int k = 0; k < 4; ++k) out[k] = in[k];
+    return;
+  }
+  double f[4];
+  f[0] = in[0];
+  f[3] = in[3];
+  f[1] = axis == 0 ? in[1] : in[2];
+  f[2] = axis == 0 ? in[2] : in[1];
+  double o[4];
+  if (kind == GKS_BC_SLIPWALL) {
+    o[0] = f[0]; o[1] = -f[1]; o[2] = f[2]; o[3] = f[3];
+  } else {
+    const double rho = f[0], mn = f[1], mt = f[2];
+    o[0] = rho;
+    o[1] = -mn;
+    o[2] = 2.0 * rho * uwt - mt;
+    o[3] = 2.0 * rho * uwt * uwt - 2.0 * uwt * mt + (mn * mn + mt * mt) / rho +
+           2.0 * rho * Tw / (gamma - 1.0) - f[3];
+  }
+  out[0] = o[0];
+  out[3] = o[3];
+  out[1] = axis == 0 ? o[1] : o[2];
+  out[2] = axis == 0 ? o[2] : o[1];
+}
+
+__device__ __forceinline__ double wall_t_velocity(const BCs& b, int side) {
+  // tangential wall velocity in the face frame: y-component on x-sides, x on y-sides
+  return side < 2 ? b.vw[side] : b.uw[side];
+}
+
+// value of a ghost cell; y is resolved first, so corners are x-images of y-ghosts
+__device__ void ghost_cell(const Geo& g, const double* __restrict__ U, int i, int j, double out[4]) {
+  int is = i, js = j;
+  int xs = -1, ys = -1;  // boundary side applied
+  if (j < 0) { ys = 2; js = g.bc.kind[2] == GKS_BC_PERIODIC ? g.ny - 1 : 0; }
+  if (j >= g.ny) { ys = 3; js = g.bc.kind[3] == GKS_BC_PERIODIC ? 0 : g.ny - 1; }
+  if (i < 0) { xs = 0; is = g.bc.kind[0] == GKS_BC_PERIODIC ? g.nx - 1 : 0; }
+  if (i >= g.nx) { xs = 1; is = g.bc.kind[1] == GKS_BC_PERIODIC ? 0 : g.nx - 1; }
+  double w[4], t[4];
+  for (int v = 0; v < 4; ++v) w[v] = U[ci(g, v, is, js)];
+  if (ys >= 0) {
+    bc_value(g.bc.kind[ys], g.gamma, wall_t_velocity(g.bc, ys), g.bc.Tw[ys], 1, w, t);
+    for (int v = 0; v < 4; ++v) w[v] = t[v];
+  }
+  if (xs >= 0) {
+    bc_value(g.bc.kind[xs], g.gamma, wall_t_velocity(g.bc, xs), g.bc.Tw[xs], 0, w, t);
+    for (int v = 0; v < 4; ++v) w[v] = t[v];
+  }
+  for (int v = 0; v < 4; ++v) out[v] = w[v];
+}
+
+// ---------------------------------------------------------------------------
+// control kernels
+// ---------------------------------------------------------------------------
+__global__ void k_begin(Ctrl* c, double cfl, double dt_max, double t_end) {
+  const int s = (int)(c->steps & 1);
+  const double bound = bitsd(c->dtbits[s]);
+  double dt = fmin(cfl * bound, dt_max);
+  dt = fmin(dt, t_end - c->t);
+  c->dt = dt;
+  c->skip = (c->status != GKS_OK || !(dt > 0.0)) ? 1 : 0;
+  if (!c->skip) c->dtbits[s ^ 1] = dbits(INFINITY);
+}
+
+__global__ void k_end(Ctrl* c) {
+  if (c->skip || c->status != GKS_OK) return;
+  c->t += c->dt;
+  c->steps += 1;
+}
+
+// ---------------------------------------------------------------------------
+// ghost ring: perimeter of the padded cell array of the current buffer
+// ---------------------------------------------------------------------------
+__global__ void k_ghost(Geo g, double* U0, double* U1, const Ctrl* c, int force) {
+  if (!force && c->skip) return;
+  double* U = (c->steps & 1) ? U1 : U0;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = g.nx + 2;
+  int i, j;
+  if (p < row) { i = p - 1; j = -1; }
+  else if (p < 2 * row) { i = p - row - 1; j = g.ny; }
+  else if (p < 2 * row + g.ny) { i = -1; j = p - 2 * row; }
+  else if (p < 2 * row + 2 * g.ny) { i = g.nx; j = p - 2 * row - g.ny; }
+  else return;
+  double w[4];
+  ghost_cell(g, U, i, j, w);
+  for (int v = 0; v < 4; ++v) U[ci(g, v, i, j)] = w[v];
+}
+
+// ---------------------------------------------------------------------------
+// reconstruction
+// ---------------------------------------------------------------------------
+template <class R, class TW>
+__global__ void __launch_bounds__(256) k_recon(Geo g, const double* U0, const double* U1, const TW* Wx0,
+                                               const TW* Wx1, const TW* Wy0, const TW* Wy1, R* __restrict__ coef,
+                                               const Ctrl* c, int force) {
+  if (!force && c->skip) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  const int par = (int)(c->steps & 1);
+  const double* __restrict__ U = par ? U1 : U0;
+  const TW* __restrict__ Wx = par ? Wx1 : Wx0;
+  const TW* __restrict__ Wy = par ? Wy1 : Wy0;
+  const int nx = g.nx, ny = g.ny;
+  const size_t fxp = (size_t)ny * (nx + 1), fyp = (size_t)(ny + 1) * nx;
+  const R dx = R(g.dx), dy = R(g.dy);
+  R a[4][5];
+  R cbar[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const R cc = R(U[ci(g, v, i, j)]);
+    cbar[v] = cc;
+    const TW* wx = Wx + (size_t)v * 2 * fxp + (size_t)j * (nx + 1);
+    const TW* wy = Wy + (size_t)v * 2 * fyp;
+    recon_var<R>(cc, R(U[ci(g, v, i + 1, j)]), R(U[ci(g, v, i - 1, j)]), R(U[ci(g, v, i, j + 1)]),
+                 R(U[ci(g, v, i, j - 1)]), R(wx[i + 1]), R(wx[fxp + i + 1]), R(wx[i]), R(wx[fxp + i]),
+                 R(wy[(size_t)(j + 1) * nx + i]), R(wy[fyp + (size_t)(j + 1) * nx + i]),
+                 R(wy[(size_t)j * nx + i]), R(wy[fyp + (size_t)j * nx + i]), dx, dy, R(g.weno_eps),
+                 R(g.weno_C), a[v]);
+  }
+  // positivity: rho and p at the four face centres, else the constant average
+  const R gm1 = R(g.gamma - 1.0);
+  bool bad = false;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    R w[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const R x = f == 0 ? R(0.5) * dx : (f == 1 ? -R(0.5) * dx : R(0));
+      const R y = f == 2 ? R(0.5) * dy : (f == 3 ? -R(0.5) * dy : R(0));
+      w[v] = cbar[v] + a[v][0] * x + a[v][1] * y + a[v][2] * R(0.5) * (x * x - dx * dx / R(12)) +
+             a[v][3] * R(0.5) * (y * y - dy * dy / R(12)) + a[v][4] * x * y;
+    }
+    const R p = gm1 * (w[3] - R(0.5) * (w[1] * w[1] + w[2] * w[2]) / w[0]);
+    if (!(w[0] > R(0)) || !(p > R(0))) bad = true;
+  }
+  const size_t N = (size_t)nx * ny, o = (size_t)j * nx + i;
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) coef[(size_t)(k * 4 + v) * N + o] = bad ? R(0) : a[v][k];
+}
+
+// ---------------------------------------------------------------------------
+// face evolution
+// ---------------------------------------------------------------------------
+// face-frame slot of physical variable v (y-faces swap the momenta)
+template <int AX> __device__ __forceinline__ int slot(int v) { return AX == 0 ? v : (v == 1 ? 2 : (v == 2 ? 1 : v)); }
+
+// value and derivatives of cell (i, j)'s polynomial at the centre of its face
+// on side s (+1: the face at +h_n/2, -1: at -h_n/2), in the face frame of axis AX
+template <int AX, class R>
+__device__ __forceinline__ void side_state(const Geo& g, const double* __restrict__ U, const R* __restrict__ coef,
+                                           int i, int j, int s, FaceState<R>& S) {
+  const size_t N = (size_t)g.nx * g.ny, o = (size_t)j * g.nx + i;
+  const R hn = R(AX == 0 ? g.dx : g.dy), ht = R(AX == 0 ? g.dy : g.dx);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const R c = R(U[ci(g, v, i, j)]);
+    const R a2 = coef[(size_t)(0 * 4 + v) * N + o], a3 = coef[(size_t)(1 * 4 + v) * N + o];
+    const R a4 = coef[(size_t)(2 * 4 + v) * N + o], a5 = coef[(size_t)(3 * 4 + v) * N + o];
+    const R a6 = coef[(size_t)(4 * 4 + v) * N + o];
+    const R an = AX == 0 ? a2 : a3, at = AX == 0 ? a3 : a2;
+    const R ann = AX == 0 ? a4 : a5, att = AX == 0 ? a5 : a4;
+    const int k = slot<AX>(v);
+    const R sh = R(s) * R(0.5) * hn;
+    S.w[0][k] = c + an * sh + ann * hn * hn / R(12) - att * ht * ht / R(24);
+    S.w[1][k] = an + ann * sh;
+    S.w[2][k] = at + a6 * sh;
+    S.w[3][k] = ann;
+    S.w[4][k] = a6;
+    S.w[5][k] = att;
+  }
+}
+
+template <int AX, class R, class TW>
+__global__ void __launch_bounds__(128) k_flux(Geo g, const double* U0, const double* U1, const R* __restrict__ coef,
+                                              TW* Wn0, TW* Wn1, R* __restrict__ F, const Ctrl* c, int force) {
+  if (!force && c->skip) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nx = g.nx, ny = g.ny;
+  const int fx = AX == 0 ? nx + 1 : nx, fy = AX == 0 ? ny : ny + 1;
+  if (i >= fx || j >= fy) return;
+  const int par = (int)(c->steps & 1);
+  const double* __restrict__ U = par ? U1 : U0;
+  TW* __restrict__ Wn = par ? Wn0 : Wn1;  // new face values go to the other buffer
+  const double dt = c->dt;
+
+  // the two cells sharing the face and the boundary sides
+  const int f = AX == 0 ? i : j;      // face index along the normal
+  const int nf = AX == 0 ? nx : ny;   // faces 0 and nf are on the boundary
+  const int lo_side = AX == 0 ? 0 : 2, hi_side = lo_side + 1;
+  int cl = f - 1, cr = f;
+  const bool lo = f == 0, hi = f == nf;
+  const bool lo_per = g.bc.kind[lo_side] == GKS_BC_PERIODIC, hi_per = g.bc.kind[hi_side] == GKS_BC_PERIODIC;
+  if (lo && lo_per) cl = nf - 1;
+  if (hi && hi_per) cr = 0;
+
+  FaceState<R> L, Rt;
+  auto cell = [&](int n) { return AX == 0 ? n : i; };
+  auto row = [&](int n) { return AX == 0 ? j : n; };
+  if (lo && !lo_per) {
+    side_state<AX>(g, U, coef, cell(cr), row(cr), -1, Rt);
+    if (g.bc.kind[lo_side] == GKS_BC_OUTFLOW) L = Rt;
+    else wall_image<R>(g.bc.kind[lo_side], R(g.gamma), R(wall_t_velocity(g.bc, lo_side)), R(g.bc.Tw[lo_side]), Rt, L);
+  } else if (hi && !hi_per) {
+    side_state<AX>(g, U, coef, cell(cl), row(cl), +1, L);
+    if (g.bc.kind[hi_side] == GKS_BC_OUTFLOW) Rt = L;
+    else wall_image<R>(g.bc.kind[hi_side], R(g.gamma), R(wall_t_velocity(g.bc, hi_side)), R(g.bc.Tw[hi_side]), L, Rt);
+  } else {
+    side_state<AX>(g, U, coef, cell(cl), row(cl), +1, L);
+    side_state<AX>(g, U, coef, cell(cr), row(cr), -1, Rt);
+  }
+
+  // six cell averages around the face (ghost ring included), face frame
+  R avg[2][3][4];
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int ii = AX == 0 ? i - 1 + m : i - 1 + k;
+      const int jj = AX == 0 ? j - 1 + k : j - 1 + m;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) avg[m][k][slot<AX>(v)] = R(U[ci(g, v, ii, jj)]);
+    }
+
+  FaceParams P;
+  P.gamma = g.gamma; P.mu = g.mu; P.Pr = g.Pr; P.tau_eps = g.tau_eps; P.tau_C = g.tau_C;
+  P.dn = AX == 0 ? g.dx : g.dy;
+  P.dtan = AX == 0 ? g.dy : g.dx;
+  R Fl[4], Wm[4], Wp[4];
+  face_evolution<R>(P, L, Rt, avg, R(dt), Fl, Wm, Wp);
+
+  const size_t nfaces = (size_t)fx * fy, o = (size_t)j * fx + i;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int k = slot<AX>(v);
+    F[(size_t)v * nfaces + o] = Fl[k];
+    Wn[(size_t)(v * 2 + 0) * nfaces + o] = Store<TW>::to((double)Wm[k]);
+    Wn[(size_t)(v * 2 + 1) * nfaces + o] = Store<TW>::to((double)Wp[k]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// update, CFL bound of the new state, physical check
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double cell_bound(const Geo& g, const double w[4]) {
+  const double rho = w[0], u = w[1] / rho, v = w[2] / rho;
+  const double p = (g.gamma - 1.0) * (w[3] - 0.5 * rho * (u * u + v * v));
+  const double c = sqrt(g.gamma * p / rho);
+  double b = fmin(g.dx / (fabs(u) + c), g.dy / (fabs(v) + c));
+  if (g.viscous_dt && g.mu > 0.0) {
+    const double h = fmin(g.dx, g.dy);
+    b = fmin(b, rho * h * h / (2.0 * g.mu * fmax(4.0 / 3.0, g.gamma / g.Pr)));
+  }
+  return (rho > 0.0 && p > 0.0) ? b : 0.0;
+}
+
+__device__ __forceinline__ void block_min_to(double b, unsigned long long* slot) {
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) b = fmin(b, __shfl_xor_sync(0xffffffffu, b, o));
+  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+  const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+  if (lane == 0) red[warp] = b;
+  __syncthreads();
+  if (warp == 0) {
+    b = lane < nw ? red[lane] : INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b = fmin(b, __shfl_xor_sync(0xffffffffu, b, o));
+    if (lane == 0 && b < INFINITY) atomicMin(slot, dbits(b));
+  }
+}
+
+template <class TF>
+__global__ void __launch_bounds__(256) k_update(Geo g, double* U0, double* U1, const TF* __restrict__ Fx,
+                                                const TF* __restrict__ Fy, Ctrl* c) {
+  if (c->skip) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int par = (int)(c->steps & 1);
+  const double* __restrict__ U = par ? U1 : U0;
+  double* __restrict__ Un = par ? U0 : U1;
+  double b = INFINITY;
+  if (i < g.nx && j < g.ny) {
+    const int nx = g.nx, ny = g.ny;
+    const size_t nfx = (size_t)ny * (nx + 1), nfy = (size_t)(ny + 1) * nx;
+    const double idx = 1.0 / g.dx, idy = 1.0 / g.dy;
+    double w[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const double fw = (double)Fx[v * nfx + (size_t)j * (nx + 1) + i];
+      const double fe = (double)Fx[v * nfx + (size_t)j * (nx + 1) + i + 1];
+      const double gs = (double)Fy[v * nfy + (size_t)j * nx + i];
+      const double gn = (double)Fy[v * nfy + (size_t)(j + 1) * nx + i];
+      w[v] = U[ci(g, v, i, j)] + (fw - fe) * idx + (gs - gn) * idy;
+      Un[ci(g, v, i, j)] = w[v];
+    }
+    b = cell_bound(g, w);
+    if (!(b > 0.0) || !isfinite(w[3]) || !isfinite(w[1]) || !isfinite(w[2])) {
+      if (atomicCAS(&c->status, GKS_OK, GKS_ENONPHYSICAL) == GKS_OK) c->fail_step = c->steps;
+      b = INFINITY;
+    }
+  }
+  block_min_to(b, &c->dtbits[(c->steps & 1) ^ 1]);
+}
+
+// CFL bound of the current state (after set_state)
+__global__ void k_dtbound(Geo g, const double* U0, const double* U1, Ctrl* c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int par = (int)(c->steps & 1);
+  const double* U = par ? U1 : U0;
+  double b = INFINITY;
+  if (i < g.nx && j < g.ny) {
+    double w[4];
+    for (int v = 0; v < 4; ++v) w[v] = U[ci(g, v, i, j)];
+    b = cell_bound(g, w);
+    if (!(b > 0.0)) {
+      atomicCAS(&c->status, GKS_OK, GKS_ENONPHYSICAL);
+      b = INFINITY;
+    }
+  }
+  block_min_to(b, &c->dtbits[par]);
+}
+
+// ---------------------------------------------------------------------------
+// state transfer
+// ---------------------------------------------------------------------------
+__global__ void k_scatter_U(Geo g, const double* __restrict__ src, double* U0, double* U1, const Ctrl* c, int to_dev) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  double* U = (c->steps & 1) ? U1 : U0;
+  for (int v = 0; v < 4; ++v) {
+    const size_t o = ((size_t)v * g.ny + j) * g.nx + i;
+    if (to_dev) U[ci(g, v, i, j)] = src[o];
+    else const_cast<double*>(src)[o] = U[ci(g, v, i, j)];
+  }
+}
+
+template <class TW>
+__global__ void k_copy_W(const double* __restrict__ src, TW* W0, TW* W1, size_t n, const Ctrl* c, int to_dev) {
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  TW* W = (c->steps & 1) ? W1 : W0;
+  if (to_dev) W[k] = Store<TW>::to(src[k]);
+  else const_cast<double*>(src)[k] = (double)W[k];
+}
+
+// face values = mean of the two adjacent averages (ghosts included)
+template <int AX, class TW>
+__global__ void k_init_W(Geo g, const double* U0, const double* U1, TW* W0, TW* W1, const Ctrl* c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int fx = AX == 0 ? g.nx + 1 : g.nx, fy = AX == 0 ? g.ny : g.ny + 1;
+  if (i >= fx || j >= fy) return;
+  const int par = (int)(c->steps & 1);
+  const double* U = par ? U1 : U0;
+  TW* W = par ? W1 : W0;
+  const size_t n = (size_t)fx * fy, o = (size_t)j * fx + i;
+  for (int v = 0; v < 4; ++v) {
+    const double a = U[ci(g, v, AX == 0 ? i - 1 : i, AX == 0 ? j : j - 1)];
+    const double b = U[ci(g, v, i, j)];
+    W[(size_t)(v * 2) * n + o] = Store<TW>::to(0.5 * (a + b));
+    W[(size_t)(v * 2 + 1) * n + o] = Store<TW>::to(0.5 * (a + b));
+  }
+}
+
+template <class R>
+__global__ void k_coef_out(Geo g, const double* U0, const double* U1, const R* coef, double* out, const Ctrl* c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  const double* U = (c->steps & 1) ? U1 : U0;
+  const size_t N = (size_t)g.nx * g.ny, o = (size_t)j * g.nx + i;
+  for (int v = 0; v < 4; ++v) {
+    out[(size_t)(v * 6) * N + o] = U[ci(g, v, i, j)];
+    for (int k = 0; k < 5; ++k) out[(size_t)(v * 6 + k + 1) * N + o] = (double)coef[(size_t)(k * 4 + v) * N + o];
+  }
+}
+
+template <class R>
+__global__ void k_to_double(const R* src, double* dst, size_t n) {
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) dst[k] = (double)src[k];
+}
+
+__global__ void k_set_dt(Ctrl* c, double dt) {
+  c->dt = dt;
+  c->skip = 0;
+}
+
+}  // namespace
+
+// ===========================================================================
+// host side
+// ===========================================================================
+struct gks_handle {
+  Geo g;
+  int prec;
+  cudaStream_t stream;
+  bool own_stream;
+  int device;
+  double* U[2];
+  void* Wx[2];
+  void* Wy[2];
+  void* coef;
+  void* Fx;
+  void* Fy;
+  Ctrl* ctrl;
+  Ctrl* hctrl;       // pinned mirror
+  double* staging;   // device FP64 scratch for host transfers
+  size_t staging_n;
+  cudaGraphExec_t graph1, graph16;
+  double graph_cfl, graph_tend;
+  std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+namespace {
+
+size_t n_wx(const Geo& g) { return (size_t)8 * g.ny * (g.nx + 1); }
+size_t n_wy(const Geo& g) { return (size_t)8 * (g.ny + 1) * g.nx; }
+size_t n_u(const Geo& g) { return (size_t)4 * g.nx * g.ny; }
+
+gks_status fail(gks_handle* h, gks_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(h, GKS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
+  } while (0)
+
+dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
+
+template <class R, class TW>
+gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double t_end, bool with_begin_end,
+                               bool do_update, int force) {
+  const Geo& g = h->g;
+  cudaStream_t s = h->stream;
+  if (with_begin_end) k_begin<<<1, 1, 0, s>>>(h->ctrl, cfl, dt_max, t_end);
+  const int per = 2 * (g.nx + 2) + 2 * g.ny;
+  k_ghost<<<(per + 127) / 128, 128, 0, s>>>(g, h->U[0], h->U[1], h->ctrl, force);
+  const dim3 b2(32, 8), bf(32, 4);
+  k_recon<R, TW><<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, h->U[0], h->U[1], (const TW*)h->Wx[0], (const TW*)h->Wx[1],
+                                                       (const TW*)h->Wy[0], (const TW*)h->Wy[1], (R*)h->coef,
+                                                       h->ctrl, force);
+  k_flux<0, R, TW><<<grid2(g.nx + 1, g.ny, bf), bf, 0, s>>>(g, h->U[0], h->U[1], (const R*)h->coef, (TW*)h->Wx[0],
+                                                             (TW*)h->Wx[1], (R*)h->Fx, h->ctrl, force);
+  k_flux<1, R, TW><<<grid2(g.nx, g.ny + 1, bf), bf, 0, s>>>(g, h->U[0], h->U[1], (const R*)h->coef, (TW*)h->Wy[0],
+                                                             (TW*)h->Wy[1], (R*)h->Fy, h->ctrl, force);
+  if (do_update) k_update<R><<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, h->U[0], h->U[1], (const R*)h->Fx,
+                                                                   (const R*)h->Fy, h->ctrl);
+  if (with_begin_end) k_end<<<1, 1, 0, s>>>(h->ctrl);
+  CK(cudaGetLastError());
+  return GKS_OK;
+}
+
+gks_status launch_step(gks_handle* h, double cfl, double dt_max, double t_end) {
+  if (h->prec == GKS_FP64) return launch_step_kernels<double, double>(h, cfl, dt_max, t_end, true, true, 0);
+  return launch_step_kernels<float, float>(h, cfl, dt_max, t_end, true, true, 0);
+}
+
+gks_status read_ctrl(gks_handle* h) {
+  CK(cudaMemcpyAsync(h->hctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return GKS_OK;
+}
+
+void destroy_graphs(gks_handle* h) {
+  if (h->graph1) cudaGraphExecDestroy(h->graph1);
+  if (h->graph16) cudaGraphExecDestroy(h->graph16);
+  h->graph1 = h->graph16 = nullptr;
+}
+
+gks_status capture(gks_handle* h, int nsteps, double cfl, double t_end, cudaGraphExec_t* out) {
+  cudaGraph_t graph;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  gks_status st = GKS_OK;
+  for (int k = 0; k < nsteps && st == GKS_OK; ++k) st = launch_step(h, cfl, INFINITY, t_end);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  if (st != GKS_OK) return st;
+  if (e != cudaSuccess) return fail(h, GKS_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(h, GKS_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+  return GKS_OK;
+}
+
+gks_status reset_ctrl(gks_handle* h, double t) {
+  memset(h->hctrl, 0, sizeof(Ctrl));
+  const double inf = INFINITY;
+  uint64_t b;
+  memcpy(&b, &inf, 8);
+  h->hctrl->dtbits[0] = h->hctrl->dtbits[1] = b;
+  h->hctrl->t = t;
+  CK(cudaMemcpyAsync(h->ctrl, h->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return GKS_OK;
+}
+
+template <class TW>
+gks_status load_state(gks_handle* h, const double* dU, const double* dWx, const double* dWy) {
+  const Geo& g = h->g;
+  cudaStream_t s = h->stream;
+  const dim3 b2(32, 8);
+  k_scatter_U<<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, dU, h->U[0], h->U[1], h->ctrl, 1);
+  const int per = 2 * (g.nx + 2) + 2 * g.ny;
+  k_ghost<<<(per + 127) / 128, 128, 0, s>>>(g, h->U[0], h->U[1], h->ctrl, 1);
+  if (dWx) {
+    k_copy_W<TW><<<(unsigned)((n_wx(g) + 255) / 256), 256, 0, s>>>(dWx, (TW*)h->Wx[0], (TW*)h->Wx[1], n_wx(g), h->ctrl, 1);
+  } else {
+    k_init_W<0, TW><<<grid2(g.nx + 1, g.ny, b2), b2, 0, s>>>(g, h->U[0], h->U[1], (TW*)h->Wx[0], (TW*)h->Wx[1], h->ctrl);
+  }
+  if (dWy) {
+    k_copy_W<TW><<<(unsigned)((n_wy(g) + 255) / 256), 256, 0, s>>>(dWy, (TW*)h->Wy[0], (TW*)h->Wy[1], n_wy(g), h->ctrl, 1);
+  } else {
+    k_init_W<1, TW><<<grid2(g.nx, g.ny + 1, b2), b2, 0, s>>>(g, h->U[0], h->U[1], (TW*)h->Wy[0], (TW*)h->Wy[1], h->ctrl);
+  }
+  k_dtbound<<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, h->U[0], h->U[1], h->ctrl);
+  CK(cudaGetLastError());
+  return GKS_OK;
+}
+
+template <class TW>
+gks_status store_state(gks_handle* h, double* dU, double* dWx, double* dWy) {
+  const Geo& g = h->g;
+  cudaStream_t s = h->stream;
+  const dim3 b2(32, 8);
+  if (dU) k_scatter_U<<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, dU, h->U[0], h->U[1], h->ctrl, 0);
+  if (dWx)
+    k_copy_W<TW><<<(unsigned)((n_wx(g) + 255) / 256), 256, 0, s>>>(dWx, (TW*)h->Wx[0], (TW*)h->Wx[1], n_wx(g), h->ctrl, 0);
+  if (dWy)
+    k_copy_W<TW><<<(unsigned)((n_wy(g) + 255) / 256), 256, 0, s>>>(dWy, (TW*)h->Wy[0], (TW*)h->Wy[1], n_wy(g), h->ctrl, 0);
+  CK(cudaGetLastError());
+  return GKS_OK;
+}
+
+gks_status check_args(int nx, int ny, double Lx, double Ly, double gamma, double Pr, double mu, const gks_bc* bc,
+                      const gks_options* o, std::string& why) {
+  if (nx < 1 || ny < 1 || (long long)nx * ny > (1LL << 31)) { why = "nx, ny must be >= 1"; return GKS_EINVAL; }
+  if (!(Lx > 0) || !(Ly > 0)) { why = "Lx, Ly must be > 0"; return GKS_EINVAL; }
+  if (!(gamma > 1.0) || !(gamma < 3.0)) { why = "gamma must lie in (1, 3)"; return GKS_EINVAL; }
+  if (!(Pr > 0)) { why = "Pr must be > 0"; return GKS_EINVAL; }
+  if (!(mu >= 0)) { why = "mu must be >= 0"; return GKS_EINVAL; }
+  if (o->precision != GKS_FP64 && o->precision != GKS_FP32_BULK) { why = "unknown precision"; return GKS_EINVAL; }
+  if (!(o->weno_eps >= 0) || !(o->weno_C > 0) || !(o->tau_eps >= 0) || !(o->tau_C >= 0)) {
+    why = "invalid scheme constants"; return GKS_EINVAL;
+  }
+  if (bc) {
+    for (int k = 0; k < 4; ++k) {
+      if (bc[k].kind < 0 || bc[k].kind > 3) { why = "unknown boundary kind"; return GKS_EINVAL; }
+      if (bc[k].kind == GKS_BC_NOSLIP_ISOTHERMAL && !(bc[k].T_wall > 0)) { why = "T_wall must be > 0"; return GKS_EINVAL; }
+    }
+    if ((bc[0].kind == GKS_BC_PERIODIC) != (bc[1].kind == GKS_BC_PERIODIC) ||
+        (bc[2].kind == GKS_BC_PERIODIC) != (bc[3].kind == GKS_BC_PERIODIC)) {
+      why = "periodic must be set on both sides of an axis"; return GKS_EINVAL;
+    }
+    if ((nx == 1 && bc[0].kind != GKS_BC_PERIODIC) || (ny == 1 && bc[2].kind != GKS_BC_PERIODIC)) {
+      why = "a single cell across needs periodic sides"; return GKS_EINVAL;
+    }
+  }
+  return GKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gks_default_options(gks_options* o) {
+  if (!o) return;
+  o->precision = GKS_FP64;
+  o->weno_eps = 1e-6;
+  o->weno_C = 1.0;
+  o->tau_eps = 0.05;
+  o->tau_C = 1.0;
+  o->viscous_dt = 0;
+}
+
+gks_status gks_create(int nx, int ny, double Lx, double Ly, double gamma, double Pr, double mu, const gks_bc* bc,
+                      const gks_options* opt, void* cuda_stream, gks_handle** out) {
+  if (!out) { g_create_err = "out is NULL"; return GKS_EINVAL; }
+  *out = nullptr;
+  gks_options o;
+  gks_default_options(&o);
+  if (opt) o = *opt;
+  std::string why;
+  if (check_args(nx, ny, Lx, Ly, gamma, Pr, mu, bc, &o, why) != GKS_OK) { g_create_err = why; return GKS_EINVAL; }
+  gks_handle* h = new gks_handle();
+  Geo& g = h->g;
+  g.nx = nx; g.ny = ny;
+  g.pitch = ((nx + 2) + 1) & ~1;
+  g.plane = (size_t)(ny + 2) * g.pitch;
+  g.dx = Lx / nx; g.dy = Ly / ny;
+  g.gamma = gamma; g.mu = mu; g.Pr = Pr;
+  g.weno_eps = o.weno_eps; g.weno_C = o.weno_C; g.tau_eps = o.tau_eps; g.tau_C = o.tau_C;
+  g.viscous_dt = o.viscous_dt;
+  for (int k = 0; k < 4; ++k) {
+    g.bc.kind[k] = bc ? bc[k].kind : GKS_BC_PERIODIC;
+    g.bc.uw[k] = bc ? bc[k].u_wall : 0.0;
+    g.bc.vw[k] = bc ? bc[k].v_wall : 0.0;
+    g.bc.Tw[k] = bc ? bc[k].T_wall : 1.0;
+  }
+  h->prec = o.precision;
+  const size_t wsz = h->prec == GKS_FP64 ? 8 : 4;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) {
+    if (cuda_stream) { h->stream = (cudaStream_t)cuda_stream; h->own_stream = false; }
+    else { e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking); h->own_stream = true; }
+  }
+  auto alloc = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+  };
+  for (int b = 0; b < 2; ++b) {
+    alloc((void**)&h->U[b], 4 * g.plane * sizeof(double));
+    alloc(&h->Wx[b], n_wx(g) * wsz);
+    alloc(&h->Wy[b], n_wy(g) * wsz);
+  }
+  alloc(&h->coef, (size_t)20 * nx * ny * wsz);
+  alloc(&h->Fx, (size_t)4 * ny * (nx + 1) * wsz);
+  alloc(&h->Fy, (size_t)4 * (ny + 1) * nx * wsz);
+  alloc((void**)&h->ctrl, sizeof(Ctrl));
+  h->staging_n = n_u(g);
+  if (n_wx(g) > h->staging_n) h->staging_n = n_wx(g);
+  if (n_wy(g) > h->staging_n) h->staging_n = n_wy(g);
+  if (h->staging_n < (size_t)24 * nx * ny) h->staging_n = (size_t)24 * nx * ny;
+  alloc((void**)&h->staging, h->staging_n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->hctrl, sizeof(Ctrl));
+  if (e == cudaSuccess)
+    for (int b = 0; b < 2; ++b) {
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->U[b], 0, 4 * g.plane * sizeof(double), h->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->Wx[b], 0, n_wx(g) * wsz, h->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->Wy[b], 0, n_wy(g) * wsz, h->stream);
+    }
+  if (e != cudaSuccess) {
+    g_create_err = std::string("gks_create: ") + cudaGetErrorString(e);
+    const gks_status st = e == cudaErrorMemoryAllocation ? GKS_ENOMEM : GKS_ECUDA;
+    gks_destroy(h);
+    return st;
+  }
+  if (reset_ctrl(h, 0.0) != GKS_OK) {
+    g_create_err = h->err;
+    gks_destroy(h);
+    return GKS_ECUDA;
+  }
+  *out = h;
+  return GKS_OK;
+}
+
+gks_status gks_set_state_device(gks_handle* h, const double* dU, const double* dWx, const double* dWy, double t) {
+  if (!h || !dU) return fail(h, GKS_EINVAL, "gks_set_state: U is required");
+  CK(cudaSetDevice(h->device));
+  gks_status st = reset_ctrl(h, t);
+  if (st != GKS_OK) return st;
+  st = h->prec == GKS_FP64 ? load_state<double>(h, dU, dWx, dWy) : load_state<float>(h, dU, dWx, dWy);
+  if (st != GKS_OK) return st;
+  st = read_ctrl(h);
+  if (st != GKS_OK) return st;
+  if (h->hctrl->status != GKS_OK) return fail(h, GKS_ENONPHYSICAL, "gks_set_state: state has rho <= 0 or p <= 0");
+  return GKS_OK;
+}
+
+gks_status gks_set_state(gks_handle* h, const double* U, const double* Wx, const double* Wy, double t) {
+  if (!h || !U) return fail(h, GKS_EINVAL, "gks_set_state: U is required");
+  CK(cudaSetDevice(h->device));
+  const Geo& g = h->g;
+  // U goes through the staging buffer; face values through the same buffer in turn
+  gks_status st = reset_ctrl(h, t);
+  if (st != GKS_OK) return st;
+  CK(cudaMemcpyAsync(h->staging, U, n_u(g) * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  const dim3 b2(32, 8);
+  k_scatter_U<<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, h->staging, h->U[0], h->U[1], h->ctrl, 1);
+  const int per = 2 * (g.nx + 2) + 2 * g.ny;
+  k_ghost<<<(per + 127) / 128, 128, 0, h->stream>>>(g, h->U[0], h->U[1], h->ctrl, 1);
+  for (int axis = 0; axis < 2; ++axis) {
+    const double* src = axis == 0 ? Wx : Wy;
+    const size_t n = axis == 0 ? n_wx(g) : n_wy(g);
+    void** W = axis == 0 ? h->Wx : h->Wy;
+    if (src) {
+      CK(cudaMemcpyAsync(h->staging, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      if (h->prec == GKS_FP64)
+        k_copy_W<double><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->staging, (double*)W[0], (double*)W[1], n, h->ctrl, 1);
+      else
+        k_copy_W<float><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->staging, (float*)W[0], (float*)W[1], n, h->ctrl, 1);
+    } else if (axis == 0) {
+      if (h->prec == GKS_FP64)
+        k_init_W<0, double><<<grid2(g.nx + 1, g.ny, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], (double*)W[0], (double*)W[1], h->ctrl);
+      else
+        k_init_W<0, float><<<grid2(g.nx + 1, g.ny, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], (float*)W[0], (float*)W[1], h->ctrl);
+    } else {
+      if (h->prec == GKS_FP64)
+        k_init_W<1, double><<<grid2(g.nx, g.ny + 1, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], (double*)W[0], (double*)W[1], h->ctrl);
+      else
+        k_init_W<1, float><<<grid2(g.nx, g.ny + 1, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], (float*)W[0], (float*)W[1], h->ctrl);
+    }
+  }
+  k_dtbound<<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], h->ctrl);
+  CK(cudaGetLastError());
+  st = read_ctrl(h);
+  if (st != GKS_OK) return st;
+  if (h->hctrl->status != GKS_OK) return fail(h, GKS_ENONPHYSICAL, "gks_set_state: state has rho <= 0 or p <= 0");
+  return GKS_OK;
+}
+
+gks_status gks_step(gks_handle* h, double CFL, double dt_max, double* dt_taken) {
+  if (!h) return GKS_EINVAL;
+  if (!(CFL > 0) || !(dt_max > 0)) return fail(h, GKS_EINVAL, "gks_step: CFL and dt_max must be > 0");
+  CK(cudaSetDevice(h->device));
+  gks_status st = launch_step(h, CFL, dt_max, INFINITY);
+  if (st != GKS_OK) return st;
+  st = read_ctrl(h);
+  if (st != GKS_OK) return st;
+  if (dt_taken) *dt_taken = h->hctrl->skip ? 0.0 : h->hctrl->dt;
+  if (h->hctrl->status != GKS_OK) return fail(h, (gks_status)h->hctrl->status, "step produced a non-physical state; state kept");
+  return GKS_OK;
+}
+
+gks_status gks_advance(gks_handle* h, int nsteps, double CFL, double t_end) {
+  if (!h) return GKS_EINVAL;
+  if (nsteps < 0 || !(CFL > 0)) return fail(h, GKS_EINVAL, "gks_advance: nsteps >= 0 and CFL > 0 required");
+  CK(cudaSetDevice(h->device));
+  if (!h->graph1 || h->graph_cfl != CFL || h->graph_tend != t_end) {
+    destroy_graphs(h);
+    gks_status st = capture(h, 1, CFL, t_end, &h->graph1);
+    if (st == GKS_OK) st = capture(h, 16, CFL, t_end, &h->graph16);
+    if (st != GKS_OK) { destroy_graphs(h); return st; }
+    h->graph_cfl = CFL;
+    h->graph_tend = t_end;
+  }
+  int left = nsteps;
+  while (left >= 16) { CK(cudaGraphLaunch(h->graph16, h->stream)); left -= 16; }
+  while (left > 0) { CK(cudaGraphLaunch(h->graph1, h->stream)); --left; }
+  return GKS_OK;
+}
+
+gks_status gks_sync(gks_handle* h, double* t, long long* steps) {
+  if (!h) return GKS_EINVAL;
+  CK(cudaSetDevice(h->device));
+  gks_status st = read_ctrl(h);
+  if (st != GKS_OK) return st;
+  if (t) *t = h->hctrl->t;
+  if (steps) *steps = h->hctrl->steps;
+  if (h->hctrl->status != GKS_OK) return fail(h, (gks_status)h->hctrl->status, "a queued step produced a non-physical state; state kept");
+  return GKS_OK;
+}
+
+gks_status gks_get_state_device(gks_handle* h, double* dU, double* dWx, double* dWy, double* t) {
+  if (!h) return GKS_EINVAL;
+  CK(cudaSetDevice(h->device));
+  gks_status st = h->prec == GKS_FP64 ? store_state<double>(h, dU, dWx, dWy) : store_state<float>(h, dU, dWx, dWy);
+  if (st != GKS_OK) return st;
+  st = read_ctrl(h);
+  if (st != GKS_OK) return st;
+  if (t) *t = h->hctrl->t;
+  if (h->hctrl->status != GKS_OK) return fail(h, (gks_status)h->hctrl->status, "a step produced a non-physical state; state kept");
+  return GKS_OK;
+}
+
+gks_status gks_get_state(gks_handle* h, double* U, double* Wx, double* Wy, double* t) {
+  if (!h) return GKS_EINVAL;
+  CK(cudaSetDevice(h->device));
+  const Geo& g = h->g;
+  struct { double* host; size_t n; int which; } parts[3] = {{U, n_u(g), 0}, {Wx, n_wx(g), 1}, {Wy, n_wy(g), 2}};
+  for (auto& p : parts) {
+    if (!p.host) continue;
+    gks_status st = h->prec == GKS_FP64
+                        ? store_state<double>(h, p.which == 0 ? h->staging : nullptr, p.which == 1 ? h->staging : nullptr,
+                                              p.which == 2 ? h->staging : nullptr)
+                        : store_state<float>(h, p.which == 0 ? h->staging : nullptr, p.which == 1 ? h->staging : nullptr,
+                                             p.which == 2 ? h->staging : nullptr);
+    if (st != GKS_OK) return st;
+    CK(cudaMemcpyAsync(p.host, h->staging, p.n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
+  gks_status st = read_ctrl(h);
+  if (st != GKS_OK) return st;
+  if (t) *t = h->hctrl->t;
+  if (h->hctrl->status != GKS_OK) return fail(h, (gks_status)h->hctrl->status, "a step produced a non-physical state; state kept");
+  return GKS_OK;
+}
+
+void gks_destroy(gks_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  destroy_graphs(h);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(h->U[b]);
+    cudaFree(h->Wx[b]);
+    cudaFree(h->Wy[b]);
+  }
+  cudaFree(h->coef);
+  cudaFree(h->Fx);
+  cudaFree(h->Fy);
+  cudaFree(h->ctrl);
+  cudaFree(h->staging);
+  if (h->hctrl) cudaFreeHost(h->hctrl);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+const char* gks_last_error(const gks_handle* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+int gks_launches_per_step(const gks_handle* h) {
+  (void)h;
+  return kLaunchesPerStep;
+}
+
+gks_status gks_debug_recon(gks_handle* h, double* coef) {
+  if (!h || !coef) return GKS_EINVAL;
+  CK(cudaSetDevice(h->device));
+  const Geo& g = h->g;
+  const dim3 b2(32, 8);
+  const int per = 2 * (g.nx + 2) + 2 * g.ny;
+  k_ghost<<<(per + 127) / 128, 128, 0, h->stream>>>(g, h->U[0], h->U[1], h->ctrl, 1);
+  if (h->prec == GKS_FP64) {
+    k_recon<double, double><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(
+        g, h->U[0], h->U[1], (const double*)h->Wx[0], (const double*)h->Wx[1], (const double*)h->Wy[0],
+        (const double*)h->Wy[1], (double*)h->coef, h->ctrl, 1);
+    k_coef_out<double><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], (const double*)h->coef, h->staging, h->ctrl);
+  } else {
+    k_recon<float, float><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(
+        g, h->U[0], h->U[1], (const float*)h->Wx[0], (const float*)h->Wx[1], (const float*)h->Wy[0],
+        (const float*)h->Wy[1], (float*)h->coef, h->ctrl, 1);
+    k_coef_out<float><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], (const float*)h->coef, h->staging, h->ctrl);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(coef, h->staging, (size_t)24 * g.nx * g.ny * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return GKS_OK;
+}
+
+gks_status gks_debug_flux(gks_handle* h, double dt, double* Fx, double* Fy, double* Wxn, double* Wyn) {
+  if (!h || !(dt > 0)) return fail(h, GKS_EINVAL, "gks_debug_flux: dt > 0 required");
+  CK(cudaSetDevice(h->device));
+  const Geo& g = h->g;
+  k_set_dt<<<1, 1, 0, h->stream>>>(h->ctrl, dt);
+  gks_status st = h->prec == GKS_FP64 ? launch_step_kernels<double, double>(h, 0, 0, 0, false, false, 1)
+                                      : launch_step_kernels<float, float>(h, 0, 0, 0, false, false, 1);
+  if (st != GKS_OK) return st;
+  st = read_ctrl(h);
+  if (st != GKS_OK) return st;
+  const int par = (int)(h->hctrl->steps & 1) ^ 1;  // new values were written to the other buffer
+  const size_t nfx = (size_t)4 * g.ny * (g.nx + 1), nfy = (size_t)4 * (g.ny + 1) * g.nx;
+  struct { void* src; double* dst; size_t n; } parts[4] = {
+      {h->Fx, Fx, nfx}, {h->Fy, Fy, nfy}, {h->Wx[par], Wxn, n_wx(g)}, {h->Wy[par], Wyn, n_wy(g)}};
+  for (auto& p : parts) {
+    if (!p.dst) continue;
+    if (h->prec == GKS_FP64)
+      k_to_double<double><<<(unsigned)((p.n + 255) / 256), 256, 0, h->stream>>>((const double*)p.src, h->staging, p.n);
+    else
+      k_to_double<float><<<(unsigned)((p.n + 255) / 256), 256, 0, h->stream>>>((const float*)p.src, h->staging, p.n);
+    CK(cudaMemcpyAsync(p.dst, h->staging, p.n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return GKS_OK;
+}
+
+}  // extern "C"

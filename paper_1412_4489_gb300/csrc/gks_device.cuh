@@ -1,0 +1,632 @@
+// Device arithmetic of the compact third-order gas-kinetic scheme
+// (Pan & Xu, arXiv:1412.4489), templated on the compute type R (double or float).
+//
+//   Section 2.1  Maxwellian moments: full space and the half spaces u > 0, u < 0
+//   Section 2.2  closed-form solve of <a> = r, the nine coefficient systems,
+//                time weights of Eq. dis1 / Eq. dis2 integrated over [0, dt]
+//                and at t = dt, assembly of the flux and of Eq. point
+//   Section 3.2  compact reconstruction of one cell
+//   Section 3.3  equilibrium polynomial across a face
+//   Section 4    collision time
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace gks {
+
+template <class R> struct Prec;
+template <> struct Prec<double> {
+  static constexpr double series_below = 0.5;  // x = dt/tau below which series are used
+  static constexpr int series_terms = 22;
+};
+template <> struct Prec<float> {
+  static constexpr float series_below = 2.0f;
+  static constexpr int series_terms = 24;
+};
+
+__device__ __forceinline__ double d_exp(double x) { return exp(x); }
+__device__ __forceinline__ float d_exp(float x) { return __expf(x); }
+__device__ __forceinline__ double d_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float d_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double d_erfc(double x) { return erfc(x); }
+__device__ __forceinline__ float d_erfc(float x) { return erfcf(x); }
+__device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double d_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float d_rsqrt(float x) { return rsqrtf(x); }
+
+template <class R> __device__ __forceinline__ R sq(R a) { return a * a; }
+
+// ---------------------------------------------------------------------------
+// Section 2.1: moments of g = rho (lam/pi)^((K+2)/2) exp(-lam((u-U)^2+(v-V)^2+xi^2)),
+// normalised by rho.  NU u-moments, NV v-moments.
+// ---------------------------------------------------------------------------
+template <class R, int NU, int NV>
+struct Moments {
+  R u[NU];
+  R v[NV];
+  R xi2, xi4;
+};
+
+// kind: 0 full space, +1 over u > 0, -1 over u < 0
+template <class R, int NU, int NV>
+__device__ __forceinline__ void moments(R U, R V, R lam, R K, int kind, Moments<R, NU, NV>& m) {
+  const R var = R(0.5) / lam;
+  if (kind == 0) {
+    m.u[0] = R(1);
+    m.u[1] = U;
+  } else {
+    const R s = d_sqrt(lam);
+    const R h = R(0.5) * d_erfc(-R(kind) * s * U);
+    // boundary term of the integration by parts at u = 0
+    const R b = d_exp(-lam * U * U) * R(0.28209479177387814) * d_rsqrt(lam);  // 1/(2 sqrt(pi lam))
+    m.u[0] = h;
+    m.u[1] = U * h + R(kind) * b;
+  }
+#pragma unroll
+  for (int n = 2; n < NU; ++n) m.u[n] = U * m.u[n - 1] + R(n - 1) * var * m.u[n - 2];
+  m.v[0] = R(1);
+  m.v[1] = V;
+#pragma unroll
+  for (int n = 2; n < NV; ++n) m.v[n] = V * m.v[n - 1] + R(n - 1) * var * m.v[n - 2];
+  m.xi2 = K * var;
+  m.xi4 = K * (K + R(2)) * var * var;
+}
+
+// <u^A v^B psi> and <xi^2 u^A v^B psi>, psi = (1, u, v, (u^2+v^2+xi^2)/2)
+template <int A, int B, class R, int NU, int NV>
+__device__ __forceinline__ void psi_mom(const Moments<R, NU, NV>& m, R o[4]) {
+  static_assert(A + 2 < NU && B + 2 < NV, "moment table too short");
+  const R ab = m.u[A] * m.v[B];
+  o[0] = ab;
+  o[1] = m.u[A + 1] * m.v[B];
+  o[2] = m.u[A] * m.v[B + 1];
+  o[3] = R(0.5) * (m.u[A + 2] * m.v[B] + m.u[A] * m.v[B + 2] + ab * m.xi2);
+}
+
+// <X u^A v^B psi> for X = X0 + X1 u + X2 v + X3 (u^2+v^2+xi^2)/2
+template <int A, int B, class R, int NU, int NV>
+__device__ __forceinline__ void coef_mom(const R X[4], const Moments<R, NU, NV>& m, R o[4]) {
+  R p0[4], p1[4], p2[4], pa[4], pb[4];
+  psi_mom<A, B>(m, p0);
+  psi_mom<A + 1, B>(m, p1);
+  psi_mom<A, B + 1>(m, p2);
+  psi_mom<A + 2, B>(m, pa);
+  psi_mom<A, B + 2>(m, pb);
+  const R ab = m.u[A] * m.v[B];
+  R pc[4];
+  pc[0] = m.xi2 * ab;
+  pc[1] = m.xi2 * m.u[A + 1] * m.v[B];
+  pc[2] = m.xi2 * m.u[A] * m.v[B + 1];
+  pc[3] = R(0.5) * (m.xi2 * (m.u[A + 2] * m.v[B] + m.u[A] * m.v[B + 2]) + m.xi4 * ab);
+  const R h = R(0.5) * X[3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o[k] = X[0] * p0[k] + X[1] * p1[k] + X[2] * p2[k] + h * (pa[k] + pb[k] + pc[k]);
+}
+
+// ---------------------------------------------------------------------------
+// Section 2.2: <a> = rho r for a expanded in psi has a closed-form solution
+// (the moment matrix of a Maxwellian is block structured about (U, V)).
+// N = K + 2.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void solve(R U, R V, R lam, R N, const R r[4], R x[4]) {
+  const R q2 = U * U + V * V;
+  const R x4 = R(4) * lam * lam / N *
+               (R(2) * r[3] - R(2) * U * r[1] - R(2) * V * r[2] + (q2 - N / (R(2) * lam)) * r[0]);
+  const R x3 = R(2) * lam * (r[2] - V * r[0]) - V * x4;
+  const R x2 = R(2) * lam * (r[1] - U * r[0]) - U * x4;
+  x[0] = r[0] - U * x2 - V * x3 - x4 * (R(0.5) * q2 + N / (R(4) * lam));
+  x[1] = x2;
+  x[2] = x3;
+  x[3] = x4;
+}
+
+// ---------------------------------------------------------------------------
+// Time weights.  With x = dt/tau and e = exp(-x), the flux needs the integrals
+// over [0, dt] of C_1..C_8, C_7 t and C_7 t^2; Eq. point needs their values at
+// t = dt.  Several are differences of nearly equal terms when x is small; there
+// they are summed from their Taylor series in x.
+// ---------------------------------------------------------------------------
+template <class R>
+struct TimeW {
+  R I[11];  // integrals, index 1..8 = C_1..C_8, 9 = C_7 t, 10 = C_7 t^2
+  R E[11];  // values at t = dt
+};
+
+template <class R>
+__device__ __forceinline__ void time_weights(R T, R tau, TimeW<R>& w) {
+  const R x = tau > R(0) ? T / tau : R(INFINITY);
+  const R e = tau > R(0) ? d_exp(-x) : R(0);
+  const R om = tau > R(0) ? -d_expm1(-x) : R(1);  // 1 - e
+  R f1, f2, f3, f4, f5, f6;  // see below
+  if (x < Prec<R>::series_below) {
+    // t_n = (-x)^n / n!:  f1 = x-1+e = sum_{n>=2} t_n;  f2 = 1-(1+x)e = sum (n-1) t_n;
+    // f3 = 2-2e-x-xe = sum (n-2) t_n;  f4 = x^2/2-x+1-e = -sum_{n>=3} t_n;
+    // f5 = 4-(x+2)^2 e = -sum (n-1)(n-4) t_n;  f6 = 2-(x^2+2x+2) e = -sum_{n>=3} (n-1)(n-2) t_n
+    R t = R(0.5) * x * x;
+    f1 = t; f2 = t; f3 = R(0); f4 = R(0); f5 = R(2) * t; f6 = R(0);
+#pragma unroll
+    for (int n = 3; n < Prec<R>::series_terms; ++n) {
+      t *= -x / R(n);
+      f1 += t;
+      f2 += R(n - 1) * t;
+      f3 += R(n - 2) * t;
+      f4 -= t;
+      f5 -= R((n - 1) * (n - 4)) * t;
+      f6 -= R((n - 1) * (n - 2)) * t;
+    }
+    const R t2 = tau * tau, t3 = t2 * tau;
+    w.I[1] = tau * f1;
+    w.I[2] = t2 * f3;
+    w.I[3] = t2 * f4;
+    w.I[4] = -t3 * f5;
+    w.I[9] = t2 * f2;
+    w.I[10] = t3 * f6;
+    w.E[2] = -tau * f2;
+    w.E[3] = tau * f1;
+  } else {
+    const R t2 = tau * tau;
+    w.I[1] = T - tau * om;
+    w.I[2] = R(2) * t2 * om - tau * T * (R(1) + e);
+    w.I[3] = R(0.5) * T * T - tau * T + t2 * om;
+    w.I[4] = -R(4) * t2 * tau + tau * sq(T + R(2) * tau) * e;
+    w.I[9] = t2 - tau * (tau + T) * e;
+    w.I[10] = R(2) * t2 * tau - tau * (T * T + R(2) * T * tau + R(2) * t2) * e;
+    w.E[2] = (T + tau) * e - tau;
+    w.E[3] = T - tau + tau * e;
+  }
+  w.I[5] = T * T * T / R(3) - tau * T * T;
+  w.I[6] = -tau * (R(0.5) * T * T + w.I[9]);
+  w.I[7] = tau * om;
+  w.I[8] = -w.I[9];
+  w.E[1] = om;
+  w.E[4] = -(T * T + R(2) * T * tau) * e;
+  w.E[5] = T * T - R(2) * T * tau;
+  w.E[6] = -T * tau * (R(1) + e);
+  w.E[7] = e;
+  w.E[8] = -T * e;
+  w.E[9] = T * e;
+  w.E[10] = T * T * e;
+}
+
+// ---------------------------------------------------------------------------
+// The nine coefficients of one equilibrium state (system after Eq. dis3).
+// The composites (a1^2+d11), (a1 a2+d12), (a2^2+d22), (A a1+b1), (A a2+b2),
+// (A^2+B) are single unknowns expanded in psi: Axx, Axy, Ayy, Atx, Aty, Att.
+// d[] = (dn, dt, dnn, dnt, dtt) of the conservative variables.
+// ---------------------------------------------------------------------------
+template <class R>
+struct Coefs {
+  R a1[4], a2[4], Axx[4], Axy[4], Ayy[4], A[4], Atx[4], Aty[4], Att[4];
+};
+
+template <class R, int NU, int NV>
+__device__ __forceinline__ void coef_systems(const Moments<R, NU, NV>& m, R rho, R U, R V, R lam, R N,
+                                             const R d[5][4], bool time_terms, bool second_time,
+                                             Coefs<R>& c) {
+  const R ir = R(1) / rho;
+  R r[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r[k] = d[0][k] * ir;
+  solve(U, V, lam, N, r, c.a1);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r[k] = d[1][k] * ir;
+  solve(U, V, lam, N, r, c.a2);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r[k] = d[2][k] * ir;
+  solve(U, V, lam, N, r, c.Axx);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r[k] = d[3][k] * ir;
+  solve(U, V, lam, N, r, c.Axy);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r[k] = d[4][k] * ir;
+  solve(U, V, lam, N, r, c.Ayy);
+  if (!time_terms) return;
+  R p[4], q[4];
+  coef_mom<1, 0>(c.a1, m, p);  // <A + a1 u + a2 v> = 0
+  coef_mom<0, 1>(c.a2, m, q);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r[k] = -(p[k] + q[k]);
+  solve(U, V, lam, N, r, c.A);
+  coef_mom<1, 0>(c.Axx, m, p);  // <Axx u + Axy v + Atx> = 0
+  coef_mom<0, 1>(c.Axy, m, q);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r[k] = -(p[k] + q[k]);
+  solve(U, V, lam, N, r, c.Atx);
+  coef_mom<1, 0>(c.Axy, m, p);  // <Axy u + Ayy v + Aty> = 0
+  coef_mom<0, 1>(c.Ayy, m, q);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r[k] = -(p[k] + q[k]);
+  solve(U, V, lam, N, r, c.Aty);
+  if (!second_time) return;
+  coef_mom<1, 0>(c.Atx, m, p);  // <Atx u + Aty v + Att> = 0
+  coef_mom<0, 1>(c.Aty, m, q);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r[k] = -(p[k] + q[k]);
+  solve(U, V, lam, N, r, c.Att);
+}
+
+// The interface distribution grouped by velocity monomial: f = sum over
+// m in {1, u, v, u^2, u v, v^2} of X_m(psi) m g, plus y X'_m for the part
+// linear along the face.  accumulate() adds
+//   flux   += rho sum <X_m m u psi>       (time-integrated weights)
+//   point0 += rho sum <X_m m psi>          (weights at t = dt)
+//   point1 += rho sum <X'_m m psi>         (weights at t = dt, y-linear part)
+//   mean   += rho sum <X_m m psi>          (time-integrated weights; heat flux)
+template <class R>
+struct Groups {
+  R X1[4], Xu[4], Xv[4], Xuu[4], Xuv[4], Xvv[4];
+};
+
+template <class R, int NU, int NV>
+__device__ __forceinline__ void add_flux(const Groups<R>& g, const Moments<R, NU, NV>& m, R rho, R out[4]) {
+  R t[4], s[4];
+  coef_mom<1, 0>(g.X1, m, s);
+  coef_mom<2, 0>(g.Xu, m, t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s[k] += t[k];
+  coef_mom<1, 1>(g.Xv, m, t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s[k] += t[k];
+  coef_mom<3, 0>(g.Xuu, m, t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s[k] += t[k];
+  coef_mom<2, 1>(g.Xuv, m, t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s[k] += t[k];
+  coef_mom<1, 2>(g.Xvv, m, t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out[k] += rho * (s[k] + t[k]);
+}
+
+template <class R, int NU, int NV>
+__device__ __forceinline__ void add_point(const Groups<R>& g, const Moments<R, NU, NV>& m, R rho, R out[4]) {
+  R t[4], s[4];
+  coef_mom<0, 0>(g.X1, m, s);
+  coef_mom<1, 0>(g.Xu, m, t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s[k] += t[k];
+  coef_mom<0, 1>(g.Xv, m, t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s[k] += t[k];
+  coef_mom<2, 0>(g.Xuu, m, t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s[k] += t[k];
+  coef_mom<1, 1>(g.Xuv, m, t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s[k] += t[k];
+  coef_mom<0, 2>(g.Xvv, m, t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out[k] += rho * (s[k] + t[k]);
+}
+
+template <class R, int NU, int NV>
+__device__ __forceinline__ void add_point_linear(const R Y1[4], const R Yu[4], const R Yv[4],
+                                                 const Moments<R, NU, NV>& m, R rho, R out[4]) {
+  R s[4], t[4];
+  coef_mom<0, 0>(Y1, m, s);
+  coef_mom<1, 0>(Yu, m, t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s[k] += t[k];
+  coef_mom<0, 1>(Yv, m, t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out[k] += rho * (s[k] + t[k]);
+}
+
+// Eq. dis1 grouped: weights W = I (flux, mean) or E (point); y2 = dtan^2/12 is both
+// the face mean of y^2 and y^2 at the Gauss points.
+template <class R>
+__device__ __forceinline__ void hydro_groups(const Coefs<R>& c, const R* W, R y2, Groups<R>& g) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    g.X1[k] = W[3] * c.A[k] + R(0.5) * W[5] * c.Att[k] + R(0.5) * y2 * W[1] * c.Ayy[k];
+    g.Xu[k] = W[2] * c.a1[k] + W[6] * c.Atx[k];
+    g.Xv[k] = W[2] * c.a2[k] + W[6] * c.Aty[k];
+    g.Xuu[k] = R(0.5) * W[4] * c.Axx[k];
+    g.Xuv[k] = W[4] * c.Axy[k];
+    g.Xvv[k] = R(0.5) * W[4] * c.Ayy[k];
+  }
+  g.X1[0] += W[1];
+}
+
+// Eq. dis2 grouped for one side; tn = tau for the Navier-Stokes f_G, 0 for Euler
+template <class R>
+__device__ __forceinline__ void kinetic_groups(const Coefs<R>& c, const R* W, R y2, R tn, Groups<R>& g) {
+  const R w78 = W[8] - tn * W[7];
+  const R wq = R(0.5) * W[10] - tn * W[8];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    g.X1[k] = -tn * W[7] * c.A[k] + R(0.5) * y2 * W[7] * c.Ayy[k];
+    g.Xu[k] = w78 * c.a1[k] - tn * W[8] * c.Atx[k];
+    g.Xv[k] = w78 * c.a2[k] - tn * W[8] * c.Aty[k];
+    g.Xuu[k] = wq * c.Axx[k];
+    g.Xuv[k] = R(2) * wq * c.Axy[k];
+    g.Xvv[k] = wq * c.Ayy[k];
+  }
+  g.X1[0] += W[7];
+}
+
+// ---------------------------------------------------------------------------
+// Face states in the face frame: value and (dn, dt, dnn, dnt, dtt)
+// ---------------------------------------------------------------------------
+template <class R>
+struct FaceState {
+  R w[6][4];
+};
+
+template <class R>
+__device__ __forceinline__ void prim(const R w[4], R gm1, R& rho, R& U, R& V, R& p) {
+  rho = w[0];
+  const R ir = R(1) / rho;
+  U = w[1] * ir;
+  V = w[2] * ir;
+  p = gm1 * (w[3] - R(0.5) * rho * (U * U + V * V));
+}
+
+struct FaceParams {
+  double gamma, mu, Pr, tau_eps, tau_C;
+  double dn, dtan;  // cell size normal to and along the face
+};
+
+// Wall images G(n, t) = Phi(P(-n, t)) of the inside face state (face frame).
+// kind 2: slip wall (normal momentum negated).  kind 3: isothermal no-slip with
+// tangential wall velocity uwt and wall temperature Tw: rho' = rho,
+// m' = 2 rho u_w - m, rho E' = 2 rho |u_w|^2 - 2 u_w.m + |m|^2/rho + 2 rho Tw/(gamma-1) - rho E.
+template <class R>
+__device__ __forceinline__ void wall_image(int kind, R gamma, R uwt, R Tw, const FaceState<R>& in, FaceState<R>& out) {
+  if (kind == 2) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      const R s = (d == 1 || d == 4) ? R(-1) : R(1);  // odd derivatives in n flip
+      out.w[d][0] = s * in.w[d][0];
+      out.w[d][1] = -s * in.w[d][1];
+      out.w[d][2] = s * in.w[d][2];
+      out.w[d][3] = s * in.w[d][3];
+    }
+    return;
+  }
+  const R rho = in.w[0][0], mn = in.w[0][1], mt = in.w[0][2];
+  const R ir = R(1) / rho;
+  const R m2 = mn * mn + mt * mt;
+  const R cT = R(2) * Tw / (gamma - R(1));
+  // value
+  out.w[0][0] = rho;
+  out.w[0][1] = -mn;
+  out.w[0][2] = R(2) * rho * uwt - mt;
+  out.w[0][3] = R(2) * rho * uwt * uwt - R(2) * uwt * mt + m2 * ir + rho * cT - in.w[0][3];
+  // Jacobian rows applied to a derivative vector a
+  auto lin = [&](const R a[4], R o[4]) {
+    o[0] = a[0];
+    o[1] = -a[1];
+    o[2] = R(2) * uwt * a[0] - a[2];
+    o[3] = (R(2) * uwt * uwt - m2 * ir * ir + cT) * a[0] + R(2) * mn * ir * a[1] +
+           (R(2) * mt * ir - R(2) * uwt) * a[2] - a[3];
+  };
+  // second derivative of |m|^2/rho along a, b
+  auto hess = [&](const R a[4], const R b[4]) {
+    const R ma = mn * a[1] + mt * a[2], mb = mn * b[1] + mt * b[2];
+    return R(2) * m2 * ir * ir * ir * a[0] * b[0] - R(2) * ir * ir * (ma * b[0] + mb * a[0]) +
+           R(2) * ir * (a[1] * b[1] + a[2] * b[2]);
+  };
+  R o[4];
+  lin(in.w[1], o);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out.w[1][k] = -o[k];
+  lin(in.w[2], o);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out.w[2][k] = o[k];
+  lin(in.w[3], o);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out.w[3][k] = o[k];
+  out.w[3][3] += hess(in.w[1], in.w[1]);
+  lin(in.w[4], o);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out.w[4][k] = -o[k];
+  out.w[4][3] -= hess(in.w[1], in.w[2]);
+  lin(in.w[5], o);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out.w[5][k] = o[k];
+  out.w[5][3] += hess(in.w[2], in.w[2]);
+}
+
+// ---------------------------------------------------------------------------
+// Section 2.2 at one face centre.  L, R: the two sides; avg[m][k]: the six
+// cell averages of Section 3.3 (m = 0 left, 1 right; k = tangential -1, 0, 1).
+// Outputs the time-integrated face-mean flux and the point values at the two
+// Gauss points (tangential -/+ sqrt(3)/6 dtan) at t = dt.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void face_evolution(const FaceParams& P, const FaceState<R>& L,
+                                               const FaceState<R>& Rs, const R avg[2][3][4], R dt,
+                                               R F[4], R Wm[4], R Wp[4]) {
+  const R gamma = R(P.gamma), gm1 = gamma - R(1);
+  const R K = (R(4) - R(2) * gamma) / gm1;
+  const R N = K + R(2);
+  const R dn = R(P.dn), dtan = R(P.dtan);
+  const R y2 = dtan * dtan / R(12);
+  const bool ns = P.mu > 0.0;
+
+  R rl, ul, vl, pl, rr, ur, vr, pr;
+  prim(L.w[0], gm1, rl, ul, vl, pl);
+  prim(Rs.w[0], gm1, rr, ur, vr, pr);
+  const R laml = R(0.5) * rl / pl, lamr = R(0.5) * rr / pr;
+
+  // Eq. compatibility2: U0 = rho_l <psi>_{u>0} + rho_r <psi>_{u<0}
+  R U0[4];
+  {
+    Moments<R, 4, 3> ml, mr;
+    moments(ul, vl, laml, K, +1, ml);
+    moments(ur, vr, lamr, K, -1, mr);
+    R a[4], b[4];
+    psi_mom<0, 0>(ml, a);
+    psi_mom<0, 0>(mr, b);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) U0[k] = rl * a[k] + rr * b[k];
+  }
+  R r0, u0, v0, p0;
+  prim(U0, gm1, r0, u0, v0, p0);
+  const R lam0 = R(0.5) * r0 / p0;
+
+  // Section 4: collision time
+  const R jump = fabs((pl - pr) / (pl + pr)) * dt;
+  const R tau = ns ? R(P.mu) / p0 + jump : R(P.tau_eps) * dt + R(P.tau_C) * jump;
+  const R tn = ns ? tau : R(0);
+
+  TimeW<R> tw;
+  time_weights(dt, tau, tw);
+
+  R Fl[4] = {0, 0, 0, 0}, P0[4] = {0, 0, 0, 0}, P1[4] = {0, 0, 0, 0}, Mn[4] = {0, 0, 0, 0};
+  const bool prandtl = P.Pr != 1.0;
+
+  // ---- equilibrium part, Eq. dis1, with g0 and the polynomial of Section 3.3 ----
+  {
+    R d[5][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const R um = avg[0][0][k], uc = avg[0][1][k], up = avg[0][2][k];
+      const R wm = avg[1][0][k], wc = avg[1][1][k], wp = avg[1][2][k];
+      d[0][k] = ((wp - up) + R(2) * (wc - uc) + (wm - um)) / (R(4) * dn);                // b2
+      d[1][k] = (wp - wm + up - um) / (R(4) * dtan);                                       // b3
+      d[2][k] = (R(26) * (wc + uc) - (wp + up + wm + um) - R(48) * U0[k]) / (R(8) * dn * dn);  // b4
+      d[3][k] = (wp - up - wm + um) / (R(2) * dn * dtan);                                  // b6
+      d[4][k] = (wp - R(2) * wc + wm + up - R(2) * uc + um) / (R(2) * dtan * dtan);         // b5
+    }
+    Moments<R, 8, 7> m;
+    moments(u0, v0, lam0, K, 0, m);
+    Coefs<R> c;
+    coef_systems(m, r0, u0, v0, lam0, N, d, true, true, c);
+    Groups<R> g;
+    hydro_groups(c, tw.I, y2, g);
+    add_flux(g, m, r0, Fl);
+    if (prandtl) add_point(g, m, r0, Mn);
+    hydro_groups(c, tw.E, y2, g);
+    add_point(g, m, r0, P0);
+    R Y1[4], Yu[4], Yv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Y1[k] = tw.E[1] * c.a2[k] + tw.E[3] * c.Aty[k];
+      Yu[k] = tw.E[2] * c.Axy[k];
+      Yv[k] = tw.E[2] * c.Ayy[k];
+    }
+    add_point_linear(Y1, Yu, Yv, m, r0, P1);
+  }
+
+  // ---- kinetic part, Eq. dis2, for both sides ----
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    const FaceState<R>& S = side == 0 ? L : Rs;
+    const R rho = side == 0 ? rl : rr, U = side == 0 ? ul : ur, V = side == 0 ? vl : vr;
+    const R lam = side == 0 ? laml : lamr;
+    R d[5][4];
+#pragma unroll
+    for (int s = 0; s < 5; ++s)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) d[s][k] = S.w[s + 1][k];
+    Coefs<R> c;
+    {
+      Moments<R, 6, 6> mf;  // full-space moments fix the coefficients of g_k
+      moments(U, V, lam, K, 0, mf);
+      coef_systems(mf, rho, U, V, lam, N, d, ns, false, c);
+    }
+    if (!ns) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) c.A[k] = c.Atx[k] = c.Aty[k] = R(0);
+    }
+    Moments<R, 8, 7> mh;
+    moments(U, V, lam, K, side == 0 ? +1 : -1, mh);
+    Groups<R> g;
+    kinetic_groups(c, tw.I, y2, tn, g);
+    add_flux(g, mh, rho, Fl);
+    if (prandtl) add_point(g, mh, rho, Mn);
+    kinetic_groups(c, tw.E, y2, tn, g);
+    add_point(g, mh, rho, P0);
+    R Y1[4], Yu[4], Yv[4];
+    const R wy = -tn * tw.E[7] - tw.E[9];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Y1[k] = tw.E[7] * (c.a2[k] - tn * c.Aty[k]);
+      Yu[k] = wy * c.Axy[k];
+      Yv[k] = wy * c.Ayy[k];
+    }
+    add_point_linear(Y1, Yu, Yv, mh, rho, P1);
+  }
+
+  // Prandtl-number fix: energy flux += (1/Pr - 1) q, q the time-integrated
+  // face-mean heat flux (1/2) int (u-U0)((u-U0)^2+(v-V0)^2+xi^2) f, written with the
+  // flux and the time-integrated conservative moments.
+  if (prandtl) {
+    const R q2 = u0 * u0 + v0 * v0;
+    const R q = Fl[3] - u0 * Fl[1] - v0 * Fl[2] + (R(0.5) * q2 + u0 * u0) * Fl[0] - u0 * Mn[3] +
+                u0 * v0 * Mn[2] - R(0.5) * u0 * q2 * Mn[0];
+    Fl[3] += (R(1) / R(P.Pr) - R(1)) * q;
+  }
+  const R yg = R(0.28867513459481287) * dtan;  // sqrt(3)/6
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    F[k] = Fl[k];
+    Wm[k] = P0[k] - yg * P1[k];
+    Wp[k] = P0[k] + yg * P1[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Section 3.2: compact reconstruction of one variable of one cell.
+// c: cell average; e, w, n, s: neighbour averages; em/ep: east-face Gauss
+// values (y-/y+), wm/wp west face, nm/np north face (x-/x+), sm/sp south face.
+// Output a[0..4] = (a2, a3, a4, a5, a6) of
+//   U(x,y) = c + a2 x + a3 y + a4 (x^2-dx^2/12)/2 + a5 (y^2-dy^2/12)/2 + a6 x y.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ R minmod(R a, R b) {
+  return a * b > R(0) ? (fabs(a) < fabs(b) ? a : b) : R(0);
+}
+
+template <class R>
+__device__ __forceinline__ void recon_var(R c, R e, R w, R n, R s, R em, R ep, R wm, R wp, R nm, R np, R sm,
+                                          R sp, R dx, R dy, R weps, R wC, R a[5]) {
+  const R idx = R(1) / dx, idy = R(1) / dy;
+  const R idx2 = idx * idx, idy2 = idy * idy;
+  // one-sided stencils: face Gauss mean S and neighbour average (Eq. over-sys)
+  const R Se = R(0.5) * (em + ep), Sw = R(0.5) * (wm + wp);
+  const R Sn = R(0.5) * (nm + np), Ss = R(0.5) * (sm + sp);
+  const R a4 = minmod(R(3) * (c + w - R(2) * Sw) * idx2, R(3) * (c + e - R(2) * Se) * idx2);
+  const R a2 = minmod(-R(2) * (Sw - c) * idx + a4 * dx / R(6), R(2) * (Se - c) * idx - a4 * dx / R(6));
+  const R a5 = minmod(R(3) * (c + s - R(2) * Ss) * idy2, R(3) * (c + n - R(2) * Sn) * idy2);
+  const R a3 = minmod(-R(2) * (Ss - c) * idy + a5 * dy / R(6), R(2) * (Sn - c) * idy - a5 * dy / R(6));
+  // cross derivative of the four one-sided stencils with limited a2, a3:
+  // sx (sqrt3 Dx/(dx dy) - a3/dx) + sy (sqrt3 Dy/(dx dy) - a2/dy), smallest magnitude
+  const R r3 = R(1.7320508075688772) * idx * idy;
+  const R xe = r3 * (ep - em) - a3 * idx, xw = r3 * (wp - wm) - a3 * idx;
+  const R yn = r3 * (np - nm) - a2 * idy, ys = r3 * (sp - sm) - a2 * idy;
+  // magnitudes within a relative 1e-8 of the current choice are ties (piecewise
+  // constant data give exact ties of opposite sign); the earlier stencil is kept
+  const R keep = R(1) - R(1e-8);
+  R a6 = xe + yn;        // (+, +)
+  R cand = -xw + yn;     // (-, +)
+  if (fabs(cand) < fabs(a6) * keep) a6 = cand;
+  cand = -xw - ys;       // (-, -)
+  if (fabs(cand) < fabs(a6) * keep) a6 = cand;
+  cand = xe - ys;        // (+, -)
+  if (fabs(cand) < fabs(a6) * keep) a6 = cand;
+  // central stencil
+  const R c2 = R(0.5) * (e - w) * idx, c4 = (e - R(2) * c + w) * idx2;
+  const R c3 = R(0.5) * (n - s) * idy, c5 = (n - R(2) * c + s) * idy2;
+  const R c6 = R(0.5) * r3 * ((ep - em) - (wp - wm) + (np - nm) - (sp - sm));
+  // Eq. average: alpha = 1/(eps + I)^2, I(U1) = C dx dy
+  const R dx2 = dx * dx, dy2 = dy * dy;
+  const R I2 = dx2 * (c2 * c2 + (c4 * c4 * dx2 + c6 * c6 * dy2) / R(12)) +
+               dy2 * (c3 * c3 + (c5 * c5 * dy2 + c6 * c6 * dx2) / R(12)) + dx2 * dx2 * c4 * c4 +
+               dx2 * dy2 * c6 * c6 + dy2 * dy2 * c5 * c5;
+  const R I1 = wC * dx * dy;
+  const R b1 = weps + I1, b2 = weps + I2;
+  // w1 = (1/b1^2) / (1/b1^2 + 1/b2^2) = b2^2 / (b1^2 + b2^2)
+  const R w1 = b2 * b2 / (b1 * b1 + b2 * b2), w2 = R(1) - w1;
+  a[0] = w1 * a2 + w2 * c2;
+  a[1] = w1 * a3 + w2 * c3;
+  a[2] = w1 * a4 + w2 * c4;
+  a[3] = w1 * a5 + w2 * c5;
+  a[4] = w1 * a6 + w2 * c6;
+}
+
+}  // namespace gks

@@ -1,0 +1,230 @@
+"""ctypes binding of ``libgks.so`` (the C ABI declared in ``include/gks.h``).
+
+Argument marshalling only: every step of the scheme runs in the CUDA kernels of the
+library.  Functions keep the C names (``gks_create``, ``gks_set_state``, ``gks_step``,
+``gks_advance``, ``gks_get_state``, ``gks_destroy`` ...); ``Solver`` wraps one handle.
+Host arrays are float64 numpy arrays in the layouts of ``gks.h``; device arrays are
+float64 torch CUDA tensors.  Loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GKS_OK, GKS_EINVAL, GKS_ENOMEM, GKS_ECUDA, GKS_ENONPHYSICAL, GKS_ETIMEOUT, GKS_EUNSUPPORTED = range(7)
+GKS_BC_PERIODIC, GKS_BC_OUTFLOW, GKS_BC_SLIPWALL, GKS_BC_NOSLIP_ISOTHERMAL = range(4)
+GKS_FP64, GKS_FP32_BULK = 0, 1
+STATUS_NAMES = ["GKS_OK", "GKS_EINVAL", "GKS_ENOMEM", "GKS_ECUDA", "GKS_ENONPHYSICAL", "GKS_ETIMEOUT",
+                "GKS_EUNSUPPORTED"]
+
+
+class gks_bc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("u_wall", ctypes.c_double), ("v_wall", ctypes.c_double),
+                ("T_wall", ctypes.c_double)]
+
+
+class gks_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("weno_eps", ctypes.c_double), ("weno_C", ctypes.c_double),
+                ("tau_eps", ctypes.c_double), ("tau_C", ctypes.c_double), ("viscous_dt", ctypes.c_int)]
+
+
+class GKSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def load(path: str | None = None):
+    """Loads (building first if needed) the CUDA library; raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        _build.build()
+    L = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    D = ctypes.c_double
+    L.gks_default_options.argtypes = [ctypes.POINTER(gks_options)]
+    L.gks_default_options.restype = None
+    L.gks_create.argtypes = [ctypes.c_int, ctypes.c_int, D, D, D, D, D, ctypes.POINTER(gks_bc),
+                             ctypes.POINTER(gks_options), ctypes.c_void_p, ctypes.POINTER(H)]
+    L.gks_set_state.argtypes = [H, _dp, _dp, _dp, D]
+    L.gks_set_state_device.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, D]
+    L.gks_step.argtypes = [H, D, D, _dp]
+    L.gks_advance.argtypes = [H, ctypes.c_int, D, D]
+    L.gks_sync.argtypes = [H, _dp, ctypes.POINTER(ctypes.c_longlong)]
+    L.gks_get_state.argtypes = [H, _dp, _dp, _dp, _dp]
+    L.gks_get_state_device.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _dp]
+    L.gks_destroy.argtypes = [H]
+    L.gks_destroy.restype = None
+    L.gks_last_error.argtypes = [H]
+    L.gks_last_error.restype = ctypes.c_char_p
+    L.gks_launches_per_step.argtypes = [H]
+    L.gks_debug_recon.argtypes = [H, _dp]
+    L.gks_debug_flux.argtypes = [H, D, _dp, _dp, _dp, _dp]
+    for name in ("gks_create", "gks_set_state", "gks_set_state_device", "gks_step", "gks_advance", "gks_sync",
+                 "gks_get_state", "gks_get_state_device", "gks_debug_recon", "gks_debug_flux",
+                 "gks_launches_per_step"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_dp)
+
+
+def _dev(t):
+    if t is None:
+        return None
+    assert t.is_cuda and str(t.dtype) == "torch.float64" and t.is_contiguous()
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(h, st):
+    if st != GKS_OK:
+        raise GKSError(st, load().gks_last_error(h).decode())
+
+
+def gks_default_options(precision=GKS_FP64, **kw) -> gks_options:
+    o = gks_options()
+    load().gks_default_options(ctypes.byref(o))
+    o.precision = precision
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def make_bcs(spec):
+    """spec: 4 entries (kind, u_wall, v_wall, T_wall) or kinds; order x-low, x-high, y-low, y-high."""
+    arr = (gks_bc * 4)()
+    for k in range(4):
+        s = spec[k] if isinstance(spec[k], (tuple, list)) else (spec[k], 0.0, 0.0, 1.0)
+        arr[k] = gks_bc(int(s[0]), float(s[1]), float(s[2]), float(s[3]))
+    return arr
+
+
+def gks_create(nx, ny, Lx, Ly, gamma, Pr, mu, bc=None, options=None, stream=None):
+    h = ctypes.c_void_p()
+    bcs = make_bcs(bc) if bc is not None else None
+    st = load().gks_create(int(nx), int(ny), float(Lx), float(Ly), float(gamma), float(Pr), float(mu), bcs,
+                           ctypes.byref(options) if options is not None else None,
+                           ctypes.c_void_p(stream) if stream else None, ctypes.byref(h))
+    _check(None, st)
+    return h
+
+
+def gks_set_state(h, U, Wx=None, Wy=None, t=0.0):
+    _check(h, load().gks_set_state(h, _ptr(U), _ptr(Wx), _ptr(Wy), float(t)))
+
+
+def gks_set_state_device(h, U, Wx=None, Wy=None, t=0.0):
+    _check(h, load().gks_set_state_device(h, _dev(U), _dev(Wx), _dev(Wy), float(t)))
+
+
+def gks_step(h, CFL, dt_max=float("inf")):
+    dt = ctypes.c_double(0.0)
+    _check(h, load().gks_step(h, float(CFL), float(dt_max), ctypes.byref(dt)))
+    return dt.value
+
+
+def gks_advance(h, nsteps, CFL, t_end=float("inf")):
+    _check(h, load().gks_advance(h, int(nsteps), float(CFL), float(t_end)))
+
+
+def gks_sync(h):
+    t = ctypes.c_double(0.0)
+    n = ctypes.c_longlong(0)
+    _check(h, load().gks_sync(h, ctypes.byref(t), ctypes.byref(n)))
+    return t.value, n.value
+
+
+def gks_get_state(h, U=None, Wx=None, Wy=None):
+    t = ctypes.c_double(0.0)
+    _check(h, load().gks_get_state(h, _ptr(U), _ptr(Wx), _ptr(Wy), ctypes.byref(t)))
+    return t.value
+
+
+def gks_get_state_device(h, U=None, Wx=None, Wy=None):
+    t = ctypes.c_double(0.0)
+    _check(h, load().gks_get_state_device(h, _dev(U), _dev(Wx), _dev(Wy), ctypes.byref(t)))
+    return t.value
+
+
+def gks_destroy(h):
+    if h:
+        load().gks_destroy(h)
+
+
+def gks_last_error(h=None) -> str:
+    return load().gks_last_error(h).decode()
+
+
+def gks_launches_per_step(h) -> int:
+    return load().gks_launches_per_step(h)
+
+
+def gks_debug_recon(h, nx, ny):
+    coef = np.zeros((4, 6, ny, nx))
+    _check(h, load().gks_debug_recon(h, _ptr(coef)))
+    return coef
+
+
+def gks_debug_flux(h, nx, ny, dt):
+    Fx, Fy = np.zeros((4, ny, nx + 1)), np.zeros((4, ny + 1, nx))
+    Wx, Wy = np.zeros((4, 2, ny, nx + 1)), np.zeros((4, 2, ny + 1, nx))
+    _check(h, load().gks_debug_flux(h, float(dt), _ptr(Fx), _ptr(Fy), _ptr(Wx), _ptr(Wy)))
+    return Fx, Fy, Wx, Wy
+
+
+class Solver:
+    """One grid on the GPU.  ``problem`` is a workloads.Problem (or any object with the same
+    attributes); the state is loaded at construction."""
+
+    def __init__(self, problem, precision=GKS_FP64, stream=None, **opts):
+        self.p = problem
+        self.nx, self.ny = problem.nx, problem.ny
+        o = gks_default_options(precision, **opts)
+        self.h = gks_create(problem.nx, problem.ny, problem.Lx, problem.Ly, problem.gamma, problem.Pr, problem.mu,
+                            problem.bc, o, stream)
+        gks_set_state(self.h, np.ascontiguousarray(problem.U), np.ascontiguousarray(problem.Wx),
+                      np.ascontiguousarray(problem.Wy), 0.0)
+
+    def step(self, CFL, dt_max=float("inf")):
+        return gks_step(self.h, CFL, dt_max)
+
+    def advance(self, nsteps, CFL, t_end=float("inf")):
+        gks_advance(self.h, nsteps, CFL, t_end)
+
+    def sync(self):
+        return gks_sync(self.h)
+
+    def state(self):
+        U = np.zeros((4, self.ny, self.nx))
+        Wx = np.zeros((4, 2, self.ny, self.nx + 1))
+        Wy = np.zeros((4, 2, self.ny + 1, self.nx))
+        t = gks_get_state(self.h, U, Wx, Wy)
+        return U, Wx, Wy, t
+
+    def close(self):
+        if self.h:
+            gks_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,39 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, and exports every
+function declared in include/gks.h (no compute call is made without a GPU)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gks.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gks_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("gks_create", "gks_set_state", "gks_step", "gks_get_state", "gks_destroy", "gks_advance"):
+        assert n in names
+
+
+def test_library_exports_every_declared_function():
+    from paper_1412_4489_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_the_abi():
+    from paper_1412_4489_gb300 import gks
+    for n in ("gks_create", "gks_set_state", "gks_set_state_device", "gks_step", "gks_advance", "gks_sync",
+              "gks_get_state", "gks_get_state_device", "gks_destroy", "gks_last_error"):
+        assert callable(getattr(gks, n))
+
+
+def test_default_options():
+    from paper_1412_4489_gb300 import gks
+    o = gks.gks_default_options()
+    assert (o.precision, o.weno_eps, o.weno_C, o.tau_eps, o.tau_C, o.viscous_dt) == (0, 1e-6, 1.0, 0.05, 1.0, 0)
