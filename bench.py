@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Throughput of the compact third-order GKS hot path on GB300, in Mcell-steps/s.
+
+Workload: the 2D Euler smooth wave of Section 4.1's analogue on the periodic square
+[0, 2]^2 at 512 x 512 cells (rho = 1 + 0.2 sin(pi (x + y) + phi), U = V = 1, p = 1,
+gamma = 1.4, CFL 0.5, seeded phi), the largest grid of its convergence sweep.  One
+step = ghost fill + compact reconstruction + face evolution on every x- and y-face +
+conservative update + CFL dt reduction, all in the library's CUDA kernels.
+
+The headline form is FP32-bulk (reconstruction, face evolution and face values in
+FP32; cell averages, update and dt in FP64); the plain FP64 form and the L1 density
+difference between the two are reported in the same line.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the
+solver's stream, with a 256 MiB write between steps to flush L2 (the state is smaller
+than L2).  Under torchrun each rank advances its own grid (replicas; no collective on
+the data path) and the max over ranks is used.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-steps/s on one GB300, FP32/batched form vs plain FP64, at stated L1 error"
+UNIT = "Mcell-steps/s"
+N_GRID = 512
+CFL = 0.5
+SEED = 2
+L2_FLUSH_BYTES = 256 << 20
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per Blackwell SM
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def workload_config(n=N_GRID):
+    return {"workload": f"2D Euler smooth wave {n}x{n}, periodic [0,2]^2, gamma 1.4, CFL {CFL}, seed {SEED}",
+            "grid": [n, n], "cells": n * n, "cfl": CFL, "tau_eps": 0.0,
+            "l2": "flushed between timed steps (256 MiB write); state < L2"}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "samples": len(rows),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def flux_traffic(precision_name):
+    """dram bytes per launch of the x-face kernel from the committed ncu summary, or None
+    when it is missing or the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"flux_x_{precision_name}_smooth_wave.md")
+    if not os.path.exists(path):
+        return None, None
+    h = source_hash()
+    traffic, scale, ok = None, None, False
+    for line in open(path):
+        if line.startswith("source_sha1:"):
+            ok = line.split(":", 1)[1].strip() == h
+        if line.startswith("traffic_bytes_per_face:"):
+            scale = float(line.split(":", 1)[1])
+    if ok and scale is not None:
+        traffic = scale
+    return traffic, path
+
+
+def source_hash():
+    m = hashlib.sha1()
+    for p in ("paper_1412_4489_gb300/csrc/gks_device.cuh", "paper_1412_4489_gb300/csrc/gks.cu"):
+        m.update(open(os.path.join(ROOT, p), "rb").read())
+    return m.hexdigest()
+
+
+def face_inputs(p):
+    """A representative x-face of the workload's initial state (face-frame inputs for the op count)."""
+    import numpy as np
+    g = p.gamma
+    dx = p.Lx / p.nx
+    phi = p.meta["phi"]
+    x0, y0 = dx * 10, dx * 10.5
+
+    def rho(x, y):
+        return 1 + 0.2 * math.sin(math.pi * (x + y) + phi)
+
+    def cons(r):
+        return np.array([r, r, r, 1 / (g - 1) + r])
+
+    h = 1e-4
+    S = np.zeros((6, 4))
+    S[0] = cons(rho(x0, y0))
+    dr = (rho(x0 + h, y0) - rho(x0 - h, y0)) / (2 * h)
+    ddr = (rho(x0 + h, y0) - 2 * rho(x0, y0) + rho(x0 - h, y0)) / h ** 2
+    # rho U = rho V = rho and rho E = 1/(g-1) + rho share the derivatives of rho
+    S[1] = S[2] = dr
+    S[3] = S[4] = S[5] = ddr
+    avg = np.array([[cons(rho(x0 + (m - 0.5) * dx, y0 + k * dx)) for k in (-1, 0, 1)] for m in (0, 1)])
+    return S, S.copy(), avg
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1412_4489_gb300 import gks, workloads as wl
+    gks.load()
+    dev_index = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    p = wl.smooth_wave_2d(args.size, seed=SEED)
+    cells = p.nx * p.ny
+    faces_x = (p.nx + 1) * p.ny
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def make(prec):
+        with torch.cuda.stream(stream):
+            return gks.Solver(p, prec, stream=stream.cuda_stream, tau_eps=0.0)
+
+    def timed_steps(s, K, W):
+        with torch.cuda.stream(stream):
+            s.advance(W, CFL)
+            s.sync()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            for k in range(K):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                s.advance(1, CFL)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in ev)
+            t, nsteps = s.sync()
+        return ms, nsteps
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- headline: FP32-bulk ----
+    s32 = make(gks.GKS_FP32_BULK)
+    with ClockSampler(dev_index) as clk:
+        ms32, n32 = timed_steps(s32, args.steps, args.warmup)
+    clocks = clk.summary()
+    ms32 = max_over_ranks(ms32)
+    ms_per_step = ms32 / args.steps
+    value = world * cells * args.steps / (ms32 * 1e-3) / 1e6
+
+    # per-kernel durations (events between the kernels of each step), L2 flushed between steps
+    prof = {k: 0.0 for k in gks.KERNEL_NAMES}
+    KP = max(10, min(args.steps, 50))
+    with torch.cuda.stream(stream):
+        for k in range(KP):
+            flush.fill_(float(k))
+            for name, ms in gks.gks_profile_step(s32.h, CFL).items():
+                prof[name] += ms / KP
+    prof_step = sum(prof.values())
+
+    # ---- plain FP64 ----
+    s64 = make(gks.GKS_FP64)
+    K64 = max(3, args.steps // 5)
+    ms64, _ = timed_steps(s64, K64, max(3, args.warmup // 2))
+    ms64 = max_over_ranks(ms64)
+    value64 = world * cells * K64 / (ms64 * 1e-3) / 1e6
+    prof64 = {k: 0.0 for k in gks.KERNEL_NAMES}
+    with torch.cuda.stream(stream):
+        for k in range(5):
+            flush.fill_(float(k))
+            for name, ms in gks.gks_profile_step(s64.h, CFL).items():
+                prof64[name] += ms / 5
+
+    # ---- L1 difference FP32-bulk vs FP64 after the same 100 steps from the initial state ----
+    a, b = make(gks.GKS_FP32_BULK), make(gks.GKS_FP64)
+    a.advance(100, CFL)
+    b.advance(100, CFL)
+    Ua, _, _, ta = a.state()
+    Ub, _, _, tb = b.state()
+    l1 = float(np.sum(np.abs(Ua[0] - Ub[0])) / np.sum(np.abs(Ub[0])))
+    linf = float(np.max(np.abs(Ua[0] - Ub[0])) / np.max(np.abs(Ub[0])))
+    a.close()
+    b.close()
+
+    # ---- end to end through the C ABI with host buffers ----
+    KE = max(3, min(args.steps, 20))
+    pin = lambda shape: torch.zeros(shape, dtype=torch.float64, pin_memory=True).numpy()
+    U, Wx, Wy = pin(p.U.shape), pin(p.Wx.shape), pin(p.Wy.shape)
+    U[...] = p.U
+    Wx[...] = p.Wx
+    Wy[...] = p.Wy
+    se = make(gks.GKS_FP32_BULK)
+    gks.gks_step(se.h, CFL)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    tt = 0.0
+    for _ in range(KE):
+        gks.gks_set_state(se.h, U, Wx, Wy, tt)
+        gks.gks_step(se.h, CFL)
+        tt = gks.gks_get_state(se.h, U, Wx, Wy)
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    bytes_state = 8 * (U.size + Wx.size + Wy.size)
+    se.close()
+
+    # ---- roofline of the dominant kernel ----
+    flux_kernels = {k: v for k, v in prof.items() if k.startswith("flux")}
+    dom = max(flux_kernels, key=flux_kernels.get)
+    L, R, avg = face_inputs(p)
+    ops = gks.gks_face_op_count(L, R, avg, p.Lx / p.nx, p.Ly / p.ny, 1e-3, p.gamma, 0.0, 1.0, 0.0, 1.0,
+                                gks.GKS_FP32_BULK)
+    flops_face = ops["add"] + ops["mul"] + ops["div"]
+    nfaces = faces_x if dom == "flux_x" else p.nx * (p.ny + 1)
+    achieved = flops_face * nfaces / (prof[dom] * 1e-3) / 1e12
+    peak32 = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    measured32 = gks.gks_measure_alu_peak(gks.GKS_FP32_BULK)
+    measured64 = gks.gks_measure_alu_peak(gks.GKS_FP64)
+    traffic, traffic_src = flux_traffic("fp32")
+    flops64 = flops_face  # the same arithmetic in FP64
+    achieved64 = flops64 * nfaces / (prof64[dom] * 1e-3) / 1e12
+
+    out = None
+    if rank == 0:
+        cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu_baseline) else None
+        out = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "accumulate_dtype": "f64",
+            "data": "synthetic (seeded smooth wave)",
+            "config": dict(workload_config(args.size), precision="fp32_bulk", parallelism=f"replicas x{world}"),
+            "fp64_plain": {"value": round(value64, 3), "unit": UNIT, "ms_per_step": round(ms64 / K64, 5),
+                           "steps": K64, "speedup_fp32_bulk": round(value / value64, 2)},
+            "error_fp32_bulk_vs_fp64": {"l1_rho_rel": l1, "linf_rho_rel": linf, "steps": 100,
+                                        "reference": "GPU FP64 path (oracle-pinned in tests)"},
+            "roofline": {"bound": "alu", "kernel": f"k_flux<{dom[-1]}> fp32", "achieved": round(achieved, 3),
+                         "peak": round(peak32, 2), "unit": "TFLOP/s", "frac": round(achieved / peak32, 4),
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                         "peak_measured_fma": round(measured32, 2), "frac_of_measured_fma": round(achieved / measured32, 4),
+                         "flops_per_face": flops_face, "faces_per_launch": nfaces,
+                         "special_per_face": {k: ops[k] for k in ("sqrt", "rsqrt", "exp", "expm1", "erfc")},
+                         "kernel_ms": round(prof[dom], 5), "traffic": traffic},
+            "roofline_fp64": {"bound": "alu", "kernel": f"k_flux<{dom[-1]}> fp64", "achieved": round(achieved64, 4),
+                              "peak": round(measured64, 3), "unit": "TFLOP/s", "frac": round(achieved64 / measured64, 4),
+                              "peak_source": "measured FP64 FMA throughput (gks_measure_alu_peak)",
+                              "kernel_ms": round(prof64[dom], 5)},
+            "kernels_ms_fp32": {k: round(v, 5) for k, v in prof.items()},
+            "kernels_ms_fp64": {k: round(v, 5) for k, v in prof64.items()},
+            "profiled_step_ms": round(prof_step, 5),
+            "clocks": clocks,
+            "e2e": {"value": round(world * cells * KE / e2e_s / 1e6, 3), "unit": UNIT,
+                    "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state, "steps": KE,
+                    "path": "gks_set_state (host) + gks_step + gks_get_state (host), pinned FP64 buffers"},
+            "gpu_launches": args.steps * gks.gks_launches_per_step(s32.h),
+            "cpu_baseline": cpu,
+        }
+    s32.close()
+    s64.close()
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# the oracle on the host cores
+# ----------------------------------------------------------------------------
+def oracle_rate(n, min_seconds, max_steps, warmup=1):
+    import oracle
+    from paper_1412_4489_gb300 import workloads as wl
+    p = wl.smooth_wave_2d(n, seed=SEED)
+    P = oracle.params(gamma=p.gamma, tau_eps=0.0)
+    st = oracle.State2D(p.nx, p.ny, p.Lx, p.Ly, p.U, p.Wx, p.Wy)
+    bc = oracle.bcs([0, 0, 0, 0])
+    for _ in range(warmup):
+        oracle.step2d(P, st, bc, CFL)
+    t0 = time.perf_counter()
+    k = 0
+    while k < max_steps and (k == 0 or time.perf_counter() - t0 < min_seconds):
+        oracle.step2d(P, st, bc, CFL)
+        k += 1
+    el = time.perf_counter() - t0
+    return n * n * k / el / 1e6, k, el, oracle.num_threads()
+
+
+def cpu_baseline(args):
+    v, k, el, cores = oracle_rate(args.size, 10.0, 50, warmup=0)
+    return {"value": round(v, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{k} oracle steps of the {args.size}x{args.size} smooth wave ({el:.1f} s, OpenMP over rows)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1412_4489_gb300 import workloads as wl
+    n = args.ref_size
+    p = wl.smooth_wave_2d(n, seed=SEED)
+    P = oracle.params(gamma=p.gamma, tau_eps=0.0)
+    st = oracle.State2D(p.nx, p.ny, p.Lx, p.Ly, p.U, p.Wx, p.Wy)
+    bc = oracle.bcs([0, 0, 0, 0])
+    for _ in range(args.warmup):
+        oracle.step2d(P, st, bc, CFL)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.step2d(P, st, bc, CFL)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = n * n * args.steps / total / 1e6
+    sample = f"each step: one oracle step of the smooth wave at {n}x{n} (a bounded sample of the {args.size}^2 workload)"
+    out = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded smooth wave)",
+           "impl": "reference", "config": dict(workload_config(args.size), precision="fp64", sample_grid=[n, n]),
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=N_GRID)
+    ap.add_argument("--ref-size", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        import oracle
+        oracle.build()
+        run_reference(args)
+    else:
+        import __graft_entry__
+        __graft_entry__.build()
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

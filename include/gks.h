@@ -159,6 +159,33 @@ const char* gks_last_error(const gks_handle* h);
 /* Number of kernel launches one step issues (for launch accounting). */
 int gks_launches_per_step(const gks_handle* h);
 
+/* Takes one step like gks_step(h, CFL, +inf, NULL) with CUDA events recorded on
+ * the handle's stream between its kernels, and writes the duration in ms of
+ * each of the seven kernels to ms[0..6], in launch order: begin, ghost fill,
+ * reconstruction, x-face evolution, y-face evolution, update, end.
+ * Synchronous; returns the status of the step. */
+gks_status gks_profile_step(gks_handle* h, double CFL, float* ms);
+
+/* ---- measurement helpers ---- */
+
+/* Counts the arithmetic of one evaluation of the face routine (the gas
+ * evolution of Section 2.2 at one face centre, as the kernels compute it) by
+ * running it once on the host with a counting number type, for the given
+ * face-frame inputs: L, R = [6][4] value and (dn, dt, dnn, dnt, dtt)
+ * derivatives of the two sides, avg = [2][3][4] the six cell averages of
+ * Section 3.3, cell sizes dn (normal) and dtan (along the face), time step dt.
+ * precision selects the branch thresholds of GKS_FP64 or GKS_FP32_BULK.
+ * counts[9] receives: additions/subtractions, multiplications, divisions,
+ * comparisons, sqrt, rsqrt, exp, expm1, erfc.  Host only; needs no GPU. */
+gks_status gks_face_op_count(const double* L, const double* R, const double* avg, double dn,
+                             double dtan, double dt, double gamma, double mu, double Pr,
+                             double tau_eps, double tau_C, int precision, long long* counts);
+
+/* Measures the FMA throughput of the current device in FP32 (GKS_FP32_BULK) or
+ * FP64 (GKS_FP64) with independent FMA chains on every SM; writes TFLOP/s
+ * (an FMA = 2 flops).  Synchronous; allocates 64 bytes of device memory. */
+gks_status gks_measure_alu_peak(int precision, double* tflops);
+
 /* ---- unit-level entry points used for per-kernel parity checks ---- */
 
 /* Runs only the reconstruction of the current state and copies the

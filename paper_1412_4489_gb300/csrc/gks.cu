@@ -517,25 +517,37 @@ gks_status fail(gks_handle* h, gks_status s, const std::string& msg) {
 
 dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
 
+// ev (optional, 8 events): recorded before each of the seven kernels and after the last
 template <class R, class TW>
 gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double t_end, bool with_begin_end,
-                               bool do_update, int force) {
+                               bool do_update, int force, cudaEvent_t* ev = nullptr) {
   const Geo& g = h->g;
   cudaStream_t s = h->stream;
+  auto mark = [&](int k) {
+    if (ev) cudaEventRecord(ev[k], s);
+  };
+  mark(0);
   if (with_begin_end) k_begin<<<1, 1, 0, s>>>(h->ctrl, cfl, dt_max, t_end);
+  mark(1);
   const int per = 2 * (g.nx + 2) + 2 * g.ny;
   k_ghost<<<(per + 127) / 128, 128, 0, s>>>(g, h->U[0], h->U[1], h->ctrl, force);
+  mark(2);
   const dim3 b2(32, 8), bf(32, 4);
   k_recon<R, TW><<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, h->U[0], h->U[1], (const TW*)h->Wx[0], (const TW*)h->Wx[1],
                                                        (const TW*)h->Wy[0], (const TW*)h->Wy[1], (R*)h->coef,
                                                        h->ctrl, force);
+  mark(3);
   k_flux<0, R, TW><<<grid2(g.nx + 1, g.ny, bf), bf, 0, s>>>(g, h->U[0], h->U[1], (const R*)h->coef, (TW*)h->Wx[0],
                                                              (TW*)h->Wx[1], (R*)h->Fx, h->ctrl, force);
+  mark(4);
   k_flux<1, R, TW><<<grid2(g.nx, g.ny + 1, bf), bf, 0, s>>>(g, h->U[0], h->U[1], (const R*)h->coef, (TW*)h->Wy[0],
                                                              (TW*)h->Wy[1], (R*)h->Fy, h->ctrl, force);
+  mark(5);
   if (do_update) k_update<R><<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, h->U[0], h->U[1], (const R*)h->Fx,
                                                                    (const R*)h->Fy, h->ctrl);
+  mark(6);
   if (with_begin_end) k_end<<<1, 1, 0, s>>>(h->ctrl);
+  mark(7);
   CK(cudaGetLastError());
   return GKS_OK;
 }
@@ -883,6 +895,26 @@ void gks_destroy(gks_handle* h) {
 }
 
 const char* gks_last_error(const gks_handle* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+gks_status gks_profile_step(gks_handle* h, double CFL, float* ms) {
+  if (!h || !ms || !(CFL > 0)) return fail(h, GKS_EINVAL, "gks_profile_step: CFL > 0 and ms[7] required");
+  CK(cudaSetDevice(h->device));
+  cudaEvent_t ev[8];
+  for (int k = 0; k < 8; ++k) CK(cudaEventCreate(&ev[k]));
+  gks_status st = h->prec == GKS_FP64 ? launch_step_kernels<double, double>(h, CFL, INFINITY, INFINITY, true, true, 0, ev)
+                                      : launch_step_kernels<float, float>(h, CFL, INFINITY, INFINITY, true, true, 0, ev);
+  if (st == GKS_OK) {
+    cudaError_t e = cudaEventSynchronize(ev[7]);
+    for (int k = 0; k < 7 && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
+    if (e != cudaSuccess) st = fail(h, GKS_ECUDA, std::string("gks_profile_step: ") + cudaGetErrorString(e));
+  }
+  for (int k = 0; k < 8; ++k) cudaEventDestroy(ev[k]);
+  if (st != GKS_OK) return st;
+  st = read_ctrl(h);
+  if (st != GKS_OK) return st;
+  if (h->hctrl->status != GKS_OK) return fail(h, (gks_status)h->hctrl->status, "step produced a non-physical state; state kept");
+  return GKS_OK;
+}
 
 int gks_launches_per_step(const gks_handle* h) {
   (void)h;

@@ -12,6 +12,10 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#ifndef GKS_FN
+#define GKS_FN __host__ __device__ __forceinline__
+#endif
+
 namespace gks {
 
 template <class R> struct Prec;
@@ -35,7 +39,7 @@ __device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double d_rsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float d_rsqrt(float x) { return rsqrtf(x); }
 
-template <class R> __device__ __forceinline__ R sq(R a) { return a * a; }
+template <class R> GKS_FN R sq(R a) { return a * a; }
 
 // ---------------------------------------------------------------------------
 // Section 2.1: moments of g = rho (lam/pi)^((K+2)/2) exp(-lam((u-U)^2+(v-V)^2+xi^2)),
@@ -50,7 +54,7 @@ struct Moments {
 
 // kind: 0 full space, +1 over u > 0, -1 over u < 0
 template <class R, int NU, int NV>
-__device__ __forceinline__ void moments(R U, R V, R lam, R K, int kind, Moments<R, NU, NV>& m) {
+GKS_FN void moments(R U, R V, R lam, R K, int kind, Moments<R, NU, NV>& m) {
   const R var = R(0.5) / lam;
   if (kind == 0) {
     m.u[0] = R(1);
@@ -75,7 +79,7 @@ __device__ __forceinline__ void moments(R U, R V, R lam, R K, int kind, Moments<
 
 // <u^A v^B psi> and <xi^2 u^A v^B psi>, psi = (1, u, v, (u^2+v^2+xi^2)/2)
 template <int A, int B, class R, int NU, int NV>
-__device__ __forceinline__ void psi_mom(const Moments<R, NU, NV>& m, R o[4]) {
+GKS_FN void psi_mom(const Moments<R, NU, NV>& m, R o[4]) {
   static_assert(A + 2 < NU && B + 2 < NV, "moment table too short");
   const R ab = m.u[A] * m.v[B];
   o[0] = ab;
@@ -86,7 +90,7 @@ __device__ __forceinline__ void psi_mom(const Moments<R, NU, NV>& m, R o[4]) {
 
 // <X u^A v^B psi> for X = X0 + X1 u + X2 v + X3 (u^2+v^2+xi^2)/2
 template <int A, int B, class R, int NU, int NV>
-__device__ __forceinline__ void coef_mom(const R X[4], const Moments<R, NU, NV>& m, R o[4]) {
+GKS_FN void coef_mom(const R X[4], const Moments<R, NU, NV>& m, R o[4]) {
   R p0[4], p1[4], p2[4], pa[4], pb[4];
   psi_mom<A, B>(m, p0);
   psi_mom<A + 1, B>(m, p1);
@@ -110,7 +114,7 @@ __device__ __forceinline__ void coef_mom(const R X[4], const Moments<R, NU, NV>&
 // N = K + 2.
 // ---------------------------------------------------------------------------
 template <class R>
-__device__ __forceinline__ void solve(R U, R V, R lam, R N, const R r[4], R x[4]) {
+GKS_FN void solve(R U, R V, R lam, R N, const R r[4], R x[4]) {
   const R q2 = U * U + V * V;
   const R x4 = R(4) * lam * lam / N *
                (R(2) * r[3] - R(2) * U * r[1] - R(2) * V * r[2] + (q2 - N / (R(2) * lam)) * r[0]);
@@ -135,7 +139,7 @@ struct TimeW {
 };
 
 template <class R>
-__device__ __forceinline__ void time_weights(R T, R tau, TimeW<R>& w) {
+GKS_FN void time_weights(R T, R tau, TimeW<R>& w) {
   const R x = tau > R(0) ? T / tau : R(INFINITY);
   const R e = tau > R(0) ? d_exp(-x) : R(0);
   const R om = tau > R(0) ? -d_expm1(-x) : R(1);  // 1 - e
@@ -202,7 +206,7 @@ struct Coefs {
 };
 
 template <class R, int NU, int NV>
-__device__ __forceinline__ void coef_systems(const Moments<R, NU, NV>& m, R rho, R U, R V, R lam, R N,
+GKS_FN void coef_systems(const Moments<R, NU, NV>& m, R rho, R U, R V, R lam, R N,
                                              const R d[5][4], bool time_terms, bool second_time,
                                              Coefs<R>& c) {
   const R ir = R(1) / rho;
@@ -260,7 +264,7 @@ struct Groups {
 };
 
 template <class R, int NU, int NV>
-__device__ __forceinline__ void add_flux(const Groups<R>& g, const Moments<R, NU, NV>& m, R rho, R out[4]) {
+GKS_FN void add_flux(const Groups<R>& g, const Moments<R, NU, NV>& m, R rho, R out[4]) {
   R t[4], s[4];
   coef_mom<1, 0>(g.X1, m, s);
   coef_mom<2, 0>(g.Xu, m, t);
@@ -281,7 +285,7 @@ __device__ __forceinline__ void add_flux(const Groups<R>& g, const Moments<R, NU
 }
 
 template <class R, int NU, int NV>
-__device__ __forceinline__ void add_point(const Groups<R>& g, const Moments<R, NU, NV>& m, R rho, R out[4]) {
+GKS_FN void add_point(const Groups<R>& g, const Moments<R, NU, NV>& m, R rho, R out[4]) {
   R t[4], s[4];
   coef_mom<0, 0>(g.X1, m, s);
   coef_mom<1, 0>(g.Xu, m, t);
@@ -302,7 +306,7 @@ __device__ __forceinline__ void add_point(const Groups<R>& g, const Moments<R, N
 }
 
 template <class R, int NU, int NV>
-__device__ __forceinline__ void add_point_linear(const R Y1[4], const R Yu[4], const R Yv[4],
+GKS_FN void add_point_linear(const R Y1[4], const R Yu[4], const R Yv[4],
                                                  const Moments<R, NU, NV>& m, R rho, R out[4]) {
   R s[4], t[4];
   coef_mom<0, 0>(Y1, m, s);
@@ -317,7 +321,7 @@ __device__ __forceinline__ void add_point_linear(const R Y1[4], const R Yu[4], c
 // Eq. dis1 grouped: weights W = I (flux, mean) or E (point); y2 = dtan^2/12 is both
 // the face mean of y^2 and y^2 at the Gauss points.
 template <class R>
-__device__ __forceinline__ void hydro_groups(const Coefs<R>& c, const R* W, R y2, Groups<R>& g) {
+GKS_FN void hydro_groups(const Coefs<R>& c, const R* W, R y2, Groups<R>& g) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     g.X1[k] = W[3] * c.A[k] + R(0.5) * W[5] * c.Att[k] + R(0.5) * y2 * W[1] * c.Ayy[k];
@@ -332,7 +336,7 @@ __device__ __forceinline__ void hydro_groups(const Coefs<R>& c, const R* W, R y2
 
 // Eq. dis2 grouped for one side; tn = tau for the Navier-Stokes f_G, 0 for Euler
 template <class R>
-__device__ __forceinline__ void kinetic_groups(const Coefs<R>& c, const R* W, R y2, R tn, Groups<R>& g) {
+GKS_FN void kinetic_groups(const Coefs<R>& c, const R* W, R y2, R tn, Groups<R>& g) {
   const R w78 = W[8] - tn * W[7];
   const R wq = R(0.5) * W[10] - tn * W[8];
 #pragma unroll
@@ -356,7 +360,7 @@ struct FaceState {
 };
 
 template <class R>
-__device__ __forceinline__ void prim(const R w[4], R gm1, R& rho, R& U, R& V, R& p) {
+GKS_FN void prim(const R w[4], R gm1, R& rho, R& U, R& V, R& p) {
   rho = w[0];
   const R ir = R(1) / rho;
   U = w[1] * ir;
@@ -374,7 +378,7 @@ struct FaceParams {
 // tangential wall velocity uwt and wall temperature Tw: rho' = rho,
 // m' = 2 rho u_w - m, rho E' = 2 rho |u_w|^2 - 2 u_w.m + |m|^2/rho + 2 rho Tw/(gamma-1) - rho E.
 template <class R>
-__device__ __forceinline__ void wall_image(int kind, R gamma, R uwt, R Tw, const FaceState<R>& in, FaceState<R>& out) {
+GKS_FN void wall_image(int kind, R gamma, R uwt, R Tw, const FaceState<R>& in, FaceState<R>& out) {
   if (kind == 2) {
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
@@ -437,7 +441,7 @@ __device__ __forceinline__ void wall_image(int kind, R gamma, R uwt, R Tw, const
 // Gauss points (tangential -/+ sqrt(3)/6 dtan) at t = dt.
 // ---------------------------------------------------------------------------
 template <class R>
-__device__ __forceinline__ void face_evolution(const FaceParams& P, const FaceState<R>& L,
+GKS_FN void face_evolution(const FaceParams& P, const FaceState<R>& L,
                                                const FaceState<R>& Rs, const R avg[2][3][4], R dt,
                                                R F[4], R Wm[4], R Wp[4]) {
   const R gamma = R(P.gamma), gm1 = gamma - R(1);
@@ -578,12 +582,12 @@ __device__ __forceinline__ void face_evolution(const FaceParams& P, const FaceSt
 //   U(x,y) = c + a2 x + a3 y + a4 (x^2-dx^2/12)/2 + a5 (y^2-dy^2/12)/2 + a6 x y.
 // ---------------------------------------------------------------------------
 template <class R>
-__device__ __forceinline__ R minmod(R a, R b) {
+GKS_FN R minmod(R a, R b) {
   return a * b > R(0) ? (fabs(a) < fabs(b) ? a : b) : R(0);
 }
 
 template <class R>
-__device__ __forceinline__ void recon_var(R c, R e, R w, R n, R s, R em, R ep, R wm, R wp, R nm, R np, R sm,
+GKS_FN void recon_var(R c, R e, R w, R n, R s, R em, R ep, R wm, R wp, R nm, R np, R sm,
                                           R sp, R dx, R dy, R weps, R wC, R a[5]) {
   const R idx = R(1) / dx, idy = R(1) / dy;
   const R idx2 = idx * idx, idy2 = idy * idy;

@@ -69,10 +69,14 @@ def load(path: str | None = None):
     L.gks_last_error.argtypes = [H]
     L.gks_last_error.restype = ctypes.c_char_p
     L.gks_launches_per_step.argtypes = [H]
+    L.gks_profile_step.argtypes = [H, D, ctypes.POINTER(ctypes.c_float)]
+    L.gks_face_op_count.argtypes = [_dp, _dp, _dp, D, D, D, D, D, D, D, D, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_longlong)]
+    L.gks_measure_alu_peak.argtypes = [ctypes.c_int, _dp]
     L.gks_debug_recon.argtypes = [H, _dp]
     L.gks_debug_flux.argtypes = [H, D, _dp, _dp, _dp, _dp]
     for name in ("gks_create", "gks_set_state", "gks_set_state_device", "gks_step", "gks_advance", "gks_sync",
-                 "gks_get_state", "gks_get_state_device", "gks_debug_recon", "gks_debug_flux",
+                 "gks_get_state", "gks_get_state_device", "gks_debug_recon", "gks_debug_flux", "gks_profile_step", "gks_face_op_count", "gks_measure_alu_peak",
                  "gks_launches_per_step"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -174,6 +178,36 @@ def gks_last_error(h=None) -> str:
 
 def gks_launches_per_step(h) -> int:
     return load().gks_launches_per_step(h)
+
+
+KERNEL_NAMES = ["begin", "ghost", "recon", "flux_x", "flux_y", "update", "end"]
+
+
+def gks_profile_step(h, CFL):
+    """One step with per-kernel CUDA-event timing; returns {kernel name: ms}."""
+    ms = (ctypes.c_float * 7)()
+    _check(h, load().gks_profile_step(h, float(CFL), ms))
+    return dict(zip(KERNEL_NAMES, list(ms)))
+
+
+OP_NAMES = ["add", "mul", "div", "cmp", "sqrt", "rsqrt", "exp", "expm1", "erfc"]
+
+
+def gks_face_op_count(L, R, avg, dn, dtan, dt, gamma, mu, Pr, tau_eps=0.05, tau_C=1.0, precision=GKS_FP64):
+    """Arithmetic of one face evaluation, counted on the host: {op: count}."""
+    L = np.ascontiguousarray(L, dtype=np.float64).reshape(6, 4)
+    R = np.ascontiguousarray(R, dtype=np.float64).reshape(6, 4)
+    avg = np.ascontiguousarray(avg, dtype=np.float64).reshape(2, 3, 4)
+    c = (ctypes.c_longlong * 9)()
+    _check(None, load().gks_face_op_count(_ptr(L), _ptr(R), _ptr(avg), dn, dtan, dt, gamma, mu, Pr, tau_eps, tau_C,
+                                          int(precision), c))
+    return dict(zip(OP_NAMES, list(c)))
+
+
+def gks_measure_alu_peak(precision):
+    t = ctypes.c_double(0.0)
+    _check(None, load().gks_measure_alu_peak(int(precision), ctypes.byref(t)))
+    return t.value
 
 
 def gks_debug_recon(h, nx, ny):
