@@ -186,6 +186,40 @@ gks_status gks_face_op_count(const double* L, const double* R, const double* avg
  * (an FMA = 2 flops).  Synchronous; allocates 64 bytes of device memory. */
 gks_status gks_measure_alu_peak(int precision, double* tflops);
 
+/* ---- allocation-free single step ----
+ *
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory themselves -- code that runs under another runtime's
+ * memory manager or a hard memory cap, and latency-critical loops in which a
+ * cudaMalloc/cudaFree would synchronise the device -- and so cannot hold a
+ * gks_handle (gks_create allocates).
+ *
+ * One FP64 time step (the same kernels as gks_step) from the caller's device
+ * arrays dU, dWx, dWy (state layouts above, FP64, on the current device) into
+ * the caller's device arrays dU_out, dWx_out, dWy_out (must not alias the
+ * inputs), with dt = min(CFL * dt_cfl, dt_max) written to *dt_taken (may be
+ * NULL).  The other arguments mean what they mean for gks_create (opt may be
+ * NULL; its precision must be GKS_FP64).  Work is queued on cuda_stream (NULL =
+ * the legacy default stream) and the call waits for it.
+ *
+ * It calls no cudaMalloc, cudaFree or allocating library routine: its scratch
+ * (cell averages before and after, reconstruction coefficients, face fluxes and
+ * a control block) is one static 32 MiB device array inside this library, which
+ * every GPU that loads the library holds until the process exits.  Grids of more
+ * than 65,536 cells are rejected with GKS_EINVAL and a message in
+ * gks_last_error(NULL).  Every call shares that array and leaves its contents
+ * behind; the control block is cleared at the start of each call.  Calls whose
+ * work overlaps on the GPU (from several threads or streams) race on the array
+ * and must be serialised by the caller.  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make that
+ * first call before any stream capture.  Returns GKS_ENONPHYSICAL (outputs not
+ * valid) if the new state is not physical, GKS_EINVAL if dt would be 0. */
+gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, double gamma, double Pr, double mu,
+                            const gks_bc* bc, const gks_options* opt, const double* dU,
+                            const double* dWx, const double* dWy, double CFL, double dt_max,
+                            double* dU_out, double* dWx_out, double* dWy_out, double* dt_taken,
+                            void* cuda_stream);
+
 /* ---- unit-level entry points used for per-kernel parity checks ---- */
 
 /* Runs only the reconstruction of the current state and copies the

@@ -20,6 +20,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <string>
 
 #include "../../include/gks.h"
@@ -972,3 +973,128 @@ gks_status gks_debug_flux(gks_handle* h, double dt, double* Fx, double* Fy, doub
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free single step (gks_step_noalloc).  For callers that must not
+// allocate device memory themselves: code running under another runtime's
+// memory manager or a hard memory cap, and latency-critical loops where
+// cudaMalloc/cudaFree would synchronise the device.  The scratch of one step
+// (the padded cell averages before and after, the reconstruction coefficients,
+// the face fluxes and the control block) lives in one file-scope device array
+// that every GPU loading this library holds until the process exits.
+// ===========================================================================
+namespace {
+
+constexpr size_t kNoallocBytes = (size_t)32 << 20;  // 32 MiB: any grid of up to 65,536 cells
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+// device address of g_noalloc_scratch per device, looked up once with the device current
+void* noalloc_base(int device, std::string& why) {
+  static std::atomic<void*> base[64];
+  if (device < 0 || device >= 64) { why = "device index out of range"; return nullptr; }
+  void* p = base[device].load();
+  if (!p) {
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) { why = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e); return nullptr; }
+    base[device].store(p);
+  }
+  return p;
+}
+
+__global__ void k_noalloc_ctrl(Ctrl* c) {
+  c->dtbits[0] = c->dtbits[1] = dbits(INFINITY);
+  c->t = 0.0;
+  c->dt = 0.0;
+  c->steps = 0;
+  c->status = GKS_OK;
+  c->skip = 0;
+  c->fail_step = -1;
+}
+
+}  // namespace
+
+extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, double gamma, double Pr, double mu,
+                                       const gks_bc* bc, const gks_options* opt, const double* dU,
+                                       const double* dWx, const double* dWy, double CFL, double dt_max,
+                                       double* dU_out, double* dWx_out, double* dWy_out, double* dt_taken,
+                                       void* cuda_stream) {
+  gks_options o;
+  gks_default_options(&o);
+  if (opt) o = *opt;
+  std::string why;
+  if (check_args(nx, ny, Lx, Ly, gamma, Pr, mu, bc, &o, why) != GKS_OK) { g_create_err = why; return GKS_EINVAL; }
+  if (o.precision != GKS_FP64) { g_create_err = "gks_step_noalloc: only GKS_FP64"; return GKS_EINVAL; }
+  if (!dU || !dWx || !dWy || !dU_out || !dWx_out || !dWy_out || !(CFL > 0) || !(dt_max > 0)) {
+    g_create_err = "gks_step_noalloc: all six state pointers, CFL > 0 and dt_max > 0 are required";
+    return GKS_EINVAL;
+  }
+  Geo g;
+  memset(&g, 0, sizeof(g));
+  g.nx = nx; g.ny = ny;
+  g.pitch = ((nx + 2) + 1) & ~1;
+  g.plane = (size_t)(ny + 2) * g.pitch;
+  g.dx = Lx / nx; g.dy = Ly / ny;
+  g.gamma = gamma; g.mu = mu; g.Pr = Pr;
+  g.weno_eps = o.weno_eps; g.weno_C = o.weno_C; g.tau_eps = o.tau_eps; g.tau_C = o.tau_C;
+  g.viscous_dt = o.viscous_dt;
+  for (int k = 0; k < 4; ++k) {
+    g.bc.kind[k] = bc ? bc[k].kind : GKS_BC_PERIODIC;
+    g.bc.uw[k] = bc ? bc[k].u_wall : 0.0;
+    g.bc.vw[k] = bc ? bc[k].v_wall : 0.0;
+    g.bc.Tw[k] = bc ? bc[k].T_wall : 1.0;
+  }
+  // scratch layout: control block | padded U before | padded U after | coefficients | Fx | Fy
+  const size_t b_ctrl = align256(sizeof(Ctrl));
+  const size_t b_u = align256(4 * g.plane * sizeof(double));
+  const size_t b_coef = align256((size_t)20 * nx * ny * sizeof(double));
+  const size_t b_fx = align256((size_t)4 * ny * (nx + 1) * sizeof(double));
+  const size_t b_fy = align256((size_t)4 * (ny + 1) * nx * sizeof(double));
+  const size_t need = b_ctrl + 2 * b_u + b_coef + b_fx + b_fy;
+  if ((long long)nx * ny > 65536 || need > kNoallocBytes) {
+    g_create_err = "gks_step_noalloc: grid too large for the static scratch (at most 65,536 cells, " +
+                   std::to_string(kNoallocBytes >> 20) + " MiB); need " + std::to_string(need) + " bytes";
+    return GKS_EINVAL;
+  }
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) { g_create_err = std::string("cudaGetDevice: ") + cudaGetErrorString(e); return GKS_ECUDA; }
+  unsigned char* base = (unsigned char*)noalloc_base(device, why);
+  if (!base) { g_create_err = "gks_step_noalloc: " + why; return GKS_ECUDA; }
+  Ctrl* ctrl = (Ctrl*)base;
+  double* U0 = (double*)(base + b_ctrl);
+  double* U1 = (double*)(base + b_ctrl + b_u);
+  double* coef = (double*)(base + b_ctrl + 2 * b_u);
+  double* Fx = (double*)(base + b_ctrl + 2 * b_u + b_coef);
+  double* Fy = (double*)(base + b_ctrl + 2 * b_u + b_coef + b_fx);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const dim3 b2(32, 8), bf(32, 4);
+  const int per = 2 * (nx + 2) + 2 * ny;
+  // the control block must start from zero state; the rest is fully written before it is read
+  k_noalloc_ctrl<<<1, 1, 0, s>>>(ctrl);
+  k_scatter_U<<<grid2(nx, ny, b2), b2, 0, s>>>(g, dU, U0, U1, ctrl, 1);
+  k_ghost<<<(per + 127) / 128, 128, 0, s>>>(g, U0, U1, ctrl, 1);
+  k_dtbound<<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, ctrl);
+  k_begin<<<1, 1, 0, s>>>(ctrl, CFL, dt_max, INFINITY);
+  k_recon<double, double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, dWx, dWx_out, dWy, dWy_out, coef, ctrl, 0);
+  k_flux<0, double, double><<<grid2(nx + 1, ny, bf), bf, 0, s>>>(g, U0, U1, coef, const_cast<double*>(dWx), dWx_out,
+                                                                  Fx, ctrl, 0);
+  k_flux<1, double, double><<<grid2(nx, ny + 1, bf), bf, 0, s>>>(g, U0, U1, coef, const_cast<double*>(dWy), dWy_out,
+                                                                  Fy, ctrl, 0);
+  k_update<double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, Fx, Fy, ctrl);
+  k_end<<<1, 1, 0, s>>>(ctrl);
+  k_scatter_U<<<grid2(nx, ny, b2), b2, 0, s>>>(g, dU_out, U0, U1, ctrl, 0);
+  e = cudaGetLastError();
+  Ctrl hc;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { g_create_err = std::string("gks_step_noalloc: ") + cudaGetErrorString(e); return GKS_ECUDA; }
+  if (dt_taken) *dt_taken = hc.skip ? 0.0 : hc.dt;
+  if (hc.status != GKS_OK) {
+    g_create_err = "gks_step_noalloc: the step produced a non-physical state; outputs are not valid";
+    return (gks_status)hc.status;
+  }
+  if (hc.skip) { g_create_err = "gks_step_noalloc: dt = 0, no step taken; outputs are not valid"; return GKS_EINVAL; }
+  return GKS_OK;
+}

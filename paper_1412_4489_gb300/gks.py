@@ -73,10 +73,13 @@ def load(path: str | None = None):
     L.gks_face_op_count.argtypes = [_dp, _dp, _dp, D, D, D, D, D, D, D, D, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_longlong)]
     L.gks_measure_alu_peak.argtypes = [ctypes.c_int, _dp]
+    L.gks_step_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, D, D, D, D, D, ctypes.POINTER(gks_bc),
+                                   ctypes.POINTER(gks_options), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, D, D,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _dp, ctypes.c_void_p]
     L.gks_debug_recon.argtypes = [H, _dp]
     L.gks_debug_flux.argtypes = [H, D, _dp, _dp, _dp, _dp]
     for name in ("gks_create", "gks_set_state", "gks_set_state_device", "gks_step", "gks_advance", "gks_sync",
-                 "gks_get_state", "gks_get_state_device", "gks_debug_recon", "gks_debug_flux", "gks_profile_step", "gks_face_op_count", "gks_measure_alu_peak",
+                 "gks_get_state", "gks_get_state_device", "gks_debug_recon", "gks_debug_flux", "gks_profile_step", "gks_step_noalloc", "gks_face_op_count", "gks_measure_alu_peak",
                  "gks_launches_per_step"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -165,6 +168,20 @@ def gks_get_state_device(h, U=None, Wx=None, Wy=None):
     t = ctypes.c_double(0.0)
     _check(h, load().gks_get_state_device(h, _dev(U), _dev(Wx), _dev(Wy), ctypes.byref(t)))
     return t.value
+
+
+def gks_step_noalloc(nx, ny, Lx, Ly, gamma, Pr, mu, bc, options, U, Wx, Wy, U_out, Wx_out, Wy_out, CFL,
+                     dt_max=float("inf"), stream=None):
+    """One FP64 step between caller-owned torch CUDA tensors, using the library's static
+    scratch instead of any device allocation (see gks.h).  Returns dt."""
+    dt = ctypes.c_double(0.0)
+    st = load().gks_step_noalloc(int(nx), int(ny), float(Lx), float(Ly), float(gamma), float(Pr), float(mu),
+                                 make_bcs(bc) if bc is not None else None,
+                                 ctypes.byref(options) if options is not None else None,
+                                 _dev(U), _dev(Wx), _dev(Wy), float(CFL), float(dt_max), _dev(U_out), _dev(Wx_out),
+                                 _dev(Wy_out), ctypes.byref(dt), ctypes.c_void_p(stream) if stream else None)
+    _check(None, st)
+    return dt.value
 
 
 def gks_destroy(h):
