@@ -145,11 +145,14 @@ __global__ void k_end(Ctrl* c) {
 }
 
 // ---------------------------------------------------------------------------
-// ghost ring: perimeter of the padded cell array of the current buffer
+// ghost ring: perimeter of the padded cell array of the current buffer; in
+// FP32-bulk mode the FP32 mirror (F0/F1) gets the same values
 // ---------------------------------------------------------------------------
-__global__ void k_ghost(Geo g, double* U0, double* U1, const Ctrl* c, int force) {
+__global__ void k_ghost(Geo g, double* U0, double* U1, float* F0, float* F1, const Ctrl* c, int force) {
   if (!force && c->skip) return;
-  double* U = (c->steps & 1) ? U1 : U0;
+  const int par = (int)(c->steps & 1);
+  double* U = par ? U1 : U0;
+  float* Uf = par ? F1 : F0;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = g.nx + 2;
   int i, j;
@@ -160,43 +163,54 @@ __global__ void k_ghost(Geo g, double* U0, double* U1, const Ctrl* c, int force)
   else return;
   double w[4];
   ghost_cell(g, U, i, j, w);
-  for (int v = 0; v < 4; ++v) U[ci(g, v, i, j)] = w[v];
+  for (int v = 0; v < 4; ++v) {
+    U[ci(g, v, i, j)] = w[v];
+    if (Uf) Uf[ci(g, v, i, j)] = (float)w[v];
+  }
+}
+
+// FP32 mirror of the interior of the current cell-average buffer
+__global__ void k_mirror(Geo g, const double* U0, const double* U1, float* F0, float* F1, const Ctrl* c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  const int par = (int)(c->steps & 1);
+  const double* U = par ? U1 : U0;
+  float* Uf = par ? F1 : F0;
+  for (int v = 0; v < 4; ++v) Uf[ci(g, v, i, j)] = (float)U[ci(g, v, i, j)];
 }
 
 // ---------------------------------------------------------------------------
-// reconstruction
+// reconstruction; U is the padded cell-average array in the compute type
 // ---------------------------------------------------------------------------
 template <class R, class TW>
-__global__ void __launch_bounds__(256) k_recon(Geo g, const double* U0, const double* U1, const TW* Wx0,
-                                               const TW* Wx1, const TW* Wy0, const TW* Wy1, R* __restrict__ coef,
-                                               const Ctrl* c, int force) {
+__global__ void __launch_bounds__(256) k_recon(Geo g, const R* U0, const R* U1, const TW* Wx0, const TW* Wx1,
+                                               const TW* Wy0, const TW* Wy1, R* __restrict__ coef, R dx, R dy,
+                                               R weps, R wC, R gm1, const Ctrl* c, int force) {
   if (!force && c->skip) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
   const int par = (int)(c->steps & 1);
-  const double* __restrict__ U = par ? U1 : U0;
+  const R* __restrict__ U = par ? U1 : U0;
   const TW* __restrict__ Wx = par ? Wx1 : Wx0;
   const TW* __restrict__ Wy = par ? Wy1 : Wy0;
   const int nx = g.nx, ny = g.ny;
   const size_t fxp = (size_t)ny * (nx + 1), fyp = (size_t)(ny + 1) * nx;
-  const R dx = R(g.dx), dy = R(g.dy);
   R a[4][5];
   R cbar[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    const R cc = R(U[ci(g, v, i, j)]);
+    const R cc = U[ci(g, v, i, j)];
     cbar[v] = cc;
     const TW* wx = Wx + (size_t)v * 2 * fxp + (size_t)j * (nx + 1);
     const TW* wy = Wy + (size_t)v * 2 * fyp;
-    recon_var<R>(cc, R(U[ci(g, v, i + 1, j)]), R(U[ci(g, v, i - 1, j)]), R(U[ci(g, v, i, j + 1)]),
-                 R(U[ci(g, v, i, j - 1)]), R(wx[i + 1]), R(wx[fxp + i + 1]), R(wx[i]), R(wx[fxp + i]),
-                 R(wy[(size_t)(j + 1) * nx + i]), R(wy[fyp + (size_t)(j + 1) * nx + i]),
-                 R(wy[(size_t)j * nx + i]), R(wy[fyp + (size_t)j * nx + i]), dx, dy, R(g.weno_eps),
-                 R(g.weno_C), a[v]);
+    recon_var<R>(cc, U[ci(g, v, i + 1, j)], U[ci(g, v, i - 1, j)], U[ci(g, v, i, j + 1)], U[ci(g, v, i, j - 1)],
+                 R(wx[i + 1]), R(wx[fxp + i + 1]), R(wx[i]), R(wx[fxp + i]), R(wy[(size_t)(j + 1) * nx + i]),
+                 R(wy[fyp + (size_t)(j + 1) * nx + i]), R(wy[(size_t)j * nx + i]), R(wy[fyp + (size_t)j * nx + i]),
+                 dx, dy, weps, wC, a[v]);
   }
   // positivity: rho and p at the four face centres, else the constant average
-  const R gm1 = R(g.gamma - 1.0);
   bool bad = false;
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
@@ -227,13 +241,12 @@ template <int AX> __device__ __forceinline__ int slot(int v) { return AX == 0 ? 
 // value and derivatives of cell (i, j)'s polynomial at the centre of its face
 // on side s (+1: the face at +h_n/2, -1: at -h_n/2), in the face frame of axis AX
 template <int AX, class R>
-__device__ __forceinline__ void side_state(const Geo& g, const double* __restrict__ U, const R* __restrict__ coef,
-                                           int i, int j, int s, FaceState<R>& S) {
+__device__ __forceinline__ void side_state(const Geo& g, const R* __restrict__ U, const R* __restrict__ coef,
+                                           int i, int j, int s, R hn, R ht, FaceState<R>& S) {
   const size_t N = (size_t)g.nx * g.ny, o = (size_t)j * g.nx + i;
-  const R hn = R(AX == 0 ? g.dx : g.dy), ht = R(AX == 0 ? g.dy : g.dx);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    const R c = R(U[ci(g, v, i, j)]);
+    const R c = U[ci(g, v, i, j)];
     const R a2 = coef[(size_t)(0 * 4 + v) * N + o], a3 = coef[(size_t)(1 * 4 + v) * N + o];
     const R a4 = coef[(size_t)(2 * 4 + v) * N + o], a5 = coef[(size_t)(3 * 4 + v) * N + o];
     const R a6 = coef[(size_t)(4 * 4 + v) * N + o];
@@ -250,9 +263,71 @@ __device__ __forceinline__ void side_state(const Geo& g, const double* __restric
   }
 }
 
+// resident 128-thread blocks per SM the face kernel is compiled for (register cap)
+#ifndef GKS_FLUX_MINB_F32
+#define GKS_FLUX_MINB_F32 4
+#endif
+template <class R> struct FluxBlocks;
+template <> struct FluxBlocks<double> { static constexpr int value = 1; };
+template <> struct FluxBlocks<float> { static constexpr int value = GKS_FLUX_MINB_F32; };
+
+// Inputs of one face, fetched on demand by face_evolution
+template <int AX, class R>
+struct GridFaceSource {
+  const Geo* g;
+  const R* U;
+  const R* coef;
+  int i, j;           // face index (x-faces: i in [0, nx]; y-faces: j in [0, ny])
+  int cl, cr;         // the two cells along the normal, after periodic wrap
+  int img_lo, img_hi; // boundary image on the low / high side: 0 none, else the BC kind
+  R hn, ht, gamma, uwt_lo, Tw_lo, uwt_hi, Tw_hi;
+
+  __device__ __forceinline__ int cx(int n) const { return AX == 0 ? n : i; }
+  __device__ __forceinline__ int cy(int n) const { return AX == 0 ? j : n; }
+
+  __device__ __forceinline__ void image(int kind, R uwt, R Tw, const FaceState<R>& in, FaceState<R>& out) const {
+    if (kind == GKS_BC_OUTFLOW) out = in;
+    else wall_image<R>(kind, gamma, uwt, Tw, in, out);
+  }
+
+  __device__ __forceinline__ void side(int k, FaceState<R>& S) const {
+    if (k == 0) {
+      if (img_lo) {
+        FaceState<R> in;
+        side_state<AX>(*g, U, coef, cx(cr), cy(cr), -1, hn, ht, in);
+        image(img_lo, uwt_lo, Tw_lo, in, S);
+      } else {
+        side_state<AX>(*g, U, coef, cx(cl), cy(cl), +1, hn, ht, S);
+      }
+    } else {
+      if (img_hi) {
+        FaceState<R> in;
+        side_state<AX>(*g, U, coef, cx(cl), cy(cl), +1, hn, ht, in);
+        image(img_hi, uwt_hi, Tw_hi, in, S);
+      } else {
+        side_state<AX>(*g, U, coef, cx(cr), cy(cr), -1, hn, ht, S);
+      }
+    }
+  }
+
+  // six cell averages around the face (ghost ring included), face frame
+  __device__ __forceinline__ void avg(R a[2][3][4]) const {
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int ii = AX == 0 ? i - 1 + m : i - 1 + k;
+        const int jj = AX == 0 ? j - 1 + k : j - 1 + m;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) a[m][k][slot<AX>(v)] = U[ci(*g, v, ii, jj)];
+      }
+  }
+};
+
 template <int AX, class R, class TW>
-__global__ void __launch_bounds__(128) k_flux(Geo g, const double* U0, const double* U1, const R* __restrict__ coef,
-                                              TW* Wn0, TW* Wn1, R* __restrict__ F, const Ctrl* c, int force) {
+__global__ void __launch_bounds__(128, FluxBlocks<R>::value) k_flux(Geo g, FaceConst<R> C, const R* U0, const R* U1,
+                                              const R* __restrict__ coef, TW* Wn0, TW* Wn1, R* __restrict__ F,
+                                              const Ctrl* c, int force) {
   if (!force && c->skip) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -260,147 +335,146 @@ __global__ void __launch_bounds__(128) k_flux(Geo g, const double* U0, const dou
   const int fx = AX == 0 ? nx + 1 : nx, fy = AX == 0 ? ny : ny + 1;
   if (i >= fx || j >= fy) return;
   const int par = (int)(c->steps & 1);
-  const double* __restrict__ U = par ? U1 : U0;
   TW* __restrict__ Wn = par ? Wn0 : Wn1;  // new face values go to the other buffer
-  const double dt = c->dt;
 
-  // the two cells sharing the face and the boundary sides
+  GridFaceSource<AX, R> src;
+  src.g = &g;
+  src.U = par ? U1 : U0;
+  src.coef = coef;
+  src.i = i;
+  src.j = j;
   const int f = AX == 0 ? i : j;      // face index along the normal
   const int nf = AX == 0 ? nx : ny;   // faces 0 and nf are on the boundary
   const int lo_side = AX == 0 ? 0 : 2, hi_side = lo_side + 1;
-  int cl = f - 1, cr = f;
-  const bool lo = f == 0, hi = f == nf;
-  const bool lo_per = g.bc.kind[lo_side] == GKS_BC_PERIODIC, hi_per = g.bc.kind[hi_side] == GKS_BC_PERIODIC;
-  if (lo && lo_per) cl = nf - 1;
-  if (hi && hi_per) cr = 0;
-
-  FaceState<R> L, Rt;
-  auto cell = [&](int n) { return AX == 0 ? n : i; };
-  auto row = [&](int n) { return AX == 0 ? j : n; };
-  if (lo && !lo_per) {
-    side_state<AX>(g, U, coef, cell(cr), row(cr), -1, Rt);
-    if (g.bc.kind[lo_side] == GKS_BC_OUTFLOW) L = Rt;
-    else wall_image<R>(g.bc.kind[lo_side], R(g.gamma), R(wall_t_velocity(g.bc, lo_side)), R(g.bc.Tw[lo_side]), Rt, L);
-  } else if (hi && !hi_per) {
-    side_state<AX>(g, U, coef, cell(cl), row(cl), +1, L);
-    if (g.bc.kind[hi_side] == GKS_BC_OUTFLOW) Rt = L;
-    else wall_image<R>(g.bc.kind[hi_side], R(g.gamma), R(wall_t_velocity(g.bc, hi_side)), R(g.bc.Tw[hi_side]), L, Rt);
-  } else {
-    side_state<AX>(g, U, coef, cell(cl), row(cl), +1, L);
-    side_state<AX>(g, U, coef, cell(cr), row(cr), -1, Rt);
+  src.cl = f - 1;
+  src.cr = f;
+  src.img_lo = src.img_hi = 0;
+  if (f == 0) {
+    if (g.bc.kind[lo_side] == GKS_BC_PERIODIC) src.cl = nf - 1;
+    else src.img_lo = g.bc.kind[lo_side];
   }
+  if (f == nf) {
+    if (g.bc.kind[hi_side] == GKS_BC_PERIODIC) src.cr = 0;
+    else src.img_hi = g.bc.kind[hi_side];
+  }
+  src.hn = C.dn;
+  src.ht = C.dtan;
+  src.gamma = C.gamma;
+  src.uwt_lo = R(wall_t_velocity(g.bc, lo_side));
+  src.Tw_lo = R(g.bc.Tw[lo_side]);
+  src.uwt_hi = R(wall_t_velocity(g.bc, hi_side));
+  src.Tw_hi = R(g.bc.Tw[hi_side]);
 
-  // six cell averages around the face (ghost ring included), face frame
-  R avg[2][3][4];
-#pragma unroll
-  for (int m = 0; m < 2; ++m)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int ii = AX == 0 ? i - 1 + m : i - 1 + k;
-      const int jj = AX == 0 ? j - 1 + k : j - 1 + m;
-#pragma unroll
-      for (int v = 0; v < 4; ++v) avg[m][k][slot<AX>(v)] = R(U[ci(g, v, ii, jj)]);
-    }
-
-  FaceParams P;
-  P.gamma = g.gamma; P.mu = g.mu; P.Pr = g.Pr; P.tau_eps = g.tau_eps; P.tau_C = g.tau_C;
-  P.dn = AX == 0 ? g.dx : g.dy;
-  P.dtan = AX == 0 ? g.dy : g.dx;
   R Fl[4], Wm[4], Wp[4];
-  face_evolution<R>(P, L, Rt, avg, R(dt), Fl, Wm, Wp);
+  face_evolution<R>(C, src, R(c->dt), Fl, Wm, Wp);
 
   const size_t nfaces = (size_t)fx * fy, o = (size_t)j * fx + i;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     const int k = slot<AX>(v);
     F[(size_t)v * nfaces + o] = Fl[k];
-    Wn[(size_t)(v * 2 + 0) * nfaces + o] = Store<TW>::to((double)Wm[k]);
-    Wn[(size_t)(v * 2 + 1) * nfaces + o] = Store<TW>::to((double)Wp[k]);
+    Wn[(size_t)(v * 2 + 0) * nfaces + o] = TW(Wm[k]);
+    Wn[(size_t)(v * 2 + 1) * nfaces + o] = TW(Wp[k]);
   }
 }
 
 // ---------------------------------------------------------------------------
 // update, CFL bound of the new state, physical check
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double cell_bound(const Geo& g, const double w[4]) {
-  const double rho = w[0], u = w[1] / rho, v = w[2] / rho;
-  const double p = (g.gamma - 1.0) * (w[3] - 0.5 * rho * (u * u + v * v));
-  const double c = sqrt(g.gamma * p / rho);
-  double b = fmin(g.dx / (fabs(u) + c), g.dy / (fabs(v) + c));
+// inverse CFL bound max((|U|+c)/dx, (|V|+c)/dy) (and the viscous rate) of a state;
+// ok = rho > 0 and p > 0.  The bound itself is 1/inverse.
+template <class R>
+__device__ __forceinline__ R inv_bound(const Geo& g, const R w[4], bool& ok) {
+  const R ir = R(1) / w[0];
+  const R u = w[1] * ir, v = w[2] * ir;
+  const R p = R(g.gamma - 1.0) * (w[3] - R(0.5) * (w[1] * u + w[2] * v));
+  ok = w[0] > R(0) && p > R(0);
+  const R c = sqrt(R(g.gamma) * p * ir);
+  R inv = fmax((fabs(u) + c) * R(1.0 / g.dx), (fabs(v) + c) * R(1.0 / g.dy));
   if (g.viscous_dt && g.mu > 0.0) {
     const double h = fmin(g.dx, g.dy);
-    b = fmin(b, rho * h * h / (2.0 * g.mu * fmax(4.0 / 3.0, g.gamma / g.Pr)));
+    inv = fmax(inv, R(2.0 * g.mu * fmax(4.0 / 3.0, g.gamma / g.Pr) / (h * h)) * ir);
   }
-  return (rho > 0.0 && p > 0.0) ? b : 0.0;
+  return inv;
 }
 
-__device__ __forceinline__ void block_min_to(double b, unsigned long long* slot) {
-  __shared__ double red[32];
+// block maximum of inv, then the atomic minimum of the bound 1/inv
+template <class R>
+__device__ __forceinline__ void block_bound_to(R inv, unsigned long long* slot) {
+  __shared__ R red[32];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) b = fmin(b, __shfl_xor_sync(0xffffffffu, b, o));
-  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
-  const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  for (int o = 16; o > 0; o >>= 1) inv = fmax(inv, __shfl_xor_sync(0xffffffffu, inv, o));
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = t & 31, warp = t >> 5;
   const int nw = (blockDim.x * blockDim.y + 31) >> 5;
-  if (lane == 0) red[warp] = b;
+  if (lane == 0) red[warp] = inv;
   __syncthreads();
   if (warp == 0) {
-    b = lane < nw ? red[lane] : INFINITY;
+    inv = lane < nw ? red[lane] : R(0);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) b = fmin(b, __shfl_xor_sync(0xffffffffu, b, o));
-    if (lane == 0 && b < INFINITY) atomicMin(slot, dbits(b));
+    for (int o = 16; o > 0; o >>= 1) inv = fmax(inv, __shfl_xor_sync(0xffffffffu, inv, o));
+    if (lane == 0 && inv > R(0)) atomicMin(slot, dbits(1.0 / (double)inv));
   }
 }
 
-template <class TF>
-__global__ void __launch_bounds__(256) k_update(Geo g, double* U0, double* U1, const TF* __restrict__ Fx,
-                                                const TF* __restrict__ Fy, Ctrl* c) {
+template <class R>
+__global__ void __launch_bounds__(256) k_update(Geo g, double* U0, double* U1, float* F0, float* F1,
+                                                const R* __restrict__ Fx, const R* __restrict__ Fy, Ctrl* c) {
   if (c->skip) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int par = (int)(c->steps & 1);
   const double* __restrict__ U = par ? U1 : U0;
   double* __restrict__ Un = par ? U0 : U1;
-  double b = INFINITY;
+  float* __restrict__ Ufn = par ? F0 : F1;
+  R inv = R(0);
   if (i < g.nx && j < g.ny) {
     const int nx = g.nx, ny = g.ny;
     const size_t nfx = (size_t)ny * (nx + 1), nfy = (size_t)(ny + 1) * nx;
     const double idx = 1.0 / g.dx, idy = 1.0 / g.dy;
     double w[4];
+    R wr[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      const double fw = (double)Fx[v * nfx + (size_t)j * (nx + 1) + i];
-      const double fe = (double)Fx[v * nfx + (size_t)j * (nx + 1) + i + 1];
-      const double gs = (double)Fy[v * nfy + (size_t)j * nx + i];
-      const double gn = (double)Fy[v * nfy + (size_t)(j + 1) * nx + i];
-      w[v] = U[ci(g, v, i, j)] + (fw - fe) * idx + (gs - gn) * idy;
+      const R fw = Fx[v * nfx + (size_t)j * (nx + 1) + i];
+      const R fe = Fx[v * nfx + (size_t)j * (nx + 1) + i + 1];
+      const R gs = Fy[v * nfy + (size_t)j * nx + i];
+      const R gn = Fy[v * nfy + (size_t)(j + 1) * nx + i];
+      // Eq. finite in FP64: differences of the (possibly FP32) face fluxes are exact in
+      // FP64, so the face fluxes telescope and the update stays conservative
+      w[v] = U[ci(g, v, i, j)] + ((double)fw - (double)fe) * idx + ((double)gs - (double)gn) * idy;
       Un[ci(g, v, i, j)] = w[v];
+      wr[v] = R(w[v]);
+      if (Ufn) Ufn[ci(g, v, i, j)] = (float)wr[v];
     }
-    b = cell_bound(g, w);
-    if (!(b > 0.0) || !isfinite(w[3]) || !isfinite(w[1]) || !isfinite(w[2])) {
+    bool ok;
+    inv = inv_bound<R>(g, wr, ok);
+    if (!ok || !isfinite(w[0]) || !isfinite(w[1]) || !isfinite(w[2]) || !isfinite(w[3]) || !(inv < R(INFINITY))) {
       if (atomicCAS(&c->status, GKS_OK, GKS_ENONPHYSICAL) == GKS_OK) c->fail_step = c->steps;
-      b = INFINITY;
+      inv = R(0);
     }
   }
-  block_min_to(b, &c->dtbits[(c->steps & 1) ^ 1]);
+  block_bound_to<R>(inv, &c->dtbits[(c->steps & 1) ^ 1]);
 }
 
-// CFL bound of the current state (after set_state)
+// CFL bound of the current state (after set_state), in FP64
 __global__ void k_dtbound(Geo g, const double* U0, const double* U1, Ctrl* c) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int par = (int)(c->steps & 1);
   const double* U = par ? U1 : U0;
-  double b = INFINITY;
+  double inv = 0.0;
   if (i < g.nx && j < g.ny) {
     double w[4];
     for (int v = 0; v < 4; ++v) w[v] = U[ci(g, v, i, j)];
-    b = cell_bound(g, w);
-    if (!(b > 0.0)) {
+    bool ok;
+    inv = inv_bound<double>(g, w, ok);
+    if (!ok || !(inv < INFINITY)) {
       atomicCAS(&c->status, GKS_OK, GKS_ENONPHYSICAL);
-      b = INFINITY;
+      inv = 0.0;
     }
   }
-  block_min_to(b, &c->dtbits[par]);
+  block_bound_to<double>(inv, &c->dtbits[par]);
 }
 
 // ---------------------------------------------------------------------------
@@ -482,6 +556,7 @@ struct gks_handle {
   bool own_stream;
   int device;
   double* U[2];
+  float* Uf[2];      // FP32 mirror of U (FP32-bulk mode only)
   void* Wx[2];
   void* Wy[2];
   void* coef;
@@ -519,6 +594,37 @@ gks_status fail(gks_handle* h, gks_status s, const std::string& msg) {
 dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
 
 // ev (optional, 8 events): recorded before each of the seven kernels and after the last
+template <class R>
+FaceConst<R> fconst(const Geo& g, int axis) {
+  FaceParams P;
+  P.gamma = g.gamma; P.mu = g.mu; P.Pr = g.Pr; P.tau_eps = g.tau_eps; P.tau_C = g.tau_C;
+  P.dn = axis == 0 ? g.dx : g.dy;
+  P.dtan = axis == 0 ? g.dy : g.dx;
+  return face_const<R>(P);
+}
+
+// the padded cell-average arrays the compute-type kernels read
+template <class R> const R* cells(const gks_handle* h, int b);
+template <> const double* cells<double>(const gks_handle* h, int b) { return h->U[b]; }
+template <> const float* cells<float>(const gks_handle* h, int b) { return h->Uf[b]; }
+
+void launch_ghost(gks_handle* h, int force) {
+  const Geo& g = h->g;
+  const int per = 2 * (g.nx + 2) + 2 * g.ny;
+  k_ghost<<<(per + 127) / 128, 128, 0, h->stream>>>(g, h->U[0], h->U[1], h->Uf[0], h->Uf[1], h->ctrl, force);
+}
+
+template <class R, class TW>
+void launch_recon(gks_handle* h, int force) {
+  const Geo& g = h->g;
+  const dim3 b2(32, 8);
+  k_recon<R, TW><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(
+      g, cells<R>(h, 0), cells<R>(h, 1), (const TW*)h->Wx[0], (const TW*)h->Wx[1], (const TW*)h->Wy[0],
+      (const TW*)h->Wy[1], (R*)h->coef, R(g.dx), R(g.dy), R(g.weno_eps), R(g.weno_C), R(g.gamma - 1.0), h->ctrl,
+      force);
+}
+
+// ev (optional, 8 events): recorded before each of the seven kernels and after the last
 template <class R, class TW>
 gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double t_end, bool with_begin_end,
                                bool do_update, int force, cudaEvent_t* ev = nullptr) {
@@ -530,22 +636,22 @@ gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double 
   mark(0);
   if (with_begin_end) k_begin<<<1, 1, 0, s>>>(h->ctrl, cfl, dt_max, t_end);
   mark(1);
-  const int per = 2 * (g.nx + 2) + 2 * g.ny;
-  k_ghost<<<(per + 127) / 128, 128, 0, s>>>(g, h->U[0], h->U[1], h->ctrl, force);
+  launch_ghost(h, force);
   mark(2);
-  const dim3 b2(32, 8), bf(32, 4);
-  k_recon<R, TW><<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, h->U[0], h->U[1], (const TW*)h->Wx[0], (const TW*)h->Wx[1],
-                                                       (const TW*)h->Wy[0], (const TW*)h->Wy[1], (R*)h->coef,
-                                                       h->ctrl, force);
+  launch_recon<R, TW>(h, force);
   mark(3);
-  k_flux<0, R, TW><<<grid2(g.nx + 1, g.ny, bf), bf, 0, s>>>(g, h->U[0], h->U[1], (const R*)h->coef, (TW*)h->Wx[0],
-                                                             (TW*)h->Wx[1], (R*)h->Fx, h->ctrl, force);
+  const dim3 b2(32, 8), bf(32, 4);
+  k_flux<0, R, TW><<<grid2(g.nx + 1, g.ny, bf), bf, 0, s>>>(g, fconst<R>(g, 0), cells<R>(h, 0), cells<R>(h, 1),
+                                                             (const R*)h->coef, (TW*)h->Wx[0], (TW*)h->Wx[1],
+                                                             (R*)h->Fx, h->ctrl, force);
   mark(4);
-  k_flux<1, R, TW><<<grid2(g.nx, g.ny + 1, bf), bf, 0, s>>>(g, h->U[0], h->U[1], (const R*)h->coef, (TW*)h->Wy[0],
-                                                             (TW*)h->Wy[1], (R*)h->Fy, h->ctrl, force);
+  k_flux<1, R, TW><<<grid2(g.nx, g.ny + 1, bf), bf, 0, s>>>(g, fconst<R>(g, 1), cells<R>(h, 0), cells<R>(h, 1),
+                                                             (const R*)h->coef, (TW*)h->Wy[0], (TW*)h->Wy[1],
+                                                             (R*)h->Fy, h->ctrl, force);
   mark(5);
-  if (do_update) k_update<R><<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, h->U[0], h->U[1], (const R*)h->Fx,
-                                                                   (const R*)h->Fy, h->ctrl);
+  if (do_update)
+    k_update<R><<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, h->U[0], h->U[1], h->Uf[0], h->Uf[1], (const R*)h->Fx,
+                                                      (const R*)h->Fy, h->ctrl);
   mark(6);
   if (with_begin_end) k_end<<<1, 1, 0, s>>>(h->ctrl);
   mark(7);
@@ -602,8 +708,8 @@ gks_status load_state(gks_handle* h, const double* dU, const double* dWx, const 
   cudaStream_t s = h->stream;
   const dim3 b2(32, 8);
   k_scatter_U<<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, dU, h->U[0], h->U[1], h->ctrl, 1);
-  const int per = 2 * (g.nx + 2) + 2 * g.ny;
-  k_ghost<<<(per + 127) / 128, 128, 0, s>>>(g, h->U[0], h->U[1], h->ctrl, 1);
+  if (h->Uf[0]) k_mirror<<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, h->U[0], h->U[1], h->Uf[0], h->Uf[1], h->ctrl);
+  launch_ghost(h, 1);
   if (dWx) {
     k_copy_W<TW><<<(unsigned)((n_wx(g) + 255) / 256), 256, 0, s>>>(dWx, (TW*)h->Wx[0], (TW*)h->Wx[1], n_wx(g), h->ctrl, 1);
   } else {
@@ -710,6 +816,7 @@ gks_status gks_create(int nx, int ny, double Lx, double Ly, double gamma, double
   };
   for (int b = 0; b < 2; ++b) {
     alloc((void**)&h->U[b], 4 * g.plane * sizeof(double));
+    if (h->prec == GKS_FP32_BULK) alloc((void**)&h->Uf[b], 4 * g.plane * sizeof(float));
     alloc(&h->Wx[b], n_wx(g) * wsz);
     alloc(&h->Wy[b], n_wy(g) * wsz);
   }
@@ -726,6 +833,7 @@ gks_status gks_create(int nx, int ny, double Lx, double Ly, double gamma, double
   if (e == cudaSuccess)
     for (int b = 0; b < 2; ++b) {
       if (e == cudaSuccess) e = cudaMemsetAsync(h->U[b], 0, 4 * g.plane * sizeof(double), h->stream);
+      if (e == cudaSuccess && h->Uf[b]) e = cudaMemsetAsync(h->Uf[b], 0, 4 * g.plane * sizeof(float), h->stream);
       if (e == cudaSuccess) e = cudaMemsetAsync(h->Wx[b], 0, n_wx(g) * wsz, h->stream);
       if (e == cudaSuccess) e = cudaMemsetAsync(h->Wy[b], 0, n_wy(g) * wsz, h->stream);
     }
@@ -767,8 +875,9 @@ gks_status gks_set_state(gks_handle* h, const double* U, const double* Wx, const
   CK(cudaMemcpyAsync(h->staging, U, n_u(g) * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   const dim3 b2(32, 8);
   k_scatter_U<<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, h->staging, h->U[0], h->U[1], h->ctrl, 1);
-  const int per = 2 * (g.nx + 2) + 2 * g.ny;
-  k_ghost<<<(per + 127) / 128, 128, 0, h->stream>>>(g, h->U[0], h->U[1], h->ctrl, 1);
+  if (h->Uf[0])
+    k_mirror<<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], h->Uf[0], h->Uf[1], h->ctrl);
+  launch_ghost(h, 1);
   for (int axis = 0; axis < 2; ++axis) {
     const double* src = axis == 0 ? Wx : Wy;
     const size_t n = axis == 0 ? n_wx(g) : n_wy(g);
@@ -882,6 +991,7 @@ void gks_destroy(gks_handle* h) {
   destroy_graphs(h);
   for (int b = 0; b < 2; ++b) {
     cudaFree(h->U[b]);
+    cudaFree(h->Uf[b]);
     cudaFree(h->Wx[b]);
     cudaFree(h->Wy[b]);
   }
@@ -927,17 +1037,12 @@ gks_status gks_debug_recon(gks_handle* h, double* coef) {
   CK(cudaSetDevice(h->device));
   const Geo& g = h->g;
   const dim3 b2(32, 8);
-  const int per = 2 * (g.nx + 2) + 2 * g.ny;
-  k_ghost<<<(per + 127) / 128, 128, 0, h->stream>>>(g, h->U[0], h->U[1], h->ctrl, 1);
+  launch_ghost(h, 1);
   if (h->prec == GKS_FP64) {
-    k_recon<double, double><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(
-        g, h->U[0], h->U[1], (const double*)h->Wx[0], (const double*)h->Wx[1], (const double*)h->Wy[0],
-        (const double*)h->Wy[1], (double*)h->coef, h->ctrl, 1);
+    launch_recon<double, double>(h, 1);
     k_coef_out<double><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], (const double*)h->coef, h->staging, h->ctrl);
   } else {
-    k_recon<float, float><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(
-        g, h->U[0], h->U[1], (const float*)h->Wx[0], (const float*)h->Wx[1], (const float*)h->Wy[0],
-        (const float*)h->Wy[1], (float*)h->coef, h->ctrl, 1);
+    launch_recon<float, float>(h, 1);
     k_coef_out<float><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], (const float*)h->coef, h->staging, h->ctrl);
   }
   CK(cudaGetLastError());
@@ -1074,15 +1179,16 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
   // the control block must start from zero state; the rest is fully written before it is read
   k_noalloc_ctrl<<<1, 1, 0, s>>>(ctrl);
   k_scatter_U<<<grid2(nx, ny, b2), b2, 0, s>>>(g, dU, U0, U1, ctrl, 1);
-  k_ghost<<<(per + 127) / 128, 128, 0, s>>>(g, U0, U1, ctrl, 1);
+  k_ghost<<<(per + 127) / 128, 128, 0, s>>>(g, U0, U1, nullptr, nullptr, ctrl, 1);
   k_dtbound<<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, ctrl);
   k_begin<<<1, 1, 0, s>>>(ctrl, CFL, dt_max, INFINITY);
-  k_recon<double, double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, dWx, dWx_out, dWy, dWy_out, coef, ctrl, 0);
-  k_flux<0, double, double><<<grid2(nx + 1, ny, bf), bf, 0, s>>>(g, U0, U1, coef, const_cast<double*>(dWx), dWx_out,
-                                                                  Fx, ctrl, 0);
-  k_flux<1, double, double><<<grid2(nx, ny + 1, bf), bf, 0, s>>>(g, U0, U1, coef, const_cast<double*>(dWy), dWy_out,
-                                                                  Fy, ctrl, 0);
-  k_update<double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, Fx, Fy, ctrl);
+  k_recon<double, double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, dWx, dWx_out, dWy, dWy_out, coef, g.dx, g.dy,
+                                                            g.weno_eps, g.weno_C, g.gamma - 1.0, ctrl, 0);
+  k_flux<0, double, double><<<grid2(nx + 1, ny, bf), bf, 0, s>>>(g, fconst<double>(g, 0), U0, U1, coef,
+                                                                  const_cast<double*>(dWx), dWx_out, Fx, ctrl, 0);
+  k_flux<1, double, double><<<grid2(nx, ny + 1, bf), bf, 0, s>>>(g, fconst<double>(g, 1), U0, U1, coef,
+                                                                  const_cast<double*>(dWy), dWy_out, Fy, ctrl, 0);
+  k_update<double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, nullptr, nullptr, Fx, Fy, ctrl);
   k_end<<<1, 1, 0, s>>>(ctrl);
   k_scatter_U<<<grid2(nx, ny, b2), b2, 0, s>>>(g, dU_out, U0, U1, ctrl, 0);
   e = cudaGetLastError();

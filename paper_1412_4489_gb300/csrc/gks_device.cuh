@@ -110,17 +110,38 @@ GKS_FN void coef_mom(const R X[4], const Moments<R, NU, NV>& m, R o[4]) {
 
 // ---------------------------------------------------------------------------
 // Section 2.2: <a> = rho r for a expanded in psi has a closed-form solution
-// (the moment matrix of a Maxwellian is block structured about (U, V)).
-// N = K + 2.
+// (the moment matrix of a Maxwellian is block structured about (U, V)).  The
+// factors that depend only on the Maxwellian are formed once per Maxwellian.
 // ---------------------------------------------------------------------------
 template <class R>
-GKS_FN void solve(R U, R V, R lam, R N, const R r[4], R x[4]) {
+struct SolveK {
+  R U, V;
+  R l2;  // 2 lam
+  R c4;  // 4 lam^2 / N, N = K + 2
+  R s0;  // U^2 + V^2 - N / (2 lam)
+  R s1;  // (U^2 + V^2) / 2 + N / (4 lam)
+};
+
+template <class R>
+GKS_FN SolveK<R> solve_k(R U, R V, R lam, R N, R iN) {
+  SolveK<R> k;
   const R q2 = U * U + V * V;
-  const R x4 = R(4) * lam * lam / N *
-               (R(2) * r[3] - R(2) * U * r[1] - R(2) * V * r[2] + (q2 - N / (R(2) * lam)) * r[0]);
-  const R x3 = R(2) * lam * (r[2] - V * r[0]) - V * x4;
-  const R x2 = R(2) * lam * (r[1] - U * r[0]) - U * x4;
-  x[0] = r[0] - U * x2 - V * x3 - x4 * (R(0.5) * q2 + N / (R(4) * lam));
+  const R nl = N / lam;
+  k.U = U;
+  k.V = V;
+  k.l2 = R(2) * lam;
+  k.c4 = R(4) * lam * lam * iN;
+  k.s0 = q2 - R(0.5) * nl;
+  k.s1 = R(0.5) * q2 + R(0.25) * nl;
+  return k;
+}
+
+template <class R>
+GKS_FN void solve(const SolveK<R>& k, const R r[4], R x[4]) {
+  const R x4 = k.c4 * (R(2) * (r[3] - k.U * r[1] - k.V * r[2]) + k.s0 * r[0]);
+  const R x3 = k.l2 * (r[2] - k.V * r[0]) - k.V * x4;
+  const R x2 = k.l2 * (r[1] - k.U * r[0]) - k.U * x4;
+  x[0] = r[0] - k.U * x2 - k.V * x3 - x4 * k.s1;
   x[1] = x2;
   x[2] = x3;
   x[3] = x4;
@@ -152,7 +173,7 @@ GKS_FN void time_weights(R T, R tau, TimeW<R>& w) {
     f1 = t; f2 = t; f3 = R(0); f4 = R(0); f5 = R(2) * t; f6 = R(0);
 #pragma unroll
     for (int n = 3; n < Prec<R>::series_terms; ++n) {
-      t *= -x / R(n);
+      t *= -x * R(1.0 / n);
       f1 += t;
       f2 += R(n - 1) * t;
       f3 += R(n - 2) * t;
@@ -206,49 +227,48 @@ struct Coefs {
 };
 
 template <class R, int NU, int NV>
-GKS_FN void coef_systems(const Moments<R, NU, NV>& m, R rho, R U, R V, R lam, R N,
-                                             const R d[5][4], bool time_terms, bool second_time,
-                                             Coefs<R>& c) {
+GKS_FN void coef_systems(const Moments<R, NU, NV>& m, R rho, const SolveK<R>& sk, const R d[5][4],
+                         bool time_terms, bool second_time, Coefs<R>& c) {
   const R ir = R(1) / rho;
   R r[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = d[0][k] * ir;
-  solve(U, V, lam, N, r, c.a1);
+  solve(sk, r, c.a1);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = d[1][k] * ir;
-  solve(U, V, lam, N, r, c.a2);
+  solve(sk, r, c.a2);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = d[2][k] * ir;
-  solve(U, V, lam, N, r, c.Axx);
+  solve(sk, r, c.Axx);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = d[3][k] * ir;
-  solve(U, V, lam, N, r, c.Axy);
+  solve(sk, r, c.Axy);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = d[4][k] * ir;
-  solve(U, V, lam, N, r, c.Ayy);
+  solve(sk, r, c.Ayy);
   if (!time_terms) return;
   R p[4], q[4];
   coef_mom<1, 0>(c.a1, m, p);  // <A + a1 u + a2 v> = 0
   coef_mom<0, 1>(c.a2, m, q);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = -(p[k] + q[k]);
-  solve(U, V, lam, N, r, c.A);
+  solve(sk, r, c.A);
   coef_mom<1, 0>(c.Axx, m, p);  // <Axx u + Axy v + Atx> = 0
   coef_mom<0, 1>(c.Axy, m, q);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = -(p[k] + q[k]);
-  solve(U, V, lam, N, r, c.Atx);
+  solve(sk, r, c.Atx);
   coef_mom<1, 0>(c.Axy, m, p);  // <Axy u + Ayy v + Aty> = 0
   coef_mom<0, 1>(c.Ayy, m, q);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = -(p[k] + q[k]);
-  solve(U, V, lam, N, r, c.Aty);
+  solve(sk, r, c.Aty);
   if (!second_time) return;
   coef_mom<1, 0>(c.Atx, m, p);  // <Atx u + Aty v + Att> = 0
   coef_mom<0, 1>(c.Aty, m, q);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = -(p[k] + q[k]);
-  solve(U, V, lam, N, r, c.Att);
+  solve(sk, r, c.Att);
 }
 
 // The interface distribution grouped by velocity monomial: f = sum over
@@ -373,6 +393,47 @@ struct FaceParams {
   double dn, dtan;  // cell size normal to and along the face
 };
 
+// Per-launch constants of the face routine in the compute type
+template <class R>
+struct FaceConst {
+  R gamma, gm1, K, N, iN, dn, dtan, y2, mu, pr_fix, tau_eps, tau_C;
+  bool ns, prandtl;
+};
+
+template <class R>
+GKS_FN FaceConst<R> face_const(const FaceParams& P) {
+  FaceConst<R> c;
+  c.gamma = R(P.gamma);
+  c.gm1 = R(P.gamma - 1.0);
+  c.K = R((4.0 - 2.0 * P.gamma) / (P.gamma - 1.0));  // internal degrees of freedom, Section 2.1
+  c.N = R(2.0 / (P.gamma - 1.0));                     // K + 2
+  c.iN = R(0.5 * (P.gamma - 1.0));
+  c.dn = R(P.dn);
+  c.dtan = R(P.dtan);
+  c.y2 = R(P.dtan * P.dtan / 12.0);
+  c.mu = R(P.mu);
+  c.pr_fix = R(1.0 / P.Pr - 1.0);
+  c.tau_eps = R(P.tau_eps);
+  c.tau_C = R(P.tau_C);
+  c.ns = P.mu > 0.0;
+  c.prandtl = P.Pr != 1.0;
+  return c;
+}
+
+// A face source over the two sides and the six averages of one face, for
+// callers that hold them in arrays (the host operation count).
+template <class R>
+struct ArrayFaceSource {
+  const FaceState<R>* s[2];
+  const R (*a)[3][4];
+  GKS_FN void side(int k, FaceState<R>& out) const { out = *s[k]; }
+  GKS_FN void avg(R out[2][3][4]) const {
+    for (int m = 0; m < 2; ++m)
+      for (int n = 0; n < 3; ++n)
+        for (int v = 0; v < 4; ++v) out[m][n][v] = a[m][n][v];
+  }
+};
+
 // Wall images G(n, t) = Phi(P(-n, t)) of the inside face state (face frame).
 // kind 2: slip wall (normal momentum negated).  kind 3: isothermal no-slip with
 // tangential wall velocity uwt and wall temperature Tw: rho' = rho,
@@ -435,76 +496,74 @@ GKS_FN void wall_image(int kind, R gamma, R uwt, R Tw, const FaceState<R>& in, F
 }
 
 // ---------------------------------------------------------------------------
-// Section 2.2 at one face centre.  L, R: the two sides; avg[m][k]: the six
-// cell averages of Section 3.3 (m = 0 left, 1 right; k = tangential -1, 0, 1).
-// Outputs the time-integrated face-mean flux and the point values at the two
-// Gauss points (tangential -/+ sqrt(3)/6 dtan) at t = dt.
+// Section 2.2 at one face centre.  The two sides (value and derivatives in the
+// face frame) and the six cell averages of Section 3.3 (avg[m][k], m = 0 left,
+// 1 right; k = tangential -1, 0, 1) come from src.side(k, S) and src.avg(a),
+// which are called where they are needed so that they need not stay live in
+// registers.  Outputs the time-integrated face-mean flux and the point values
+// at the two Gauss points (tangential -/+ sqrt(3)/6 dtan) at t = dt.
 // ---------------------------------------------------------------------------
-template <class R>
-GKS_FN void face_evolution(const FaceParams& P, const FaceState<R>& L,
-                                               const FaceState<R>& Rs, const R avg[2][3][4], R dt,
-                                               R F[4], R Wm[4], R Wp[4]) {
-  const R gamma = R(P.gamma), gm1 = gamma - R(1);
-  const R K = (R(4) - R(2) * gamma) / gm1;
-  const R N = K + R(2);
-  const R dn = R(P.dn), dtan = R(P.dtan);
-  const R y2 = dtan * dtan / R(12);
-  const bool ns = P.mu > 0.0;
-
-  R rl, ul, vl, pl, rr, ur, vr, pr;
-  prim(L.w[0], gm1, rl, ul, vl, pl);
-  prim(Rs.w[0], gm1, rr, ur, vr, pr);
-  const R laml = R(0.5) * rl / pl, lamr = R(0.5) * rr / pr;
-
+template <class R, class Src>
+GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], R Wm[4], R Wp[4]) {
+  R rs[2], us[2], vs[2], ls[2], ps[2];
+  R U0[4] = {R(0), R(0), R(0), R(0)};
   // Eq. compatibility2: U0 = rho_l <psi>_{u>0} + rho_r <psi>_{u<0}
-  R U0[4];
-  {
-    Moments<R, 4, 3> ml, mr;
-    moments(ul, vl, laml, K, +1, ml);
-    moments(ur, vr, lamr, K, -1, mr);
-    R a[4], b[4];
-    psi_mom<0, 0>(ml, a);
-    psi_mom<0, 0>(mr, b);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) U0[k] = rl * a[k] + rr * b[k];
+  for (int k = 0; k < 2; ++k) {
+    FaceState<R> S;
+    src.side(k, S);
+    prim(S.w[0], C.gm1, rs[k], us[k], vs[k], ps[k]);
+    ls[k] = R(0.5) * rs[k] / ps[k];
+    Moments<R, 4, 3> m;
+    moments(us[k], vs[k], ls[k], C.K, k == 0 ? +1 : -1, m);
+    R a[4];
+    psi_mom<0, 0>(m, a);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) U0[v] += rs[k] * a[v];
   }
   R r0, u0, v0, p0;
-  prim(U0, gm1, r0, u0, v0, p0);
+  prim(U0, C.gm1, r0, u0, v0, p0);
   const R lam0 = R(0.5) * r0 / p0;
 
   // Section 4: collision time
-  const R jump = fabs((pl - pr) / (pl + pr)) * dt;
-  const R tau = ns ? R(P.mu) / p0 + jump : R(P.tau_eps) * dt + R(P.tau_C) * jump;
-  const R tn = ns ? tau : R(0);
+  const R jump = fabs((ps[0] - ps[1]) / (ps[0] + ps[1])) * dt;
+  const R tau = C.ns ? C.mu / p0 + jump : C.tau_eps * dt + C.tau_C * jump;
+  const R tn = C.ns ? tau : R(0);
 
   TimeW<R> tw;
   time_weights(dt, tau, tw);
 
   R Fl[4] = {0, 0, 0, 0}, P0[4] = {0, 0, 0, 0}, P1[4] = {0, 0, 0, 0}, Mn[4] = {0, 0, 0, 0};
-  const bool prandtl = P.Pr != 1.0;
 
   // ---- equilibrium part, Eq. dis1, with g0 and the polynomial of Section 3.3 ----
   {
     R d[5][4];
+    {
+      R avg[2][3][4];
+      src.avg(avg);
+      const R i4n = R(1) / (R(4) * C.dn), i4t = R(1) / (R(4) * C.dtan);
+      const R i8n2 = R(1) / (R(8) * C.dn * C.dn), i2nt = R(1) / (R(2) * C.dn * C.dtan);
+      const R i2t2 = R(1) / (R(2) * C.dtan * C.dtan);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const R um = avg[0][0][k], uc = avg[0][1][k], up = avg[0][2][k];
-      const R wm = avg[1][0][k], wc = avg[1][1][k], wp = avg[1][2][k];
-      d[0][k] = ((wp - up) + R(2) * (wc - uc) + (wm - um)) / (R(4) * dn);                // b2
-      d[1][k] = (wp - wm + up - um) / (R(4) * dtan);                                       // b3
-      d[2][k] = (R(26) * (wc + uc) - (wp + up + wm + um) - R(48) * U0[k]) / (R(8) * dn * dn);  // b4
-      d[3][k] = (wp - up - wm + um) / (R(2) * dn * dtan);                                  // b6
-      d[4][k] = (wp - R(2) * wc + wm + up - R(2) * uc + um) / (R(2) * dtan * dtan);         // b5
+      for (int k = 0; k < 4; ++k) {
+        const R um = avg[0][0][k], uc = avg[0][1][k], up = avg[0][2][k];
+        const R wm = avg[1][0][k], wc = avg[1][1][k], wp = avg[1][2][k];
+        d[0][k] = ((wp - up) + R(2) * (wc - uc) + (wm - um)) * i4n;                // b2
+        d[1][k] = (wp - wm + up - um) * i4t;                                       // b3
+        d[2][k] = (R(26) * (wc + uc) - (wp + up + wm + um) - R(48) * U0[k]) * i8n2;  // b4
+        d[3][k] = (wp - up - wm + um) * i2nt;                                      // b6
+        d[4][k] = (wp - R(2) * wc + wm + up - R(2) * uc + um) * i2t2;               // b5
+      }
     }
     Moments<R, 8, 7> m;
-    moments(u0, v0, lam0, K, 0, m);
+    moments(u0, v0, lam0, C.K, 0, m);
     Coefs<R> c;
-    coef_systems(m, r0, u0, v0, lam0, N, d, true, true, c);
+    coef_systems(m, r0, solve_k(u0, v0, lam0, C.N, C.iN), d, true, true, c);
     Groups<R> g;
-    hydro_groups(c, tw.I, y2, g);
+    hydro_groups(c, tw.I, C.y2, g);
     add_flux(g, m, r0, Fl);
-    if (prandtl) add_point(g, m, r0, Mn);
-    hydro_groups(c, tw.E, y2, g);
+    if (C.prandtl) add_point(g, m, r0, Mn);
+    hydro_groups(c, tw.E, C.y2, g);
     add_point(g, m, r0, P0);
     R Y1[4], Yu[4], Yv[4];
 #pragma unroll
@@ -519,31 +578,33 @@ GKS_FN void face_evolution(const FaceParams& P, const FaceState<R>& L,
   // ---- kinetic part, Eq. dis2, for both sides ----
 #pragma unroll 1
   for (int side = 0; side < 2; ++side) {
-    const FaceState<R>& S = side == 0 ? L : Rs;
-    const R rho = side == 0 ? rl : rr, U = side == 0 ? ul : ur, V = side == 0 ? vl : vr;
-    const R lam = side == 0 ? laml : lamr;
-    R d[5][4];
-#pragma unroll
-    for (int s = 0; s < 5; ++s)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) d[s][k] = S.w[s + 1][k];
+    const R rho = rs[side], U = us[side], V = vs[side], lam = ls[side];
     Coefs<R> c;
     {
+      R d[5][4];
+      {
+        FaceState<R> S;
+        src.side(side, S);
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) d[q][k] = S.w[q + 1][k];
+      }
       Moments<R, 6, 6> mf;  // full-space moments fix the coefficients of g_k
-      moments(U, V, lam, K, 0, mf);
-      coef_systems(mf, rho, U, V, lam, N, d, ns, false, c);
+      moments(U, V, lam, C.K, 0, mf);
+      coef_systems(mf, rho, solve_k(U, V, lam, C.N, C.iN), d, C.ns, false, c);
     }
-    if (!ns) {
+    if (!C.ns) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) c.A[k] = c.Atx[k] = c.Aty[k] = R(0);
     }
     Moments<R, 8, 7> mh;
-    moments(U, V, lam, K, side == 0 ? +1 : -1, mh);
+    moments(U, V, lam, C.K, side == 0 ? +1 : -1, mh);
     Groups<R> g;
-    kinetic_groups(c, tw.I, y2, tn, g);
+    kinetic_groups(c, tw.I, C.y2, tn, g);
     add_flux(g, mh, rho, Fl);
-    if (prandtl) add_point(g, mh, rho, Mn);
-    kinetic_groups(c, tw.E, y2, tn, g);
+    if (C.prandtl) add_point(g, mh, rho, Mn);
+    kinetic_groups(c, tw.E, C.y2, tn, g);
     add_point(g, mh, rho, P0);
     R Y1[4], Yu[4], Yv[4];
     const R wy = -tn * tw.E[7] - tw.E[9];
@@ -559,13 +620,13 @@ GKS_FN void face_evolution(const FaceParams& P, const FaceState<R>& L,
   // Prandtl-number fix: energy flux += (1/Pr - 1) q, q the time-integrated
   // face-mean heat flux (1/2) int (u-U0)((u-U0)^2+(v-V0)^2+xi^2) f, written with the
   // flux and the time-integrated conservative moments.
-  if (prandtl) {
+  if (C.prandtl) {
     const R q2 = u0 * u0 + v0 * v0;
     const R q = Fl[3] - u0 * Fl[1] - v0 * Fl[2] + (R(0.5) * q2 + u0 * u0) * Fl[0] - u0 * Mn[3] +
                 u0 * v0 * Mn[2] - R(0.5) * u0 * q2 * Mn[0];
-    Fl[3] += (R(1) / R(P.Pr) - R(1)) * q;
+    Fl[3] += C.pr_fix * q;
   }
-  const R yg = R(0.28867513459481287) * dtan;  // sqrt(3)/6
+  const R yg = R(0.28867513459481287) * C.dtan;  // sqrt(3)/6
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     F[k] = Fl[k];

@@ -83,7 +83,13 @@ void count_face(const double* L, const double* R, const double* avg, double dn, 
   FP.gamma = gamma; FP.mu = mu; FP.Pr = Pr; FP.tau_eps = tau_eps; FP.tau_C = tau_C;
   FP.dn = dn; FP.dtan = dtan;
   N F[4], Wm[4], Wp[4];
-  gks::face_evolution<N>(FP, SL, SR, av, N(dt), F, Wm, Wp);
+  gks::ArrayFaceSource<N> src;
+  src.s[0] = &SL;
+  src.s[1] = &SR;
+  src.a = av;
+  const gks::FaceConst<N> C = gks::face_const<N>(FP);
+  opc::C = opc::Counts{};  // per-launch constants are not per-face work
+  gks::face_evolution<N>(C, src, N(dt), F, Wm, Wp);
 }
 
 template <class R>
@@ -111,7 +117,6 @@ gks_status gks_face_op_count(const double* L, const double* R, const double* avg
                              double gamma, double mu, double Pr, double tau_eps, double tau_C, int precision,
                              long long* counts) {
   if (!L || !R || !avg || !counts || !(dt > 0) || !(dn > 0) || !(dtan > 0)) return GKS_EINVAL;
-  memset(&opc::C, 0, sizeof(opc::C));
   if (precision == GKS_FP64)
     count_face<0>(L, R, avg, dn, dtan, dt, gamma, mu, Pr, tau_eps, tau_C);
   else if (precision == GKS_FP32_BULK)
