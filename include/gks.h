@@ -34,11 +34,18 @@
  * to the *_device calls must hold FP64 arrays of the layouts above on the
  * handle's device.
  *
+ * Positivity fallback (the paper is silent on positivity): when the update
+ * makes a cell non-physical (rho <= 0, p <= 0 or not finite), every face of
+ * that cell is evolved again with the collisionless first-order flux of the two
+ * cell averages (the tau -> infinity limit of the scheme) and the update is
+ * redone; if a cell is still non-physical, every face of the grid gets that
+ * flux for this step.
+ *
  * Errors are returned as gks_status, never by aborting; gks_last_error gives a
- * message.  A step whose new state is not physical (rho <= 0, p <= 0 or not
- * finite in some cell) is not taken: the state stays the one before the step and
- * GKS_ENONPHYSICAL is reported (by gks_step, or by the next gks_sync /
- * gks_get_state after gks_advance).
+ * message.  A step whose new state is still not physical after the fallback is
+ * not taken: the state stays the one before the step and GKS_ENONPHYSICAL is
+ * reported (by gks_step, or by the next gks_sync / gks_get_state after
+ * gks_advance).
  */
 #ifndef GKS_H
 #define GKS_H
@@ -161,10 +168,79 @@ int gks_launches_per_step(const gks_handle* h);
 
 /* Takes one step like gks_step(h, CFL, +inf, NULL) with CUDA events recorded on
  * the handle's stream between its kernels, and writes the duration in ms of
- * each of the seven kernels to ms[0..6], in launch order: begin, ghost fill,
- * reconstruction, x-face evolution, y-face evolution, update, end.
+ * each of the nine kernels to ms[0..8], in launch order: begin, ghost fill,
+ * reconstruction, x-face evolution, y-face evolution, update, the two update
+ * passes of the positivity fallback (no work unless a cell needed it), end.
  * Synchronous; returns the status of the step. */
 gks_status gks_profile_step(gks_handle* h, double CFL, float* ms);
+
+/* ---- batched form: many independent grids in one persistent launch ----
+ *
+ * Grids of uneven sizes, each with its own gamma, mu, Pr, boundary conditions,
+ * time step and time, advance together: gks_batch_step queues ONE cooperative
+ * kernel that runs nsteps steps of every grid (the phases of Section 2-3 over
+ * flat work lists of 128-element tiles from all grids, separated by device-wide
+ * barriers), captured once into a CUDA graph and replayed.  Each grid takes
+ * dt = CFL * (its own CFL bound), as gks_step does.  Every barrier wait is
+ * bounded in time: a wait that runs out abandons the call and gks_batch_sync
+ * returns GKS_ETIMEOUT (the batch must then be set up again with
+ * gks_batch_set_state).  A grid whose new state is not physical stops (its
+ * last good state is kept) and gks_batch_sync returns GKS_ENONPHYSICAL.
+ * Host arrays are FP64 in the per-grid layouts of the single-grid API. */
+typedef struct {
+  int nx, ny;                /* >= 2 */
+  double Lx, Ly, gamma, Pr, mu;
+  gks_bc bc[4];              /* x-low, x-high, y-low, y-high */
+} gks_grid_desc;
+
+typedef struct gks_batch gks_batch;
+
+/* Creates a batch of n grids (device memory for all of them is allocated here).
+ * opt may be NULL; its precision selects FP64 or FP32-bulk for every grid. */
+gks_status gks_batch_create(int n, const gks_grid_desc* grids, const gks_options* opt,
+                            void* cuda_stream, gks_batch** out);
+
+/* Copies grid g's state from host memory (all three arrays required); t is
+ * its time.  Synchronous. */
+gks_status gks_batch_set_state(gks_batch* b, int g, const double* U, const double* Wx,
+                               const double* Wy, double t);
+
+/* Copies grid g's state to host memory (any pointer may be NULL).  Synchronous;
+ * returns the grid's status. */
+gks_status gks_batch_get_state(gks_batch* b, int g, double* U, double* Wx, double* Wy, double* t,
+                               long long* steps);
+
+/* Queues nsteps steps of every grid as one persistent launch (graph replay). */
+gks_status gks_batch_step(gks_batch* b, int nsteps, double CFL);
+
+/* Waits; steps_min/steps_max (may be NULL) receive the range of per-grid step
+ * counts.  Returns GKS_ETIMEOUT, GKS_ENONPHYSICAL or GKS_OK. */
+gks_status gks_batch_sync(gks_batch* b, long long* steps_min, long long* steps_max);
+
+/* Time, step count and status of grid g (synchronous). */
+gks_status gks_batch_grid_info(gks_batch* b, int g, double* t, long long* steps, int* status);
+
+/* Sets the face-phase tile width (16, 32, 64 or 128 faces per row of a
+ * 128-face tile) and the resident blocks per SM of the persistent kernel. */
+gks_status gks_batch_configure(gks_batch* b, int face_tile_width, int blocks_per_sm);
+
+/* Autotuner: times trial_steps steps for every tile width and every feasible
+ * blocks-per-SM on the batch itself (the state is saved and restored), keeps
+ * the fastest and reports it (any output may be NULL; best_ms per step). */
+gks_status gks_batch_autotune(gks_batch* b, double CFL, int trial_steps, int* face_tile_width,
+                              int* blocks_per_sm, float* best_ms);
+
+/* Limit of every device barrier wait, in seconds (default 2).
+ * test_skip_block >= 0 makes that block of the persistent kernel skip its
+ * barrier arrivals -- a test hook that makes every other wait run out, so that
+ * the timeout path can be exercised; -1 disables it. */
+gks_status gks_batch_set_wait_limit(gks_batch* b, double seconds, int test_skip_block);
+
+/* Total cells of all grids; kernel launches per gks_batch_step call. */
+long long gks_batch_cells(const gks_batch* b);
+int gks_batch_launches_per_call(const gks_batch* b);
+void gks_batch_destroy(gks_batch* b);
+const char* gks_batch_last_error(const gks_batch* b);
 
 /* ---- measurement helpers ---- */
 

@@ -64,6 +64,7 @@ def lib():
         L.orc_time_integrals.argtypes = [D, D, dp]
         L.orc_face.argtypes = [P(Params), dp, dp, dp, D, D, D, dp, dp, dp]
         L.orc_bc_image.argtypes = [P(Params), ctypes.c_int, D, D, dp, dp]
+        L.orc_face_first_order.argtypes = [P(Params), dp, dp, D, D, D, dp, dp, dp]
         L.orc_recon_cell.argtypes = [P(Params), dp, dp, dp, D, D, dp]
         L.orc_dt2d.argtypes = [P(Params), ctypes.c_int, ctypes.c_int, D, D, dp, D, D, ctypes.c_int]
         L.orc_dt2d.restype = D
@@ -135,6 +136,15 @@ def face(P, L, R, avg, dn, dtan, dt):
     avg = np.ascontiguousarray(avg, dtype=np.float64).reshape(2, 3, 4)
     F, W, dbg = np.zeros(4), np.zeros((2, 4)), np.zeros(64)
     lib().orc_face(ctypes.byref(P), _p(L), _p(R), _p(avg), dn, dtan, dt, _p(F), _p(W), _p(dbg))
+    return F, W, dbg
+
+
+def face_first_order(P, L, R, dn, dtan, dt):
+    """First-order evolution of the positivity fallback: L, R used as constant states."""
+    L = np.ascontiguousarray(L, dtype=np.float64).reshape(6, 4)
+    R = np.ascontiguousarray(R, dtype=np.float64).reshape(6, 4)
+    F, W, dbg = np.zeros(4), np.zeros((2, 4)), np.zeros(64)
+    lib().orc_face_first_order(ctypes.byref(P), _p(L), _p(R), dn, dtan, dt, _p(F), _p(W), _p(dbg))
     return F, W, dbg
 
 

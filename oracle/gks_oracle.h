@@ -73,6 +73,13 @@ void orc_face(const orc_params* P, const double L[6][4], const double R[6][4],
               const double avg[2][3][4], double dn, double dtan, double dt,
               double Fhat[4], double Wg[2][4], double* dbg);
 
+/* The evolution of the positivity fallback: the collisionless first-order
+ * limit for constant states L[0], R[0] (derivatives ignored).  Outputs as
+ * orc_face; dbg[0..3] = U0. */
+void orc_face_first_order(const orc_params* P, const double L[6][4], const double R[6][4],
+                          double dn, double dtan, double dt, double Fhat[4], double Wg[2][4],
+                          double* dbg);
+
 /* Same for a face whose outside state is the boundary image of the inside one
  * (outflow continuation or a wall mirror).  inside_right = 1 when the inside
  * cell lies at n>0.  The face frame's tangential wall velocity is u_wall_t. */
@@ -104,8 +111,11 @@ void orc_flux2d(const orc_params* P, int nx, int ny, double Lx, double Ly, const
                 const double* U, const double* Wx, const double* Wy, double dt,
                 double* Fx, double* Fy, double* Wx_new, double* Wy_new);
 
-/* One full step in place.  bc order: x-low, x-high, y-low, y-high.  Returns
- * ORC_OK or ORC_ENONPHYSICAL (state left unchanged). */
+/* One full step in place.  bc order: x-low, x-high, y-low, y-high.  If the
+ * update makes cells non-physical, their faces are evolved again with the
+ * collisionless first-order flux and the update is redone; if cells are still
+ * non-physical, every face of the grid gets that flux.  Returns ORC_OK or
+ * ORC_ENONPHYSICAL (still not physical; state left unchanged). */
 int orc_step2d(const orc_params* P, int nx, int ny, double Lx, double Ly, const orc_bc bc[4],
                double CFL, double dt_max, int viscous_dt, double* U, double* Wx, double* Wy,
                double* dt_out);

@@ -359,9 +359,12 @@ static void cons_prim(const double w[4], double gamma, double* rho, double* u, d
   *p = (gamma - 1.0) * (w[3] - 0.5 * w[0] * (*u * *u + *v * *v));
 }
 
-void orc_face(const orc_params* P, const double L[6][4], const double R[6][4],
-              const double avg[2][3][4], double dn, double dtan, double dt,
-              double Fhat[4], double Wg[2][4], double* dbg) {
+/* first_order = 1: the first-order evolution used by the positivity fallback of
+ * the update -- both sides are constant (their derivatives are ignored) and the
+ * equilibrium state has no slopes (b2..b6 = 0) */
+static void face_impl(const orc_params* P, const double L[6][4], const double R[6][4],
+                      const double avg[2][3][4], double dn, double dtan, double dt,
+                      double Fhat[4], double Wg[2][4], double* dbg, int first_order) {
   const double gam = P->gamma;
   const double K = (4.0 - 2.0 * gam) / (gam - 1.0); /* Section 2.1 */
   maxw gl, gr, g0;
@@ -390,6 +393,7 @@ void orc_face(const orc_params* P, const double L[6][4], const double R[6][4],
     b[4][k] = (26.0 * (v0 + u0) - (vp1 + up1 + vm1 + um1) - 48.0 * U0[k]) / (8.0 * dn * dn);
     b[5][k] = (vp1 - 2.0 * v0 + vm1 + up1 - 2.0 * u0 + um1) / (2.0 * dtan * dtan);
     b[6][k] = (vp1 - up1 - vm1 + um1) / (2.0 * dn * dtan);
+    if (first_order) b[2][k] = b[3][k] = b[4][k] = b[5][k] = b[6][k] = 0.0;
   }
 
   /* Section 4: collision time */
@@ -408,7 +412,10 @@ void orc_face(const orc_params* P, const double L[6][4], const double R[6][4],
     double d0[5][4], dl[5][4], dr[5][4];
     for (int k = 0; k < 4; ++k) {
       d0[0][k] = b[2][k]; d0[1][k] = b[3][k]; d0[2][k] = b[4][k]; d0[3][k] = b[6][k]; d0[4][k] = b[5][k];
-      for (int s = 0; s < 5; ++s) { dl[s][k] = L[s + 1][k]; dr[s][k] = R[s + 1][k]; }
+      for (int s = 0; s < 5; ++s) {
+        dl[s][k] = first_order ? 0.0 : L[s + 1][k];
+        dr[s][k] = first_order ? 0.0 : R[s + 1][k];
+      }
     }
     coefs_solve(&g0, d0, &c0);
     coefs_solve(&gl, dl, &cl);
@@ -494,6 +501,42 @@ void orc_face(const orc_params* P, const double L[6][4], const double R[6][4],
       for (int k = 0; k < 4; ++k) dbg[5 + (s - 2) * 4 + k] = b[s][k];
     dbg[25] = q;
   }
+}
+
+void orc_face(const orc_params* P, const double L[6][4], const double R[6][4],
+              const double avg[2][3][4], double dn, double dtan, double dt,
+              double Fhat[4], double Wg[2][4], double* dbg) {
+  face_impl(P, L, R, avg, dn, dtan, dt, Fhat, Wg, dbg, 0);
+}
+
+/* The fallback evolution: the collisionless (tau -> infinity) limit of Eq.
+ * integral for constant states, f = f0: the flux over [0, dt] is
+ * dt (rho_l <u psi>_{u>0,l} + rho_r <u psi>_{u<0,r}) and the point values are
+ * U0 of Eq. compatibility2 at every point of the face. */
+void orc_face_first_order(const orc_params* P, const double L[6][4], const double R[6][4],
+                          double dn, double dtan, double dt, double Fhat[4], double Wg[2][4],
+                          double* dbg) {
+  (void)dn;
+  (void)dtan;
+  const double gam = P->gamma;
+  const double K = (4.0 - 2.0 * gam) / (gam - 1.0);
+  maxw gl, gr;
+  maxw_from_cons(&gl, L[0], K);
+  maxw_from_cons(&gr, R[0], K);
+  poly one, u;
+  poly_mono(1.0, 0, 0, &one);
+  poly_mono(1.0, 1, 0, &u);
+  double hl[4], hr[4], fl[4], fr[4];
+  maxw_mom4(&gl, 1, &one, hl);
+  maxw_mom4(&gr, 2, &one, hr);
+  maxw_mom4(&gl, 1, &u, fl);
+  maxw_mom4(&gr, 2, &u, fr);
+  for (int k = 0; k < 4; ++k) {
+    Fhat[k] = dt * (gl.rho * fl[k] + gr.rho * fr[k]);
+    Wg[0][k] = Wg[1][k] = gl.rho * hl[k] + gr.rho * hr[k];
+  }
+  if (dbg)
+    for (int k = 0; k < 4; ++k) dbg[k] = Wg[0][k];
 }
 
 /* ------------------------------------------------------------------ */
@@ -896,20 +939,48 @@ void orc_flux2d(const orc_params* P, int nx, int ny, double Lx, double Ly, const
   free(coef);
 }
 
-int orc_step2d(const orc_params* P, int nx, int ny, double Lx, double Ly, const orc_bc bc[4],
-               double CFL, double dt_max, int viscous_dt, double* U, double* Wx, double* Wy,
-               double* dt_out) {
-  const double dx = Lx / nx, dy = Ly / ny;
-  const double dt = orc_dt2d(P, nx, ny, Lx, Ly, U, CFL, dt_max, viscous_dt);
-  const size_t nU = (size_t)4 * nx * ny, nWx = (size_t)8 * ny * (nx + 1), nWy = (size_t)8 * (ny + 1) * nx;
-  double* Fx = (double*)malloc(sizeof(double) * 4 * ny * (nx + 1));
-  double* Fy = (double*)malloc(sizeof(double) * 4 * (ny + 1) * nx);
-  double* Wxn = (double*)malloc(sizeof(double) * nWx);
-  double* Wyn = (double*)malloc(sizeof(double) * nWy);
-  double* Un = (double*)malloc(sizeof(double) * nU);
-  orc_flux2d(P, nx, ny, Lx, Ly, bc, U, Wx, Wy, dt, Fx, Fy, Wxn, Wyn);
-  /* Eq. finite with the analytically time-integrated, face-averaged fluxes */
-  int bad = 0;
+/* state of cell (i, j) as a constant face state (value only), face frame */
+static void const_state(const double* U, int nx, int ny, int i, int j, int axis, double S[6][4]) {
+  double w[4];
+  memset(S, 0, sizeof(double) * 24);
+  for (int v = 0; v < 4; ++v) w[v] = U[UI(v, j, i)];
+  to_frame(axis, w, S[0]);
+}
+
+/* first-order evolution at x-face (i, j) (axis 0) or y-face (i, j) (axis 1) */
+static void face_first_order(const orc_params* P, int nx, int ny, double dx, double dy, const orc_bc bc[4],
+                             const double* U, int axis, int i, int j, double dt, double F[4], double Wg[2][4]) {
+  double L[6][4], R[6][4], Ff[4], Wf[2][4];
+  const int f = axis == 0 ? i : j, nf = axis == 0 ? nx : ny;
+  const orc_bc* blo = &bc[axis == 0 ? 0 : 2];
+  const orc_bc* bhi = &bc[axis == 0 ? 1 : 3];
+  int cl = f - 1, cr = f;
+  if (f == 0 && blo->kind == ORC_BC_PERIODIC) cl = nf - 1;
+  if (f == nf && bhi->kind == ORC_BC_PERIODIC) cr = 0;
+#define CELL_I(n) (axis == 0 ? (n) : i)
+#define CELL_J(n) (axis == 0 ? j : (n))
+  if (f == 0 && blo->kind != ORC_BC_PERIODIC) {
+    const_state(U, nx, ny, CELL_I(cr), CELL_J(cr), axis, R);
+    orc_bc_image(P, blo->kind, wall_tangent_velocity(blo, axis), blo->T_wall, R, L);
+  } else if (f == nf && bhi->kind != ORC_BC_PERIODIC) {
+    const_state(U, nx, ny, CELL_I(cl), CELL_J(cl), axis, L);
+    orc_bc_image(P, bhi->kind, wall_tangent_velocity(bhi, axis), bhi->T_wall, L, R);
+  } else {
+    const_state(U, nx, ny, CELL_I(cl), CELL_J(cl), axis, L);
+    const_state(U, nx, ny, CELL_I(cr), CELL_J(cr), axis, R);
+  }
+#undef CELL_I
+#undef CELL_J
+  orc_face_first_order(P, L, R, axis == 0 ? dx : dy, axis == 0 ? dy : dx, dt, Ff, Wf, NULL);
+  to_frame(axis, Ff, F);
+  to_frame(axis, Wf[0], Wg[0]);
+  to_frame(axis, Wf[1], Wg[1]);
+}
+
+/* Eq. finite into Un; returns the number of non-physical cells and marks them */
+static int update_cells(const orc_params* P, int nx, int ny, double dx, double dy, const double* U,
+                        const double* Fx, const double* Fy, double* Un, unsigned char* bad) {
+  int nbad = 0;
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       double w[4];
@@ -923,16 +994,73 @@ int orc_step2d(const orc_params* P, int nx, int ny, double Lx, double Ly, const 
       }
       double r, u, vv, p;
       cons_prim(w, P->gamma, &r, &u, &vv, &p);
-      if (!(r > 0.0) || !(p > 0.0) || !isfinite(w[3])) bad = 1;
+      const int b = !(r > 0.0) || !(p > 0.0) || !isfinite(w[0]) || !isfinite(w[1]) || !isfinite(w[2]) ||
+                    !isfinite(w[3]);
+      bad[(size_t)j * nx + i] = (unsigned char)b;
+      nbad += b;
     }
-  if (!bad) {
+  return nbad;
+}
+
+int orc_step2d(const orc_params* P, int nx, int ny, double Lx, double Ly, const orc_bc bc[4],
+               double CFL, double dt_max, int viscous_dt, double* U, double* Wx, double* Wy,
+               double* dt_out) {
+  const double dx = Lx / nx, dy = Ly / ny;
+  const double dt = orc_dt2d(P, nx, ny, Lx, Ly, U, CFL, dt_max, viscous_dt);
+  const size_t nU = (size_t)4 * nx * ny, nWx = (size_t)8 * ny * (nx + 1), nWy = (size_t)8 * (ny + 1) * nx;
+  double* Fx = (double*)malloc(sizeof(double) * 4 * ny * (nx + 1));
+  double* Fy = (double*)malloc(sizeof(double) * 4 * (ny + 1) * nx);
+  double* Wxn = (double*)malloc(sizeof(double) * nWx);
+  double* Wyn = (double*)malloc(sizeof(double) * nWy);
+  double* Un = (double*)malloc(sizeof(double) * nU);
+  unsigned char* bad = (unsigned char*)malloc((size_t)nx * ny);
+  orc_flux2d(P, nx, ny, Lx, Ly, bc, U, Wx, Wy, dt, Fx, Fy, Wxn, Wyn);
+  /* Eq. finite with the analytically time-integrated, face-averaged fluxes */
+  int nbad = update_cells(P, nx, ny, dx, dy, U, Fx, Fy, Un, bad);
+  /* positivity fallback (the paper is silent on positivity): if the update makes
+   * some cell non-physical, every face of such a cell is evolved again with the
+   * collisionless first-order flux and the update is redone; if some cell is
+   * still non-physical, every face of the grid gets that flux for this step */
+  for (int level = 1; nbad && level <= 2; ++level) {
+    unsigned char* marked = (unsigned char*)malloc((size_t)nx * ny);
+    for (size_t c = 0; c < (size_t)nx * ny; ++c) marked[c] = level == 2 ? 1 : bad[c];
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i <= nx; ++i) {
+        const int il = i == 0 ? (bc[0].kind == ORC_BC_PERIODIC ? nx - 1 : -1) : i - 1;
+        const int ir = i == nx ? (bc[1].kind == ORC_BC_PERIODIC ? 0 : -1) : i;
+        if (!((il >= 0 && marked[(size_t)j * nx + il]) || (ir >= 0 && marked[(size_t)j * nx + ir]))) continue;
+        double F[4], Wg[2][4];
+        face_first_order(P, nx, ny, dx, dy, bc, U, 0, i, j, dt, F, Wg);
+        for (int v = 0; v < 4; ++v) {
+          Fx[((size_t)v * ny + j) * (nx + 1) + i] = F[v];
+          Wxn[WXI(v, 0, j, i)] = Wg[0][v];
+          Wxn[WXI(v, 1, j, i)] = Wg[1][v];
+        }
+      }
+    for (int j = 0; j <= ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const int jl = j == 0 ? (bc[2].kind == ORC_BC_PERIODIC ? ny - 1 : -1) : j - 1;
+        const int jr = j == ny ? (bc[3].kind == ORC_BC_PERIODIC ? 0 : -1) : j;
+        if (!((jl >= 0 && marked[(size_t)jl * nx + i]) || (jr >= 0 && marked[(size_t)jr * nx + i]))) continue;
+        double F[4], Wg[2][4];
+        face_first_order(P, nx, ny, dx, dy, bc, U, 1, i, j, dt, F, Wg);
+        for (int v = 0; v < 4; ++v) {
+          Fy[((size_t)v * (ny + 1) + j) * nx + i] = F[v];
+          Wyn[WYI(v, 0, j, i)] = Wg[0][v];
+          Wyn[WYI(v, 1, j, i)] = Wg[1][v];
+        }
+      }
+    free(marked);
+    nbad = update_cells(P, nx, ny, dx, dy, U, Fx, Fy, Un, bad);
+  }
+  if (!nbad) {
     memcpy(U, Un, sizeof(double) * nU);
     memcpy(Wx, Wxn, sizeof(double) * nWx);
     memcpy(Wy, Wyn, sizeof(double) * nWy);
   }
-  free(Fx); free(Fy); free(Wxn); free(Wyn); free(Un);
+  free(Fx); free(Fy); free(Wxn); free(Wyn); free(Un); free(bad);
   if (dt_out) *dt_out = dt;
-  return bad ? ORC_ENONPHYSICAL : ORC_OK;
+  return nbad ? ORC_ENONPHYSICAL : ORC_OK;
 }
 
 /* ------------------------------------------------------------------ */

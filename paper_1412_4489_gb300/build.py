@@ -13,8 +13,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libgks.so")
-SOURCES = [os.path.join(HERE, "csrc", "gks.cu"), os.path.join(HERE, "csrc", "gks_tools.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", "gks_device.cuh"), os.path.join(ROOT, "include", "gks.h")]
+SOURCES = [os.path.join(HERE, "csrc", n) for n in ("gks.cu", "gks_batch.cu", "gks_tools.cu")]
+DEPS = SOURCES + [os.path.join(HERE, "csrc", "gks_device.cuh"), os.path.join(HERE, "csrc", "gks_grid.cuh"),
+                  os.path.join(ROOT, "include", "gks.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,7 +31,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if os.path.getmtime(LIB) >= max(os.path.getmtime(p) for p in DEPS):
             return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared", "--threads", "2",
+    cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared", "--threads", "3",
            "-diag-suppress", "20011,20014",
            "-I", os.path.join(ROOT, "include"), "-o", tmp, *SOURCES]
     if verbose:

@@ -25,124 +25,24 @@
 
 #include "../../include/gks.h"
 #include "gks_device.cuh"
+#include "gks_grid.cuh"
 
 using namespace gks;
 
 namespace {
 
-constexpr int kLaunchesPerStep = 7;
-
-struct Ctrl {
-  unsigned long long dtbits[2];  // running min of the CFL bound, per parity
-  double t;
-  double dt;
-  long long steps;
-  int status;
-  int skip;
-  long long fail_step;
-};
-
-struct BCs {
-  int kind[4];
-  double uw[4], vw[4], Tw[4];
-};
-
-struct Geo {
-  int nx, ny, pitch;   // pitch: row length of the padded cell arrays
-  size_t plane;        // (ny+2) * pitch
-  double dx, dy;
-  double gamma, mu, Pr;
-  double weno_eps, weno_C, tau_eps, tau_C;
-  int viscous_dt;
-  BCs bc;
-};
-
-__device__ __forceinline__ size_t ci(const Geo& g, int v, int i, int j) {
-  return (size_t)v * g.plane + (size_t)(j + 1) * g.pitch + (i + 1);
-}
-
-__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
-__device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
+constexpr int kLaunchesPerStep = 9;
 
 template <class T> struct Store;
 template <> struct Store<double> { static __device__ __forceinline__ double to(double x) { return x; } };
 template <> struct Store<float> { static __device__ __forceinline__ float to(double x) { return (float)x; } };
 
 // ---------------------------------------------------------------------------
-// boundary images of cell averages (ghost ring)
-// ---------------------------------------------------------------------------
-__device__ void bc_value(int kind, double gamma, double uwt, double Tw, int axis, const double in[4],
-                         double out[4]) {
-  if (kind == GKS_BC_PERIODIC || kind == GKS_BC_OUTFLOW) {
-    for (int k = 0; k < 4; ++k) out[k] = in[k];
-    return;
-  }
-  double f[4];
-  f[0] = in[0];
-  f[3] = in[3];
-  f[1] = axis == 0 ? in[1] : in[2];
-  f[2] = axis == 0 ? in[2] : in[1];
-  double o[4];
-  if (kind == GKS_BC_SLIPWALL) {
-    o[0] = f[0]; o[1] = -f[1]; o[2] = f[2]; o[3] = f[3];
-  } else {
-    const double rho = f[0], mn = f[1], mt = f[2];
-    o[0] = rho;
-    o[1] = -mn;
-    o[2] = 2.0 * rho * uwt - mt;
-    o[3] = 2.0 * rho * uwt * uwt - 2.0 * uwt * mt + (mn * mn + mt * mt) / rho +
-           2.0 * rho * Tw / (gamma - 1.0) - f[3];
-  }
-  out[0] = o[0];
-  out[3] = o[3];
-  out[1] = axis == 0 ? o[1] : o[2];
-  out[2] = axis == 0 ? o[2] : o[1];
-}
-
-__device__ __forceinline__ double wall_t_velocity(const BCs& b, int side) {
-  // tangential wall velocity in the face frame: y-component on x-sides, x on y-sides
-  return side < 2 ? b.vw[side] : b.uw[side];
-}
-
-// value of a ghost cell; y is resolved first, so corners are x-images of y-ghosts
-__device__ void ghost_cell(const Geo& g, const double* __restrict__ U, int i, int j, double out[4]) {
-  int is = i, js = j;
-  int xs = -1, ys = -1;  // boundary side applied
-  if (j < 0) { ys = 2; js = g.bc.kind[2] == GKS_BC_PERIODIC ? g.ny - 1 : 0; }
-  if (j >= g.ny) { ys = 3; js = g.bc.kind[3] == GKS_BC_PERIODIC ? 0 : g.ny - 1; }
-  if (i < 0) { xs = 0; is = g.bc.kind[0] == GKS_BC_PERIODIC ? g.nx - 1 : 0; }
-  if (i >= g.nx) { xs = 1; is = g.bc.kind[1] == GKS_BC_PERIODIC ? 0 : g.nx - 1; }
-  double w[4], t[4];
-  for (int v = 0; v < 4; ++v) w[v] = U[ci(g, v, is, js)];
-  if (ys >= 0) {
-    bc_value(g.bc.kind[ys], g.gamma, wall_t_velocity(g.bc, ys), g.bc.Tw[ys], 1, w, t);
-    for (int v = 0; v < 4; ++v) w[v] = t[v];
-  }
-  if (xs >= 0) {
-    bc_value(g.bc.kind[xs], g.gamma, wall_t_velocity(g.bc, xs), g.bc.Tw[xs], 0, w, t);
-    for (int v = 0; v < 4; ++v) w[v] = t[v];
-  }
-  for (int v = 0; v < 4; ++v) out[v] = w[v];
-}
-
-// ---------------------------------------------------------------------------
 // control kernels
 // ---------------------------------------------------------------------------
-__global__ void k_begin(Ctrl* c, double cfl, double dt_max, double t_end) {
-  const int s = (int)(c->steps & 1);
-  const double bound = bitsd(c->dtbits[s]);
-  double dt = fmin(cfl * bound, dt_max);
-  dt = fmin(dt, t_end - c->t);
-  c->dt = dt;
-  c->skip = (c->status != GKS_OK || !(dt > 0.0)) ? 1 : 0;
-  if (!c->skip) c->dtbits[s ^ 1] = dbits(INFINITY);
-}
+__global__ void k_begin(Ctrl* c, double cfl, double dt_max, double t_end) { ctrl_begin(c, cfl, dt_max, t_end); }
 
-__global__ void k_end(Ctrl* c) {
-  if (c->skip || c->status != GKS_OK) return;
-  c->t += c->dt;
-  c->steps += 1;
-}
+__global__ void k_end(Ctrl* c) { ctrl_end(c); }
 
 // ---------------------------------------------------------------------------
 // ghost ring: perimeter of the padded cell array of the current buffer; in
@@ -151,22 +51,7 @@ __global__ void k_end(Ctrl* c) {
 __global__ void k_ghost(Geo g, double* U0, double* U1, float* F0, float* F1, const Ctrl* c, int force) {
   if (!force && c->skip) return;
   const int par = (int)(c->steps & 1);
-  double* U = par ? U1 : U0;
-  float* Uf = par ? F1 : F0;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int row = g.nx + 2;
-  int i, j;
-  if (p < row) { i = p - 1; j = -1; }
-  else if (p < 2 * row) { i = p - row - 1; j = g.ny; }
-  else if (p < 2 * row + g.ny) { i = -1; j = p - 2 * row; }
-  else if (p < 2 * row + 2 * g.ny) { i = g.nx; j = p - 2 * row - g.ny; }
-  else return;
-  double w[4];
-  ghost_cell(g, U, i, j, w);
-  for (int v = 0; v < 4; ++v) {
-    U[ci(g, v, i, j)] = w[v];
-    if (Uf) Uf[ci(g, v, i, j)] = (float)w[v];
-  }
+  ghost_at(g, par ? U1 : U0, par ? F1 : F0, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // FP32 mirror of the interior of the current cell-average buffer
@@ -192,77 +77,12 @@ __global__ void __launch_bounds__(256) k_recon(Geo g, const R* U0, const R* U1, 
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
   const int par = (int)(c->steps & 1);
-  const R* __restrict__ U = par ? U1 : U0;
-  const TW* __restrict__ Wx = par ? Wx1 : Wx0;
-  const TW* __restrict__ Wy = par ? Wy1 : Wy0;
-  const int nx = g.nx, ny = g.ny;
-  const size_t fxp = (size_t)ny * (nx + 1), fyp = (size_t)(ny + 1) * nx;
-  R a[4][5];
-  R cbar[4];
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const R cc = U[ci(g, v, i, j)];
-    cbar[v] = cc;
-    const TW* wx = Wx + (size_t)v * 2 * fxp + (size_t)j * (nx + 1);
-    const TW* wy = Wy + (size_t)v * 2 * fyp;
-    recon_var<R>(cc, U[ci(g, v, i + 1, j)], U[ci(g, v, i - 1, j)], U[ci(g, v, i, j + 1)], U[ci(g, v, i, j - 1)],
-                 R(wx[i + 1]), R(wx[fxp + i + 1]), R(wx[i]), R(wx[fxp + i]), R(wy[(size_t)(j + 1) * nx + i]),
-                 R(wy[fyp + (size_t)(j + 1) * nx + i]), R(wy[(size_t)j * nx + i]), R(wy[fyp + (size_t)j * nx + i]),
-                 dx, dy, weps, wC, a[v]);
-  }
-  // positivity: rho and p at the four face centres, else the constant average
-  bool bad = false;
-#pragma unroll
-  for (int f = 0; f < 4; ++f) {
-    R w[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const R x = f == 0 ? R(0.5) * dx : (f == 1 ? -R(0.5) * dx : R(0));
-      const R y = f == 2 ? R(0.5) * dy : (f == 3 ? -R(0.5) * dy : R(0));
-      w[v] = cbar[v] + a[v][0] * x + a[v][1] * y + a[v][2] * R(0.5) * (x * x - dx * dx / R(12)) +
-             a[v][3] * R(0.5) * (y * y - dy * dy / R(12)) + a[v][4] * x * y;
-    }
-    const R p = gm1 * (w[3] - R(0.5) * (w[1] * w[1] + w[2] * w[2]) / w[0]);
-    if (!(w[0] > R(0)) || !(p > R(0))) bad = true;
-  }
-  const size_t N = (size_t)nx * ny, o = (size_t)j * nx + i;
-#pragma unroll
-  for (int k = 0; k < 5; ++k)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) coef[(size_t)(k * 4 + v) * N + o] = bad ? R(0) : a[v][k];
+  recon_cell<R, TW>(g, par ? U1 : U0, par ? Wx1 : Wx0, par ? Wy1 : Wy0, coef, i, j, dx, dy, weps, wC, gm1);
 }
 
 // ---------------------------------------------------------------------------
 // face evolution
 // ---------------------------------------------------------------------------
-// face-frame slot of physical variable v (y-faces swap the momenta)
-template <int AX> __device__ __forceinline__ int slot(int v) { return AX == 0 ? v : (v == 1 ? 2 : (v == 2 ? 1 : v)); }
-
-// value and derivatives of cell (i, j)'s polynomial at the centre of its face
-// on side s (+1: the face at +h_n/2, -1: at -h_n/2), in the face frame of axis AX
-template <int AX, class R>
-__device__ __forceinline__ void side_state(const Geo& g, const R* __restrict__ U, const R* __restrict__ coef,
-                                           int i, int j, int s, R hn, R ht, FaceState<R>& S) {
-  const size_t N = (size_t)g.nx * g.ny, o = (size_t)j * g.nx + i;
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const R c = U[ci(g, v, i, j)];
-    const R a2 = coef[(size_t)(0 * 4 + v) * N + o], a3 = coef[(size_t)(1 * 4 + v) * N + o];
-    const R a4 = coef[(size_t)(2 * 4 + v) * N + o], a5 = coef[(size_t)(3 * 4 + v) * N + o];
-    const R a6 = coef[(size_t)(4 * 4 + v) * N + o];
-    const R an = AX == 0 ? a2 : a3, at = AX == 0 ? a3 : a2;
-    const R ann = AX == 0 ? a4 : a5, att = AX == 0 ? a5 : a4;
-    const int k = slot<AX>(v);
-    const R sh = R(s) * R(0.5) * hn;
-    S.w[0][k] = c + an * sh + ann * hn * hn / R(12) - att * ht * ht / R(24);
-    S.w[1][k] = an + ann * sh;
-    S.w[2][k] = at + a6 * sh;
-    S.w[3][k] = ann;
-    S.w[4][k] = a6;
-    S.w[5][k] = att;
-  }
-}
-
 // resident 128-thread blocks per SM the face kernel is compiled for (register cap)
 #ifndef GKS_FLUX_MINB_F32
 #define GKS_FLUX_MINB_F32 4
@@ -271,190 +91,51 @@ template <class R> struct FluxBlocks;
 template <> struct FluxBlocks<double> { static constexpr int value = 1; };
 template <> struct FluxBlocks<float> { static constexpr int value = GKS_FLUX_MINB_F32; };
 
-// Inputs of one face, fetched on demand by face_evolution
-template <int AX, class R>
-struct GridFaceSource {
-  const Geo* g;
-  const R* U;
-  const R* coef;
-  int i, j;           // face index (x-faces: i in [0, nx]; y-faces: j in [0, ny])
-  int cl, cr;         // the two cells along the normal, after periodic wrap
-  int img_lo, img_hi; // boundary image on the low / high side: 0 none, else the BC kind
-  R hn, ht, gamma, uwt_lo, Tw_lo, uwt_hi, Tw_hi;
-
-  __device__ __forceinline__ int cx(int n) const { return AX == 0 ? n : i; }
-  __device__ __forceinline__ int cy(int n) const { return AX == 0 ? j : n; }
-
-  __device__ __forceinline__ void image(int kind, R uwt, R Tw, const FaceState<R>& in, FaceState<R>& out) const {
-    if (kind == GKS_BC_OUTFLOW) out = in;
-    else wall_image<R>(kind, gamma, uwt, Tw, in, out);
-  }
-
-  __device__ __forceinline__ void side(int k, FaceState<R>& S) const {
-    if (k == 0) {
-      if (img_lo) {
-        FaceState<R> in;
-        side_state<AX>(*g, U, coef, cx(cr), cy(cr), -1, hn, ht, in);
-        image(img_lo, uwt_lo, Tw_lo, in, S);
-      } else {
-        side_state<AX>(*g, U, coef, cx(cl), cy(cl), +1, hn, ht, S);
-      }
-    } else {
-      if (img_hi) {
-        FaceState<R> in;
-        side_state<AX>(*g, U, coef, cx(cl), cy(cl), +1, hn, ht, in);
-        image(img_hi, uwt_hi, Tw_hi, in, S);
-      } else {
-        side_state<AX>(*g, U, coef, cx(cr), cy(cr), -1, hn, ht, S);
-      }
-    }
-  }
-
-  // six cell averages around the face (ghost ring included), face frame
-  __device__ __forceinline__ void avg(R a[2][3][4]) const {
-#pragma unroll
-    for (int m = 0; m < 2; ++m)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int ii = AX == 0 ? i - 1 + m : i - 1 + k;
-        const int jj = AX == 0 ? j - 1 + k : j - 1 + m;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) a[m][k][slot<AX>(v)] = U[ci(*g, v, ii, jj)];
-      }
-  }
-};
-
 template <int AX, class R, class TW>
 __global__ void __launch_bounds__(128, FluxBlocks<R>::value) k_flux(Geo g, FaceConst<R> C, const R* U0, const R* U1,
-                                              const R* __restrict__ coef, TW* Wn0, TW* Wn1, R* __restrict__ F,
-                                              const Ctrl* c, int force) {
+                                                                    const R* __restrict__ coef, TW* Wn0, TW* Wn1,
+                                                                    R* __restrict__ F, const Ctrl* c, int force) {
   if (!force && c->skip) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int nx = g.nx, ny = g.ny;
-  const int fx = AX == 0 ? nx + 1 : nx, fy = AX == 0 ? ny : ny + 1;
+  const int fx = AX == 0 ? g.nx + 1 : g.nx, fy = AX == 0 ? g.ny : g.ny + 1;
   if (i >= fx || j >= fy) return;
   const int par = (int)(c->steps & 1);
-  TW* __restrict__ Wn = par ? Wn0 : Wn1;  // new face values go to the other buffer
-
-  GridFaceSource<AX, R> src;
-  src.g = &g;
-  src.U = par ? U1 : U0;
-  src.coef = coef;
-  src.i = i;
-  src.j = j;
-  const int f = AX == 0 ? i : j;      // face index along the normal
-  const int nf = AX == 0 ? nx : ny;   // faces 0 and nf are on the boundary
-  const int lo_side = AX == 0 ? 0 : 2, hi_side = lo_side + 1;
-  src.cl = f - 1;
-  src.cr = f;
-  src.img_lo = src.img_hi = 0;
-  if (f == 0) {
-    if (g.bc.kind[lo_side] == GKS_BC_PERIODIC) src.cl = nf - 1;
-    else src.img_lo = g.bc.kind[lo_side];
-  }
-  if (f == nf) {
-    if (g.bc.kind[hi_side] == GKS_BC_PERIODIC) src.cr = 0;
-    else src.img_hi = g.bc.kind[hi_side];
-  }
-  src.hn = C.dn;
-  src.ht = C.dtan;
-  src.gamma = C.gamma;
-  src.uwt_lo = R(wall_t_velocity(g.bc, lo_side));
-  src.Tw_lo = R(g.bc.Tw[lo_side]);
-  src.uwt_hi = R(wall_t_velocity(g.bc, hi_side));
-  src.Tw_hi = R(g.bc.Tw[hi_side]);
-
-  R Fl[4], Wm[4], Wp[4];
-  face_evolution<R>(C, src, R(c->dt), Fl, Wm, Wp);
-
-  const size_t nfaces = (size_t)fx * fy, o = (size_t)j * fx + i;
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int k = slot<AX>(v);
-    F[(size_t)v * nfaces + o] = Fl[k];
-    Wn[(size_t)(v * 2 + 0) * nfaces + o] = TW(Wm[k]);
-    Wn[(size_t)(v * 2 + 1) * nfaces + o] = TW(Wp[k]);
-  }
+  // new face values go to the other buffer
+  flux_face<AX, R, TW>(g, C, par ? U1 : U0, coef, par ? Wn0 : Wn1, F, i, j, R(c->dt));
 }
 
 // ---------------------------------------------------------------------------
 // update, CFL bound of the new state, physical check
 // ---------------------------------------------------------------------------
-// inverse CFL bound max((|U|+c)/dx, (|V|+c)/dy) (and the viscous rate) of a state;
-// ok = rho > 0 and p > 0.  The bound itself is 1/inverse.
-template <class R>
-__device__ __forceinline__ R inv_bound(const Geo& g, const R w[4], bool& ok) {
-  const R ir = R(1) / w[0];
-  const R u = w[1] * ir, v = w[2] * ir;
-  const R p = R(g.gamma - 1.0) * (w[3] - R(0.5) * (w[1] * u + w[2] * v));
-  ok = w[0] > R(0) && p > R(0);
-  const R c = sqrt(R(g.gamma) * p * ir);
-  R inv = fmax((fabs(u) + c) * R(1.0 / g.dx), (fabs(v) + c) * R(1.0 / g.dy));
-  if (g.viscous_dt && g.mu > 0.0) {
-    const double h = fmin(g.dx, g.dy);
-    inv = fmax(inv, R(2.0 * g.mu * fmax(4.0 / 3.0, g.gamma / g.Pr) / (h * h)) * ir);
-  }
-  return inv;
-}
-
-// block maximum of inv, then the atomic minimum of the bound 1/inv
-template <class R>
-__device__ __forceinline__ void block_bound_to(R inv, unsigned long long* slot) {
-  __shared__ R red[32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) inv = fmax(inv, __shfl_xor_sync(0xffffffffu, inv, o));
-  const int t = threadIdx.y * blockDim.x + threadIdx.x;
-  const int lane = t & 31, warp = t >> 5;
-  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
-  if (lane == 0) red[warp] = inv;
-  __syncthreads();
-  if (warp == 0) {
-    inv = lane < nw ? red[lane] : R(0);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) inv = fmax(inv, __shfl_xor_sync(0xffffffffu, inv, o));
-    if (lane == 0 && inv > R(0)) atomicMin(slot, dbits(1.0 / (double)inv));
-  }
-}
-
-template <class R>
-__global__ void __launch_bounds__(256) k_update(Geo g, double* U0, double* U1, float* F0, float* F1,
-                                                const R* __restrict__ Fx, const R* __restrict__ Fy, Ctrl* c) {
-  if (c->skip) return;
+// Update pass 1, 2 or 3 (see update_cell): pass 1 marks the cells it leaves
+// non-physical; pass 2 runs only if pass 1 marked cells, pass 3 only if pass 2
+// still left one; a cell non-physical after pass 3 fails the step.  Each pass
+// keeps its own running minimum of the CFL bound.
+template <class R, class TW>
+__global__ void __launch_bounds__(256) k_update(Geo g, double* U0, double* U1, float* F0, float* F1, const R* Ur0,
+                                                const R* Ur1, const R* __restrict__ Fx, const R* __restrict__ Fy,
+                                                TW* Wx0, TW* Wx1, TW* Wy0, TW* Wy1, unsigned char* __restrict__ bad,
+                                                Ctrl* c, int pass) {
+  if (c->skip || (pass == 2 && !c->bad_found[0]) || (pass == 3 && !c->bad_found[1])) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int par = (int)(c->steps & 1);
-  const double* __restrict__ U = par ? U1 : U0;
-  double* __restrict__ Un = par ? U0 : U1;
-  float* __restrict__ Ufn = par ? F0 : F1;
   R inv = R(0);
   if (i < g.nx && j < g.ny) {
-    const int nx = g.nx, ny = g.ny;
-    const size_t nfx = (size_t)ny * (nx + 1), nfy = (size_t)(ny + 1) * nx;
-    const double idx = 1.0 / g.dx, idy = 1.0 / g.dy;
-    double w[4];
-    R wr[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const R fw = Fx[v * nfx + (size_t)j * (nx + 1) + i];
-      const R fe = Fx[v * nfx + (size_t)j * (nx + 1) + i + 1];
-      const R gs = Fy[v * nfy + (size_t)j * nx + i];
-      const R gn = Fy[v * nfy + (size_t)(j + 1) * nx + i];
-      // Eq. finite in FP64: differences of the (possibly FP32) face fluxes are exact in
-      // FP64, so the face fluxes telescope and the update stays conservative
-      w[v] = U[ci(g, v, i, j)] + ((double)fw - (double)fe) * idx + ((double)gs - (double)gn) * idy;
-      Un[ci(g, v, i, j)] = w[v];
-      wr[v] = R(w[v]);
-      if (Ufn) Ufn[ci(g, v, i, j)] = (float)wr[v];
-    }
-    bool ok;
-    inv = inv_bound<R>(g, wr, ok);
-    if (!ok || !isfinite(w[0]) || !isfinite(w[1]) || !isfinite(w[2]) || !isfinite(w[3]) || !(inv < R(INFINITY))) {
-      if (atomicCAS(&c->status, GKS_OK, GKS_ENONPHYSICAL) == GKS_OK) c->fail_step = c->steps;
-      inv = R(0);
+    bool b;
+    inv = update_cell<R, TW>(g, par ? U1 : U0, par ? U0 : U1, par ? F0 : F1, par ? Ur1 : Ur0, Fx, Fy,
+                             par ? Wx0 : Wx1, par ? Wy0 : Wy1, bad, pass, R(c->dt), i, j, b);
+    if (pass == 1) {
+      bad[(size_t)j * g.nx + i] = b ? 1 : 0;
+      if (b) atomicOr(&c->bad_found[0], 1);
+    } else if (pass == 2) {
+      if (b) atomicOr(&c->bad_found[1], 1);
+    } else if (b && atomicCAS(&c->status, GKS_OK, GKS_ENONPHYSICAL) == GKS_OK) {
+      c->fail_step = c->steps;
     }
   }
-  block_bound_to<R>(inv, &c->dtbits[(c->steps & 1) ^ 1]);
+  block_bound_to<R>(inv, &c->dtb[pass - 1]);
 }
 
 // CFL bound of the current state (after set_state), in FP64
@@ -474,7 +155,7 @@ __global__ void k_dtbound(Geo g, const double* U0, const double* U1, Ctrl* c) {
       inv = 0.0;
     }
   }
-  block_bound_to<double>(inv, &c->dtbits[par]);
+  block_bound_to<double>(inv, &c->bound);
 }
 
 // ---------------------------------------------------------------------------
@@ -562,6 +243,7 @@ struct gks_handle {
   void* coef;
   void* Fx;
   void* Fy;
+  unsigned char* bad;  // cells whose first update failed (positivity fallback)
   Ctrl* ctrl;
   Ctrl* hctrl;       // pinned mirror
   double* staging;   // device FP64 scratch for host transfers
@@ -593,14 +275,10 @@ gks_status fail(gks_handle* h, gks_status s, const std::string& msg) {
 
 dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
 
-// ev (optional, 8 events): recorded before each of the seven kernels and after the last
+// ev (optional, 10 events): recorded before each of the nine kernels and after the last
 template <class R>
 FaceConst<R> fconst(const Geo& g, int axis) {
-  FaceParams P;
-  P.gamma = g.gamma; P.mu = g.mu; P.Pr = g.Pr; P.tau_eps = g.tau_eps; P.tau_C = g.tau_C;
-  P.dn = axis == 0 ? g.dx : g.dy;
-  P.dtan = axis == 0 ? g.dy : g.dx;
-  return face_const<R>(P);
+  return grid_face_const<R>(g, axis);
 }
 
 // the padded cell-average arrays the compute-type kernels read
@@ -624,7 +302,7 @@ void launch_recon(gks_handle* h, int force) {
       force);
 }
 
-// ev (optional, 8 events): recorded before each of the seven kernels and after the last
+// ev (optional, 10 events): recorded before each of the nine kernels and after the last
 template <class R, class TW>
 gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double t_end, bool with_begin_end,
                                bool do_update, int force, cudaEvent_t* ev = nullptr) {
@@ -649,12 +327,16 @@ gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double 
                                                              (const R*)h->coef, (TW*)h->Wy[0], (TW*)h->Wy[1],
                                                              (R*)h->Fy, h->ctrl, force);
   mark(5);
-  if (do_update)
-    k_update<R><<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, h->U[0], h->U[1], h->Uf[0], h->Uf[1], (const R*)h->Fx,
-                                                      (const R*)h->Fy, h->ctrl);
-  mark(6);
+  for (int pass = 1; pass <= 3; ++pass) {
+    if (do_update)
+      k_update<R, TW><<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(
+          g, h->U[0], h->U[1], h->Uf[0], h->Uf[1], cells<R>(h, 0), cells<R>(h, 1), (const R*)h->Fx, (const R*)h->Fy,
+          (TW*)h->Wx[0], (TW*)h->Wx[1], (TW*)h->Wy[0], (TW*)h->Wy[1], h->bad, h->ctrl, pass);
+    mark(5 + pass);
+  }
+  mark(8);
   if (with_begin_end) k_end<<<1, 1, 0, s>>>(h->ctrl);
-  mark(7);
+  mark(9);
   CK(cudaGetLastError());
   return GKS_OK;
 }
@@ -695,7 +377,8 @@ gks_status reset_ctrl(gks_handle* h, double t) {
   const double inf = INFINITY;
   uint64_t b;
   memcpy(&b, &inf, 8);
-  h->hctrl->dtbits[0] = h->hctrl->dtbits[1] = b;
+  h->hctrl->bound = b;
+  h->hctrl->dtb[0] = h->hctrl->dtb[1] = h->hctrl->dtb[2] = b;
   h->hctrl->t = t;
   CK(cudaMemcpyAsync(h->ctrl, h->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -823,6 +506,7 @@ gks_status gks_create(int nx, int ny, double Lx, double Ly, double gamma, double
   alloc(&h->coef, (size_t)20 * nx * ny * wsz);
   alloc(&h->Fx, (size_t)4 * ny * (nx + 1) * wsz);
   alloc(&h->Fy, (size_t)4 * (ny + 1) * nx * wsz);
+  alloc((void**)&h->bad, (size_t)nx * ny);
   alloc((void**)&h->ctrl, sizeof(Ctrl));
   h->staging_n = n_u(g);
   if (n_wx(g) > h->staging_n) h->staging_n = n_wx(g);
@@ -998,6 +682,7 @@ void gks_destroy(gks_handle* h) {
   cudaFree(h->coef);
   cudaFree(h->Fx);
   cudaFree(h->Fy);
+  cudaFree(h->bad);
   cudaFree(h->ctrl);
   cudaFree(h->staging);
   if (h->hctrl) cudaFreeHost(h->hctrl);
@@ -1008,18 +693,18 @@ void gks_destroy(gks_handle* h) {
 const char* gks_last_error(const gks_handle* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
 
 gks_status gks_profile_step(gks_handle* h, double CFL, float* ms) {
-  if (!h || !ms || !(CFL > 0)) return fail(h, GKS_EINVAL, "gks_profile_step: CFL > 0 and ms[7] required");
+  if (!h || !ms || !(CFL > 0)) return fail(h, GKS_EINVAL, "gks_profile_step: CFL > 0 and ms[9] required");
   CK(cudaSetDevice(h->device));
-  cudaEvent_t ev[8];
-  for (int k = 0; k < 8; ++k) CK(cudaEventCreate(&ev[k]));
+  cudaEvent_t ev[10];
+  for (int k = 0; k < 10; ++k) CK(cudaEventCreate(&ev[k]));
   gks_status st = h->prec == GKS_FP64 ? launch_step_kernels<double, double>(h, CFL, INFINITY, INFINITY, true, true, 0, ev)
                                       : launch_step_kernels<float, float>(h, CFL, INFINITY, INFINITY, true, true, 0, ev);
   if (st == GKS_OK) {
-    cudaError_t e = cudaEventSynchronize(ev[7]);
-    for (int k = 0; k < 7 && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
+    cudaError_t e = cudaEventSynchronize(ev[9]);
+    for (int k = 0; k < 9 && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
     if (e != cudaSuccess) st = fail(h, GKS_ECUDA, std::string("gks_profile_step: ") + cudaGetErrorString(e));
   }
-  for (int k = 0; k < 8; ++k) cudaEventDestroy(ev[k]);
+  for (int k = 0; k < 10; ++k) cudaEventDestroy(ev[k]);
   if (st != GKS_OK) return st;
   st = read_ctrl(h);
   if (st != GKS_OK) return st;
@@ -1109,7 +794,9 @@ void* noalloc_base(int device, std::string& why) {
 }
 
 __global__ void k_noalloc_ctrl(Ctrl* c) {
-  c->dtbits[0] = c->dtbits[1] = dbits(INFINITY);
+  c->bound = dbits(INFINITY);
+  c->dtb[0] = c->dtb[1] = c->dtb[2] = dbits(INFINITY);
+  c->bad_found[0] = c->bad_found[1] = 0;
   c->t = 0.0;
   c->dt = 0.0;
   c->steps = 0;
@@ -1156,7 +843,8 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
   const size_t b_coef = align256((size_t)20 * nx * ny * sizeof(double));
   const size_t b_fx = align256((size_t)4 * ny * (nx + 1) * sizeof(double));
   const size_t b_fy = align256((size_t)4 * (ny + 1) * nx * sizeof(double));
-  const size_t need = b_ctrl + 2 * b_u + b_coef + b_fx + b_fy;
+  const size_t b_bad = align256((size_t)nx * ny);
+  const size_t need = b_ctrl + 2 * b_u + b_coef + b_fx + b_fy + b_bad;
   if ((long long)nx * ny > 65536 || need > kNoallocBytes) {
     g_create_err = "gks_step_noalloc: grid too large for the static scratch (at most 65,536 cells, " +
                    std::to_string(kNoallocBytes >> 20) + " MiB); need " + std::to_string(need) + " bytes";
@@ -1173,6 +861,7 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
   double* coef = (double*)(base + b_ctrl + 2 * b_u);
   double* Fx = (double*)(base + b_ctrl + 2 * b_u + b_coef);
   double* Fy = (double*)(base + b_ctrl + 2 * b_u + b_coef + b_fx);
+  unsigned char* bad = base + b_ctrl + 2 * b_u + b_coef + b_fx + b_fy;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const dim3 b2(32, 8), bf(32, 4);
   const int per = 2 * (nx + 2) + 2 * ny;
@@ -1188,7 +877,10 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
                                                                   const_cast<double*>(dWx), dWx_out, Fx, ctrl, 0);
   k_flux<1, double, double><<<grid2(nx, ny + 1, bf), bf, 0, s>>>(g, fconst<double>(g, 1), U0, U1, coef,
                                                                   const_cast<double*>(dWy), dWy_out, Fy, ctrl, 0);
-  k_update<double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, nullptr, nullptr, Fx, Fy, ctrl);
+  for (int pass = 1; pass <= 3; ++pass)
+    k_update<double, double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, nullptr, nullptr, U0, U1, Fx, Fy,
+                                                              const_cast<double*>(dWx), dWx_out,
+                                                              const_cast<double*>(dWy), dWy_out, bad, ctrl, pass);
   k_end<<<1, 1, 0, s>>>(ctrl);
   k_scatter_U<<<grid2(nx, ny, b2), b2, 0, s>>>(g, dU_out, U0, U1, ctrl, 0);
   e = cudaGetLastError();

@@ -1,0 +1,829 @@
+// Batched form: many independent grids of uneven sizes (each with its own gamma,
+// mu, Pr, boundary conditions, dt and time) advanced together by ONE persistent
+// cooperative kernel per call, captured once in a CUDA graph and replayed.
+//
+// Inside the kernel every step runs its phases over flat work lists of
+// 128-element tiles drawn from all grids (per-grid dt, ghost rings,
+// reconstruction, face evolution of x- and y-faces, update + CFL minimum, and
+// -- only when some cell's update was not physical -- the first-order faces of
+// the positivity fallback and the second update), separated by a device-wide
+// barrier.  The barrier is a
+// counter with a generation word; every wait is bounded in time (globaltimer)
+// and gives up with GKS_ETIMEOUT instead of hanging.  The per-element
+// arithmetic is that of the single-grid kernels (gks_grid.cuh).
+//
+// gks_batch_autotune times the tile shape of the face phase and the number of
+// resident blocks per SM on the batch itself and keeps the fastest.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gks.h"
+#include "gks_device.cuh"
+#include "gks_grid.cuh"
+
+using namespace gks;
+
+namespace {
+
+constexpr int kThreads = 128;  // one work tile = one block = 128 cells or faces
+
+struct GridOff {
+  size_t u;     // padded cell arrays (U, Uf)
+  size_t wx, wy;
+  size_t coef;  // 20 * nx * ny
+  size_t fx, fy;
+  size_t bad;   // nx * ny flags of the positivity fallback
+};
+
+struct Barrier {
+  unsigned count;
+  unsigned gen;
+  int any_bad[2];            // some grid's update pass 1 / 2 left a cell non-physical this step
+  int error;
+  int skip_block;            // test hook: this block never arrives (-1: none)
+  unsigned long long limit;  // wait limit in ns
+};
+
+template <class R, class TW>
+struct Args {
+  int G;
+  const Geo* geo;
+  const GridOff* off;
+  const FaceConst<R>* fc;  // [G][2]
+  Ctrl* ctrl;
+  double* U[2];
+  float* Uf[2];
+  TW* Wx[2];
+  TW* Wy[2];
+  R* coef;
+  R* Fx;
+  R* Fy;
+  unsigned char* bad;
+  const int4* ghost_items;  // (grid, first perimeter index)
+  const int4* cell_items;   // (grid, x0, y0, -)
+  const int4* face_items;   // (grid, x0, y0, axis)
+  int n_ghost, n_cell, n_face;
+  int cell_tw, face_tw;     // tile widths (heights = 128 / width)
+  Barrier* bar;
+  double cfl;
+};
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// device-wide barrier with a bounded wait; returns false once any block gave up
+__device__ bool grid_barrier(Barrier* b) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &b->gen;
+    volatile int* verr = &b->error;
+    const unsigned my = *vgen;
+    __threadfence();
+    if ((int)blockIdx.x != b->skip_block) {
+      if (atomicAdd(&b->count, 1u) + 1 == gridDim.x) {
+        b->count = 0;
+        __threadfence();
+        atomicAdd(&b->gen, 1u);
+      }
+    }
+    const unsigned long long t0 = now_ns();
+    while (*vgen == my && *verr == 0) {
+      if (now_ns() - t0 > b->limit) {
+        atomicCAS(&b->error, 0, (int)GKS_ETIMEOUT);
+        break;
+      }
+      __nanosleep(200);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)&b->error == 0;
+}
+
+#ifndef GKS_BATCH_MINB_F32
+#define GKS_BATCH_MINB_F32 4
+#endif
+template <class R> struct BatchBlocks;
+template <> struct BatchBlocks<double> { static constexpr int value = 1; };
+template <> struct BatchBlocks<float> { static constexpr int value = GKS_BATCH_MINB_F32; };
+
+template <class R, class TW>
+__global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<R, TW> a, int nsteps) {
+  const int tid = threadIdx.x;
+  for (int s = 0; s < nsteps; ++s) {
+    // dt of this step per grid (after ending the previous one)
+    for (int g = blockIdx.x * kThreads + tid; g < a.G; g += gridDim.x * kThreads) {
+      if (s > 0) ctrl_end(&a.ctrl[g]);
+      ctrl_begin(&a.ctrl[g], a.cfl, INFINITY, INFINITY);
+    }
+    if (!grid_barrier(a.bar)) return;
+    // every block read the previous step's flags before the barrier above
+    if (blockIdx.x == 0 && tid == 0) a.bar->any_bad[0] = a.bar->any_bad[1] = 0;
+
+    // ghost rings
+    for (int it = blockIdx.x; it < a.n_ghost; it += gridDim.x) {
+      const int4 w = a.ghost_items[it];
+      const Ctrl* c = &a.ctrl[w.x];
+      if (c->skip) continue;
+      const int par = (int)(c->steps & 1);
+      const Geo& g = a.geo[w.x];
+      float* uf = a.Uf[par] ? a.Uf[par] + a.off[w.x].u : nullptr;
+      ghost_at(g, a.U[par] + a.off[w.x].u, uf, w.y + tid);
+    }
+    if (!grid_barrier(a.bar)) return;
+
+    // reconstruction
+    for (int it = blockIdx.x; it < a.n_cell; it += gridDim.x) {
+      const int4 w = a.cell_items[it];
+      const Ctrl* c = &a.ctrl[w.x];
+      if (c->skip) continue;
+      const Geo& g = a.geo[w.x];
+      const int i = w.y + tid % a.cell_tw, j = w.z + tid / a.cell_tw;
+      if (i >= g.nx || j >= g.ny) continue;
+      const int par = (int)(c->steps & 1);
+      const GridOff& o = a.off[w.x];
+      const R* U = (sizeof(R) == 4 ? (const R*)a.Uf[par] : (const R*)a.U[par]) + o.u;
+      recon_cell<R, TW>(g, U, a.Wx[par] + o.wx, a.Wy[par] + o.wy, a.coef + o.coef, i, j, R(g.dx), R(g.dy),
+                        R(g.weno_eps), R(g.weno_C), R(g.gamma - 1.0));
+    }
+    if (!grid_barrier(a.bar)) return;
+
+    // face evolution
+    for (int it = blockIdx.x; it < a.n_face; it += gridDim.x) {
+      const int4 w = a.face_items[it];
+      const Ctrl* c = &a.ctrl[w.x];
+      if (c->skip) continue;
+      const Geo& g = a.geo[w.x];
+      const int i = w.y + tid % a.face_tw, j = w.z + tid / a.face_tw;
+      const int par = (int)(c->steps & 1);
+      const GridOff& o = a.off[w.x];
+      const R* U = (sizeof(R) == 4 ? (const R*)a.Uf[par] : (const R*)a.U[par]) + o.u;
+      const R dt = R(c->dt);
+      if (w.w == 0) {
+        if (i <= g.nx && j < g.ny)
+          flux_face<0, R, TW>(g, a.fc[2 * w.x], U, a.coef + o.coef, a.Wx[par ^ 1] + o.wx, a.Fx + o.fx, i, j, dt);
+      } else {
+        if (i < g.nx && j <= g.ny)
+          flux_face<1, R, TW>(g, a.fc[2 * w.x + 1], U, a.coef + o.coef, a.Wy[par ^ 1] + o.wy, a.Fy + o.fy, i, j, dt);
+      }
+    }
+    if (!grid_barrier(a.bar)) return;
+
+    // update and the CFL minimum of the new state (update_cell): pass 1; pass 2
+    // for grids where pass 1 left a cell non-physical; pass 3 for grids where
+    // pass 2 still did.  The global flags let every block skip an unneeded pass
+    // together.
+    for (int pass = 1; pass <= 3; ++pass) {
+      if (pass > 1 && *(volatile int*)&a.bar->any_bad[pass - 2] == 0) break;
+      for (int it = blockIdx.x; it < a.n_cell; it += gridDim.x) {
+        const int4 w = a.cell_items[it];
+        Ctrl* c = &a.ctrl[w.x];
+        if (c->skip || (pass == 2 && !c->bad_found[0]) || (pass == 3 && !c->bad_found[1])) continue;  // per block
+        const Geo& g = a.geo[w.x];
+        const int i = w.y + tid % a.cell_tw, j = w.z + tid / a.cell_tw;
+        const int par = (int)(c->steps & 1);
+        const GridOff& o = a.off[w.x];
+        R inv = R(0);
+        if (i < g.nx && j < g.ny) {
+          bool bad;
+          float* ufn = a.Uf[par ^ 1] ? a.Uf[par ^ 1] + o.u : nullptr;
+          const R* Ur = (sizeof(R) == 4 ? (const R*)a.Uf[par] : (const R*)a.U[par]) + o.u;
+          inv = update_cell<R, TW>(g, a.U[par] + o.u, a.U[par ^ 1] + o.u, ufn, Ur, a.Fx + o.fx, a.Fy + o.fy,
+                                   a.Wx[par ^ 1] + o.wx, a.Wy[par ^ 1] + o.wy, a.bad + o.bad, pass, R(c->dt), i, j,
+                                   bad);
+          if (pass == 1) {
+            a.bad[o.bad + (size_t)j * g.nx + i] = bad ? 1 : 0;
+            if (bad) {
+              atomicOr(&c->bad_found[0], 1);
+              atomicOr(&a.bar->any_bad[0], 1);
+            }
+          } else if (pass == 2) {
+            if (bad) {
+              atomicOr(&c->bad_found[1], 1);
+              atomicOr(&a.bar->any_bad[1], 1);
+            }
+          } else if (bad && atomicCAS(&c->status, GKS_OK, GKS_ENONPHYSICAL) == GKS_OK) {
+            c->fail_step = c->steps;
+          }
+        }
+        block_bound_to<R>(inv, &c->dtb[pass - 1]);
+      }
+      if (!grid_barrier(a.bar)) return;
+    }
+  }
+  for (int g = blockIdx.x * kThreads + tid; g < a.G; g += gridDim.x * kThreads)
+    if (nsteps > 0) ctrl_end(&a.ctrl[g]);
+}
+
+// ---- per-grid state transfer ----
+__global__ void kb_scatter(Geo g, const double* src, double* U, float* Uf, int to_dev) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  for (int v = 0; v < 4; ++v) {
+    const size_t o = ((size_t)v * g.ny + j) * g.nx + i;
+    if (to_dev) {
+      U[ci(g, v, i, j)] = src[o];
+      if (Uf) Uf[ci(g, v, i, j)] = (float)src[o];
+    } else {
+      const_cast<double*>(src)[o] = U[ci(g, v, i, j)];
+    }
+  }
+}
+
+__global__ void kb_ghost(Geo g, double* U, float* Uf) {
+  ghost_at(g, U, Uf, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <class TW>
+__global__ void kb_copyW(const double* src, TW* W, size_t n, int to_dev) {
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  if (to_dev) W[k] = (TW)src[k];
+  else const_cast<double*>(src)[k] = (double)W[k];
+}
+
+__global__ void kb_dtbound(Geo g, const double* U, Ctrl* c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  double inv = 0.0;
+  if (i < g.nx && j < g.ny) {
+    double w[4];
+    for (int v = 0; v < 4; ++v) w[v] = U[ci(g, v, i, j)];
+    bool ok;
+    inv = inv_bound<double>(g, w, ok);
+    if (!ok || !(inv < INFINITY)) {
+      atomicCAS(&c->status, GKS_OK, GKS_ENONPHYSICAL);
+      inv = 0.0;
+    }
+  }
+  block_bound_to<double>(inv, &c->bound);
+}
+
+dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
+
+}  // namespace
+
+struct gks_batch {
+  int G;
+  int prec;
+  int device, sms;
+  cudaStream_t stream;
+  bool own_stream;
+  std::vector<Geo> geo;
+  std::vector<GridOff> off;
+  size_t n_u, n_wx, n_wy, n_coef, n_fx, n_fy;
+  long long cells;
+  // device
+  Geo* d_geo;
+  GridOff* d_off;
+  void* d_fc;
+  Ctrl* d_ctrl;
+  double* U[2];
+  float* Uf[2];
+  void* Wx[2];
+  void* Wy[2];
+  void* coef;
+  void* Fx;
+  void* Fy;
+  unsigned char* bad;
+  int4* d_ghost;
+  int4* d_cell;
+  int4* d_face;
+  int n_ghost, n_cell, n_face;
+  Barrier* d_bar;
+  Ctrl* h_ctrl;  // pinned mirror of all control blocks
+  Barrier* h_bar;
+  double* staging;
+  size_t staging_n;
+  // launch configuration
+  int face_tw, cell_tw, blocks_per_sm, max_blocks_per_sm;
+  double timeout_s;
+  int skip_block;
+  cudaGraphExec_t graph;
+  int graph_steps;
+  double graph_cfl;
+  bool graph_ok;
+  std::string err;
+};
+
+namespace {
+
+gks_status bfail(gks_batch* b, gks_status s, const std::string& m) {
+  if (b) b->err = m;
+  return s;
+}
+
+#define BCK(call)                                                                            \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return bfail(b, GKS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+size_t wsize(const gks_batch* b) { return b->prec == GKS_FP64 ? 8 : 4; }
+
+gks_status build_items(gks_batch* b) {
+  std::vector<int4> gh, cell, face;
+  const int ch = kThreads / b->cell_tw, fh = kThreads / b->face_tw;
+  for (int g = 0; g < b->G; ++g) {
+    const Geo& G = b->geo[g];
+    for (int p = 0; p < perimeter(G); p += kThreads) gh.push_back(make_int4(g, p, 0, 0));
+    for (int y = 0; y < G.ny; y += ch)
+      for (int x = 0; x < G.nx; x += b->cell_tw) cell.push_back(make_int4(g, x, y, 0));
+    for (int y = 0; y < G.ny; y += fh)
+      for (int x = 0; x < G.nx + 1; x += b->face_tw) face.push_back(make_int4(g, x, y, 0));
+    for (int y = 0; y < G.ny + 1; y += fh)
+      for (int x = 0; x < G.nx; x += b->face_tw) face.push_back(make_int4(g, x, y, 1));
+  }
+  cudaFree(b->d_ghost);
+  cudaFree(b->d_cell);
+  cudaFree(b->d_face);
+  b->d_ghost = b->d_cell = b->d_face = nullptr;
+  BCK(cudaMalloc(&b->d_ghost, gh.size() * sizeof(int4)));
+  BCK(cudaMalloc(&b->d_cell, cell.size() * sizeof(int4)));
+  BCK(cudaMalloc(&b->d_face, face.size() * sizeof(int4)));
+  BCK(cudaMemcpy(b->d_ghost, gh.data(), gh.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  BCK(cudaMemcpy(b->d_cell, cell.data(), cell.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  BCK(cudaMemcpy(b->d_face, face.data(), face.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  b->n_ghost = (int)gh.size();
+  b->n_cell = (int)cell.size();
+  b->n_face = (int)face.size();
+  return GKS_OK;
+}
+
+template <class R, class TW>
+Args<R, TW> make_args(gks_batch* b, double cfl) {
+  Args<R, TW> a;
+  a.G = b->G;
+  a.geo = b->d_geo;
+  a.off = b->d_off;
+  a.fc = (const FaceConst<R>*)b->d_fc;
+  a.ctrl = b->d_ctrl;
+  for (int k = 0; k < 2; ++k) {
+    a.U[k] = b->U[k];
+    a.Uf[k] = b->Uf[k];
+    a.Wx[k] = (TW*)b->Wx[k];
+    a.Wy[k] = (TW*)b->Wy[k];
+  }
+  a.coef = (R*)b->coef;
+  a.Fx = (R*)b->Fx;
+  a.Fy = (R*)b->Fy;
+  a.bad = b->bad;
+  a.ghost_items = b->d_ghost;
+  a.cell_items = b->d_cell;
+  a.face_items = b->d_face;
+  a.n_ghost = b->n_ghost;
+  a.n_cell = b->n_cell;
+  a.n_face = b->n_face;
+  a.cell_tw = b->cell_tw;
+  a.face_tw = b->face_tw;
+  a.bar = b->d_bar;
+  a.cfl = cfl;
+  return a;
+}
+
+template <class R, class TW>
+gks_status launch(gks_batch* b, int nsteps, double cfl) {
+  Args<R, TW> a = make_args<R, TW>(b, cfl);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(b->sms * b->blocks_per_sm));
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = b->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  BCK(cudaLaunchKernelEx(&cfg, k_batch<R, TW>, a, nsteps));
+  return GKS_OK;
+}
+
+gks_status launch_any(gks_batch* b, int nsteps, double cfl) {
+  return b->prec == GKS_FP64 ? launch<double, double>(b, nsteps, cfl) : launch<float, float>(b, nsteps, cfl);
+}
+
+gks_status reset_barrier(gks_batch* b) {
+  b->h_bar->count = 0;
+  b->h_bar->gen = 0;
+  b->h_bar->any_bad[0] = b->h_bar->any_bad[1] = 0;
+  b->h_bar->error = 0;
+  b->h_bar->skip_block = b->skip_block;
+  b->h_bar->limit = (unsigned long long)(b->timeout_s * 1e9);
+  BCK(cudaMemcpyAsync(b->d_bar, b->h_bar, sizeof(Barrier), cudaMemcpyHostToDevice, b->stream));
+  return GKS_OK;
+}
+
+void drop_graph(gks_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+}
+
+int occupancy(gks_batch* b) {
+  int n = 0;
+  if (b->prec == GKS_FP64)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<double, double>, kThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<float, float>, kThreads, 0);
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+gks_status gks_batch_create(int n, const gks_grid_desc* grids, const gks_options* opt, void* cuda_stream,
+                            gks_batch** out) {
+  if (!out || n < 1 || !grids) return GKS_EINVAL;
+  *out = nullptr;
+  gks_options o;
+  gks_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != GKS_FP64 && o.precision != GKS_FP32_BULK) return GKS_EINVAL;
+  gks_batch* b = new gks_batch();
+  b->G = n;
+  b->prec = o.precision;
+  b->cell_tw = 32;
+  b->face_tw = 32;
+  b->timeout_s = 2.0;
+  b->skip_block = -1;
+  size_t nu = 0, nwx = 0, nwy = 0, nc = 0, nfx = 0, nfy = 0, nbad = 0;
+  b->cells = 0;
+  for (int g = 0; g < n; ++g) {
+    const gks_grid_desc& d = grids[g];
+    if (d.nx < 2 || d.ny < 2 || !(d.Lx > 0) || !(d.Ly > 0) || !(d.gamma > 1.0) || !(d.Pr > 0) || !(d.mu >= 0)) {
+      delete b;
+      return GKS_EINVAL;
+    }
+    Geo G;
+    memset(&G, 0, sizeof(G));
+    G.nx = d.nx; G.ny = d.ny;
+    G.pitch = ((d.nx + 2) + 1) & ~1;
+    G.plane = (size_t)(d.ny + 2) * G.pitch;
+    G.dx = d.Lx / d.nx; G.dy = d.Ly / d.ny;
+    G.gamma = d.gamma; G.mu = d.mu; G.Pr = d.Pr;
+    G.weno_eps = o.weno_eps; G.weno_C = o.weno_C; G.tau_eps = o.tau_eps; G.tau_C = o.tau_C;
+    G.viscous_dt = o.viscous_dt;
+    for (int k = 0; k < 4; ++k) {
+      G.bc.kind[k] = d.bc[k].kind;
+      G.bc.uw[k] = d.bc[k].u_wall;
+      G.bc.vw[k] = d.bc[k].v_wall;
+      G.bc.Tw[k] = d.bc[k].T_wall;
+      if (d.bc[k].kind < 0 || d.bc[k].kind > 3) { delete b; return GKS_EINVAL; }
+    }
+    if ((G.bc.kind[0] == GKS_BC_PERIODIC) != (G.bc.kind[1] == GKS_BC_PERIODIC) ||
+        (G.bc.kind[2] == GKS_BC_PERIODIC) != (G.bc.kind[3] == GKS_BC_PERIODIC)) {
+      delete b;
+      return GKS_EINVAL;
+    }
+    GridOff of;
+    of.u = nu; nu += 4 * G.plane;
+    nu = (nu + 31) & ~(size_t)31;
+    of.wx = nwx; nwx += (size_t)8 * d.ny * (d.nx + 1);
+    of.wy = nwy; nwy += (size_t)8 * (d.ny + 1) * d.nx;
+    of.coef = nc; nc += (size_t)20 * d.nx * d.ny;
+    of.fx = nfx; nfx += (size_t)4 * d.ny * (d.nx + 1);
+    of.fy = nfy; nfy += (size_t)4 * (d.ny + 1) * d.nx;
+    of.bad = nbad; nbad += (size_t)d.nx * d.ny;
+    b->geo.push_back(G);
+    b->off.push_back(of);
+    b->cells += (long long)d.nx * d.ny;
+  }
+  b->n_u = nu; b->n_wx = nwx; b->n_wy = nwy; b->n_coef = nc; b->n_fx = nfx; b->n_fy = nfy;
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess) {
+    if (cuda_stream) { b->stream = (cudaStream_t)cuda_stream; b->own_stream = false; }
+    else { e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking); b->own_stream = true; }
+  }
+  const size_t ws = wsize(b);
+  auto alloc = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+  };
+  alloc((void**)&b->d_geo, sizeof(Geo) * n);
+  alloc((void**)&b->d_off, sizeof(GridOff) * n);
+  alloc(&b->d_fc, (b->prec == GKS_FP64 ? sizeof(FaceConst<double>) : sizeof(FaceConst<float>)) * 2 * n);
+  alloc((void**)&b->d_ctrl, sizeof(Ctrl) * n);
+  for (int k = 0; k < 2; ++k) {
+    alloc((void**)&b->U[k], nu * sizeof(double));
+    if (b->prec == GKS_FP32_BULK) alloc((void**)&b->Uf[k], nu * sizeof(float));
+    alloc(&b->Wx[k], nwx * ws);
+    alloc(&b->Wy[k], nwy * ws);
+  }
+  alloc(&b->coef, nc * ws);
+  alloc(&b->Fx, nfx * ws);
+  alloc(&b->Fy, nfy * ws);
+  alloc((void**)&b->bad, nbad);
+  alloc((void**)&b->d_bar, sizeof(Barrier));
+  size_t st = 0;
+  for (int g = 0; g < n; ++g) {
+    const Geo& G = b->geo[g];
+    st = std::max(st, std::max((size_t)4 * G.nx * G.ny, std::max((size_t)8 * G.ny * (G.nx + 1), (size_t)8 * (G.ny + 1) * G.nx)));
+  }
+  b->staging_n = st;
+  alloc((void**)&b->staging, st * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_ctrl, sizeof(Ctrl) * n);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_bar, sizeof(Barrier));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_geo, b->geo.data(), sizeof(Geo) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_off, b->off.data(), sizeof(GridOff) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    if (b->prec == GKS_FP64) {
+      std::vector<FaceConst<double>> fc;
+      for (int g = 0; g < n; ++g) { fc.push_back(grid_face_const<double>(b->geo[g], 0)); fc.push_back(grid_face_const<double>(b->geo[g], 1)); }
+      e = cudaMemcpy(b->d_fc, fc.data(), sizeof(FaceConst<double>) * 2 * n, cudaMemcpyHostToDevice);
+    } else {
+      std::vector<FaceConst<float>> fc;
+      for (int g = 0; g < n; ++g) { fc.push_back(grid_face_const<float>(b->geo[g], 0)); fc.push_back(grid_face_const<float>(b->geo[g], 1)); }
+      e = cudaMemcpy(b->d_fc, fc.data(), sizeof(FaceConst<float>) * 2 * n, cudaMemcpyHostToDevice);
+    }
+  }
+  if (e == cudaSuccess) {
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaMemset(b->U[k], 0, nu * sizeof(double));
+      if (e == cudaSuccess && b->Uf[k]) e = cudaMemset(b->Uf[k], 0, nu * sizeof(float));
+    }
+    // control blocks: t = 0, no bound yet
+    memset(b->h_ctrl, 0, sizeof(Ctrl) * n);
+    const double inf = INFINITY;
+    uint64_t bits;
+    memcpy(&bits, &inf, 8);
+    for (int g = 0; g < n; ++g) b->h_ctrl[g].bound = b->h_ctrl[g].dtb[0] = b->h_ctrl[g].dtb[1] = b->h_ctrl[g].dtb[2] = bits;
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_ctrl, b->h_ctrl, sizeof(Ctrl) * n, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    const gks_status s = e == cudaErrorMemoryAllocation ? GKS_ENOMEM : GKS_ECUDA;
+    gks_batch_destroy(b);
+    return s;
+  }
+  b->max_blocks_per_sm = occupancy(b);
+  b->blocks_per_sm = b->max_blocks_per_sm;
+  if (b->max_blocks_per_sm < 1 || build_items(b) != GKS_OK) {
+    gks_batch_destroy(b);
+    return GKS_ECUDA;
+  }
+  *out = b;
+  return GKS_OK;
+}
+
+gks_status gks_batch_set_state(gks_batch* b, int g, const double* U, const double* Wx, const double* Wy, double t) {
+  if (!b || g < 0 || g >= b->G || !U || !Wx || !Wy) return bfail(b, GKS_EINVAL, "gks_batch_set_state: bad argument");
+  BCK(cudaSetDevice(b->device));
+  const Geo& G = b->geo[g];
+  const GridOff& o = b->off[g];
+  Ctrl& c = b->h_ctrl[g];
+  BCK(cudaMemcpyAsync(&c, b->d_ctrl + g, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  const int par = (int)(c.steps & 1);
+  const dim3 b2(32, 8);
+  BCK(cudaMemcpyAsync(b->staging, U, (size_t)4 * G.nx * G.ny * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  kb_scatter<<<grid2(G.nx, G.ny, b2), b2, 0, b->stream>>>(G, b->staging, b->U[par] + o.u,
+                                                          b->Uf[par] ? b->Uf[par] + o.u : nullptr, 1);
+  kb_ghost<<<(perimeter(G) + 127) / 128, 128, 0, b->stream>>>(G, b->U[par] + o.u, b->Uf[par] ? b->Uf[par] + o.u : nullptr);
+  const size_t nx = (size_t)8 * G.ny * (G.nx + 1), ny = (size_t)8 * (G.ny + 1) * G.nx;
+  BCK(cudaMemcpyAsync(b->staging, Wx, nx * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  if (b->prec == GKS_FP64) kb_copyW<double><<<(unsigned)((nx + 255) / 256), 256, 0, b->stream>>>(b->staging, (double*)b->Wx[par] + o.wx, nx, 1);
+  else kb_copyW<float><<<(unsigned)((nx + 255) / 256), 256, 0, b->stream>>>(b->staging, (float*)b->Wx[par] + o.wx, nx, 1);
+  BCK(cudaMemcpyAsync(b->staging, Wy, ny * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  if (b->prec == GKS_FP64) kb_copyW<double><<<(unsigned)((ny + 255) / 256), 256, 0, b->stream>>>(b->staging, (double*)b->Wy[par] + o.wy, ny, 1);
+  else kb_copyW<float><<<(unsigned)((ny + 255) / 256), 256, 0, b->stream>>>(b->staging, (float*)b->Wy[par] + o.wy, ny, 1);
+  // control block: time t, status cleared, bound of the new state
+  c.t = t;
+  c.status = GKS_OK;
+  c.skip = 0;
+  const double inf = INFINITY;
+  memcpy(&c.bound, &inf, 8);
+  BCK(cudaMemcpyAsync(b->d_ctrl + g, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, b->stream));
+  kb_dtbound<<<grid2(G.nx, G.ny, b2), b2, 0, b->stream>>>(G, b->U[par] + o.u, b->d_ctrl + g);
+  BCK(cudaGetLastError());
+  BCK(cudaMemcpyAsync(&c, b->d_ctrl + g, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  if (c.status != GKS_OK) return bfail(b, GKS_ENONPHYSICAL, "gks_batch_set_state: state has rho <= 0 or p <= 0");
+  return GKS_OK;
+}
+
+gks_status gks_batch_get_state(gks_batch* b, int g, double* U, double* Wx, double* Wy, double* t, long long* steps) {
+  if (!b || g < 0 || g >= b->G) return bfail(b, GKS_EINVAL, "gks_batch_get_state: bad argument");
+  BCK(cudaSetDevice(b->device));
+  const Geo& G = b->geo[g];
+  const GridOff& o = b->off[g];
+  Ctrl& c = b->h_ctrl[g];
+  BCK(cudaMemcpyAsync(&c, b->d_ctrl + g, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  const int par = (int)(c.steps & 1);
+  const dim3 b2(32, 8);
+  if (U) {
+    kb_scatter<<<grid2(G.nx, G.ny, b2), b2, 0, b->stream>>>(G, b->staging, b->U[par] + o.u, nullptr, 0);
+    BCK(cudaMemcpyAsync(U, b->staging, (size_t)4 * G.nx * G.ny * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  }
+  const size_t nx = (size_t)8 * G.ny * (G.nx + 1), ny = (size_t)8 * (G.ny + 1) * G.nx;
+  if (Wx) {
+    if (b->prec == GKS_FP64) kb_copyW<double><<<(unsigned)((nx + 255) / 256), 256, 0, b->stream>>>(b->staging, (double*)b->Wx[par] + o.wx, nx, 0);
+    else kb_copyW<float><<<(unsigned)((nx + 255) / 256), 256, 0, b->stream>>>(b->staging, (float*)b->Wx[par] + o.wx, nx, 0);
+    BCK(cudaMemcpyAsync(Wx, b->staging, nx * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  }
+  if (Wy) {
+    if (b->prec == GKS_FP64) kb_copyW<double><<<(unsigned)((ny + 255) / 256), 256, 0, b->stream>>>(b->staging, (double*)b->Wy[par] + o.wy, ny, 0);
+    else kb_copyW<float><<<(unsigned)((ny + 255) / 256), 256, 0, b->stream>>>(b->staging, (float*)b->Wy[par] + o.wy, ny, 0);
+    BCK(cudaMemcpyAsync(Wy, b->staging, ny * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  }
+  BCK(cudaGetLastError());
+  BCK(cudaStreamSynchronize(b->stream));
+  if (t) *t = c.t;
+  if (steps) *steps = c.steps;
+  if (c.status != GKS_OK) return bfail(b, (gks_status)c.status, "grid state is the last good one");
+  return GKS_OK;
+}
+
+gks_status gks_batch_step(gks_batch* b, int nsteps, double CFL) {
+  if (!b || nsteps < 0 || !(CFL > 0)) return bfail(b, GKS_EINVAL, "gks_batch_step: nsteps >= 0 and CFL > 0 required");
+  if (nsteps == 0) return GKS_OK;
+  BCK(cudaSetDevice(b->device));
+  gks_status st = reset_barrier(b);
+  if (st != GKS_OK) return st;
+  if (!b->graph || b->graph_steps != nsteps || b->graph_cfl != CFL) {
+    drop_graph(b);
+    // capture the persistent launch once; replay it on later calls
+    cudaGraph_t graph = nullptr;
+    b->graph_ok = false;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const gks_status ls = launch_any(b, nsteps, CFL);
+      const cudaError_t ee = cudaStreamEndCapture(b->stream, &graph);
+      if (ls == GKS_OK && ee == cudaSuccess && cudaGraphInstantiate(&b->graph, graph, 0) == cudaSuccess)
+        b->graph_ok = true;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();
+    if (!b->graph_ok) {
+      drop_graph(b);
+      return launch_any(b, nsteps, CFL);  // capture unsupported: plain cooperative launch
+    }
+    b->graph_steps = nsteps;
+    b->graph_cfl = CFL;
+  }
+  BCK(cudaGraphLaunch(b->graph, b->stream));
+  return GKS_OK;
+}
+
+gks_status gks_batch_sync(gks_batch* b, long long* steps_min, long long* steps_max) {
+  if (!b) return GKS_EINVAL;
+  BCK(cudaSetDevice(b->device));
+  BCK(cudaMemcpyAsync(b->h_ctrl, b->d_ctrl, sizeof(Ctrl) * b->G, cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaMemcpyAsync(b->h_bar, b->d_bar, sizeof(Barrier), cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  long long lo = 0, hi = 0;
+  int bad = 0;
+  for (int g = 0; g < b->G; ++g) {
+    const long long s = b->h_ctrl[g].steps;
+    if (g == 0 || s < lo) lo = s;
+    if (g == 0 || s > hi) hi = s;
+    if (b->h_ctrl[g].status != GKS_OK) bad = b->h_ctrl[g].status;
+  }
+  if (steps_min) *steps_min = lo;
+  if (steps_max) *steps_max = hi;
+  if (b->h_bar->error) return bfail(b, (gks_status)b->h_bar->error, "a device barrier wait timed out; the step sequence was abandoned");
+  if (bad) return bfail(b, (gks_status)bad, "a grid produced a non-physical state; that grid stopped");
+  return GKS_OK;
+}
+
+gks_status gks_batch_grid_info(gks_batch* b, int g, double* t, long long* steps, int* status) {
+  if (!b || g < 0 || g >= b->G) return GKS_EINVAL;
+  BCK(cudaMemcpyAsync(&b->h_ctrl[g], b->d_ctrl + g, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  if (t) *t = b->h_ctrl[g].t;
+  if (steps) *steps = b->h_ctrl[g].steps;
+  if (status) *status = b->h_ctrl[g].status;
+  return GKS_OK;
+}
+
+gks_status gks_batch_configure(gks_batch* b, int face_tile_width, int blocks_per_sm) {
+  if (!b) return GKS_EINVAL;
+  if (face_tile_width != 16 && face_tile_width != 32 && face_tile_width != 64 && face_tile_width != 128)
+    return bfail(b, GKS_EINVAL, "face tile width must be 16, 32, 64 or 128");
+  if (blocks_per_sm < 1 || blocks_per_sm > b->max_blocks_per_sm)
+    return bfail(b, GKS_EINVAL, "blocks_per_sm must lie in [1, " + std::to_string(b->max_blocks_per_sm) + "]");
+  BCK(cudaStreamSynchronize(b->stream));
+  drop_graph(b);
+  b->blocks_per_sm = blocks_per_sm;
+  if (face_tile_width != b->face_tw) {
+    b->face_tw = face_tile_width;
+    return build_items(b);
+  }
+  return GKS_OK;
+}
+
+gks_status gks_batch_autotune(gks_batch* b, double CFL, int trial_steps, int* face_tile_width, int* blocks_per_sm,
+                              float* best_ms) {
+  if (!b || !(CFL > 0) || trial_steps < 1) return bfail(b, GKS_EINVAL, "gks_batch_autotune: bad argument");
+  BCK(cudaSetDevice(b->device));
+  // the trials advance the batch; save and restore the state and control blocks
+  const size_t ws = wsize(b);
+  void* save[6] = {nullptr};
+  const size_t sz[6] = {b->n_u * 8, b->n_u * 4, b->n_wx * ws, b->n_wy * ws, sizeof(Ctrl) * (size_t)b->G, 0};
+  BCK(cudaStreamSynchronize(b->stream));
+  BCK(cudaMemcpy(b->h_ctrl, b->d_ctrl, sizeof(Ctrl) * b->G, cudaMemcpyDeviceToHost));
+  for (int k = 0; k < 5; ++k)
+    if (sz[k] && !(k == 1 && !b->Uf[0])) BCK(cudaMalloc(&save[k], 2 * sz[k]));
+  auto snapshot = [&](bool restore) -> gks_status {
+    for (int par = 0; par < 2; ++par) {
+      void* live[4] = {b->U[par], b->Uf[par], b->Wx[par], b->Wy[par]};
+      for (int k = 0; k < 4; ++k) {
+        if (!save[k]) continue;
+        char* s = (char*)save[k] + par * sz[k];
+        if (restore) BCK(cudaMemcpyAsync(live[k], s, sz[k], cudaMemcpyDeviceToDevice, b->stream));
+        else BCK(cudaMemcpyAsync(s, live[k], sz[k], cudaMemcpyDeviceToDevice, b->stream));
+      }
+    }
+    if (restore) BCK(cudaMemcpyAsync(b->d_ctrl, save[4], sz[4], cudaMemcpyDeviceToDevice, b->stream));
+    else BCK(cudaMemcpyAsync(save[4], b->d_ctrl, sz[4], cudaMemcpyDeviceToDevice, b->stream));
+    return GKS_OK;
+  };
+  gks_status st = snapshot(false);
+  const int widths[4] = {16, 32, 64, 128};
+  float best = 1e30f;
+  int bw = b->face_tw, bb = b->blocks_per_sm;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int wi = 0; wi < 4 && st == GKS_OK; ++wi)
+    for (int bps = 1; bps <= b->max_blocks_per_sm && st == GKS_OK; ++bps) {
+      st = gks_batch_configure(b, widths[wi], bps);
+      if (st != GKS_OK) break;
+      st = reset_barrier(b);
+      if (st == GKS_OK) st = launch_any(b, 1, CFL);  // warm-up
+      if (st == GKS_OK) st = reset_barrier(b);
+      cudaEventRecord(e0, b->stream);
+      if (st == GKS_OK) st = launch_any(b, trial_steps, CFL);
+      cudaEventRecord(e1, b->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = bfail(b, GKS_ECUDA, "autotune trial failed");
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      BCK(cudaMemcpy(b->h_bar, b->d_bar, sizeof(Barrier), cudaMemcpyDeviceToHost));
+      if (st == GKS_OK && b->h_bar->error == 0 && ms < best) { best = ms; bw = widths[wi]; bb = bps; }
+      if (st == GKS_OK) st = snapshot(true);
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == GKS_OK) st = gks_batch_configure(b, bw, bb);
+  cudaStreamSynchronize(b->stream);
+  for (int k = 0; k < 5; ++k) cudaFree(save[k]);
+  if (st != GKS_OK) return st;
+  if (face_tile_width) *face_tile_width = bw;
+  if (blocks_per_sm) *blocks_per_sm = bb;
+  if (best_ms) *best_ms = best / trial_steps;
+  return GKS_OK;
+}
+
+gks_status gks_batch_set_wait_limit(gks_batch* b, double seconds, int test_skip_block) {
+  if (!b || !(seconds > 0)) return GKS_EINVAL;
+  BCK(cudaStreamSynchronize(b->stream));
+  drop_graph(b);
+  b->timeout_s = seconds;
+  b->skip_block = test_skip_block;
+  return GKS_OK;
+}
+
+long long gks_batch_cells(const gks_batch* b) { return b ? b->cells : 0; }
+
+int gks_batch_launches_per_call(const gks_batch* b) {
+  (void)b;
+  return 1;
+}
+
+void gks_batch_destroy(gks_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  cudaFree(b->d_geo);
+  cudaFree(b->d_off);
+  cudaFree(b->d_fc);
+  cudaFree(b->d_ctrl);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(b->U[k]);
+    cudaFree(b->Uf[k]);
+    cudaFree(b->Wx[k]);
+    cudaFree(b->Wy[k]);
+  }
+  cudaFree(b->coef);
+  cudaFree(b->Fx);
+  cudaFree(b->Fy);
+  cudaFree(b->bad);
+  cudaFree(b->d_ghost);
+  cudaFree(b->d_cell);
+  cudaFree(b->d_face);
+  cudaFree(b->d_bar);
+  cudaFree(b->staging);
+  if (b->h_ctrl) cudaFreeHost(b->h_ctrl);
+  if (b->h_bar) cudaFreeHost(b->h_bar);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+const char* gks_batch_last_error(const gks_batch* b) { return b ? b->err.c_str() : ""; }
+
+}  // extern "C"

@@ -19,13 +19,18 @@
 namespace gks {
 
 template <class R> struct Prec;
+// series_below: x = dt/tau below which the time weights are summed from series;
+// tie: relative width within which two cross-derivative candidates count as equal
+// (far above the rounding noise of the precision, far below any real difference)
 template <> struct Prec<double> {
-  static constexpr double series_below = 0.5;  // x = dt/tau below which series are used
+  static constexpr double series_below = 0.5;
   static constexpr int series_terms = 22;
+  static constexpr double tie = 1e-8;
 };
 template <> struct Prec<float> {
   static constexpr float series_below = 2.0f;
   static constexpr int series_terms = 24;
+  static constexpr float tie = 1e-4f;
 };
 
 __device__ __forceinline__ double d_exp(double x) { return exp(x); }
@@ -664,9 +669,10 @@ GKS_FN void recon_var(R c, R e, R w, R n, R s, R em, R ep, R wm, R wp, R nm, R n
   const R r3 = R(1.7320508075688772) * idx * idy;
   const R xe = r3 * (ep - em) - a3 * idx, xw = r3 * (wp - wm) - a3 * idx;
   const R yn = r3 * (np - nm) - a2 * idy, ys = r3 * (sp - sm) - a2 * idy;
-  // magnitudes within a relative 1e-8 of the current choice are ties (piecewise
-  // constant data give exact ties of opposite sign); the earlier stencil is kept
-  const R keep = R(1) - R(1e-8);
+  // magnitudes within a relative Prec<R>::tie of the current choice are ties
+  // (piecewise constant data give exact ties of opposite sign); the earlier
+  // stencil is kept
+  const R keep = R(1) - R(Prec<R>::tie);
   R a6 = xe + yn;        // (+, +)
   R cand = -xw + yn;     // (-, +)
   if (fabs(cand) < fabs(a6) * keep) a6 = cand;

@@ -1,0 +1,544 @@
+// Grid-level device work of one time step, per element: the ghost ring, the
+// reconstruction of one cell, the evolution at one face and the update of one
+// cell.  The single-grid kernels (gks.cu) and the persistent batched kernel
+// (gks_batch.cu) both call these, so both compute the same arithmetic.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "../../include/gks.h"
+#include "gks_device.cuh"
+
+namespace gks {
+
+// per-grid control block; every step's scalars stay on the device
+struct Ctrl {
+  unsigned long long bound;   // CFL bound (FP64 bits) of the current state
+  unsigned long long dtb[3];  // running minima of the CFL bound of each update pass of the step
+  double t;
+  double dt;
+  long long steps;
+  int status;
+  int skip;
+  long long fail_step;
+  int bad_found[2];           // update pass 1 / 2 left a cell non-physical
+};
+
+struct BCs {
+  int kind[4];
+  double uw[4], vw[4], Tw[4];
+};
+
+struct Geo {
+  int nx, ny, pitch;  // pitch: row length of the padded cell arrays
+  size_t plane;       // (ny+2) * pitch
+  double dx, dy;
+  double gamma, mu, Pr;
+  double weno_eps, weno_C, tau_eps, tau_C;
+  int viscous_dt;
+  BCs bc;
+};
+
+__host__ __device__ __forceinline__ size_t ci(const Geo& g, int v, int i, int j) {
+  return (size_t)v * g.plane + (size_t)(j + 1) * g.pitch + (i + 1);
+}
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// ---------------------------------------------------------------------------
+// control: dt of the coming step from the running minimum, and its end
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ctrl_begin(Ctrl* c, double cfl, double dt_max, double t_end) {
+  double dt = fmin(cfl * bitsd(c->bound), dt_max);
+  dt = fmin(dt, t_end - c->t);
+  c->dt = dt;
+  c->skip = (c->status != GKS_OK || !(dt > 0.0)) ? 1 : 0;
+  c->dtb[0] = c->dtb[1] = c->dtb[2] = dbits(INFINITY);
+  c->bad_found[0] = c->bad_found[1] = 0;
+}
+
+// the update pass whose state the step keeps: 1, or 2 / 3 after the fallbacks
+__device__ __forceinline__ int last_pass(const Ctrl* c) { return c->bad_found[1] ? 3 : (c->bad_found[0] ? 2 : 1); }
+
+__device__ __forceinline__ void ctrl_end(Ctrl* c) {
+  if (c->skip || c->status != GKS_OK) return;
+  c->bound = c->dtb[last_pass(c) - 1];
+  c->t += c->dt;
+  c->steps += 1;
+}
+
+// ---------------------------------------------------------------------------
+// boundary images of cell averages (ghost ring)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bc_value(int kind, double gamma, double uwt, double Tw, int axis, const double in[4],
+                                         double out[4]) {
+  if (kind == GKS_BC_PERIODIC || kind == GKS_BC_OUTFLOW) {
+    for (int k = 0; k < 4; ++k) out[k] = in[k];
+    return;
+  }
+  double f[4];
+  f[0] = in[0];
+  f[3] = in[3];
+  f[1] = axis == 0 ? in[1] : in[2];
+  f[2] = axis == 0 ? in[2] : in[1];
+  double o[4];
+  if (kind == GKS_BC_SLIPWALL) {
+    o[0] = f[0]; o[1] = -f[1]; o[2] = f[2]; o[3] = f[3];
+  } else {
+    const double rho = f[0], mn = f[1], mt = f[2];
+    o[0] = rho;
+    o[1] = -mn;
+    o[2] = 2.0 * rho * uwt - mt;
+    o[3] = 2.0 * rho * uwt * uwt - 2.0 * uwt * mt + (mn * mn + mt * mt) / rho +
+           2.0 * rho * Tw / (gamma - 1.0) - f[3];
+  }
+  out[0] = o[0];
+  out[3] = o[3];
+  out[1] = axis == 0 ? o[1] : o[2];
+  out[2] = axis == 0 ? o[2] : o[1];
+}
+
+__host__ __device__ __forceinline__ double wall_t_velocity(const BCs& b, int side) {
+  // tangential wall velocity in the face frame: y-component on x-sides, x on y-sides
+  return side < 2 ? b.vw[side] : b.uw[side];
+}
+
+// value of a ghost cell; y is resolved first, so corners are x-images of y-ghosts
+__device__ __forceinline__ void ghost_cell(const Geo& g, const double* __restrict__ U, int i, int j, double out[4]) {
+  int is = i, js = j;
+  int xs = -1, ys = -1;  // boundary side applied
+  if (j < 0) { ys = 2; js = g.bc.kind[2] == GKS_BC_PERIODIC ? g.ny - 1 : 0; }
+  if (j >= g.ny) { ys = 3; js = g.bc.kind[3] == GKS_BC_PERIODIC ? 0 : g.ny - 1; }
+  if (i < 0) { xs = 0; is = g.bc.kind[0] == GKS_BC_PERIODIC ? g.nx - 1 : 0; }
+  if (i >= g.nx) { xs = 1; is = g.bc.kind[1] == GKS_BC_PERIODIC ? 0 : g.nx - 1; }
+  double w[4], t[4];
+  for (int v = 0; v < 4; ++v) w[v] = U[ci(g, v, is, js)];
+  if (ys >= 0) {
+    bc_value(g.bc.kind[ys], g.gamma, wall_t_velocity(g.bc, ys), g.bc.Tw[ys], 1, w, t);
+    for (int v = 0; v < 4; ++v) w[v] = t[v];
+  }
+  if (xs >= 0) {
+    bc_value(g.bc.kind[xs], g.gamma, wall_t_velocity(g.bc, xs), g.bc.Tw[xs], 0, w, t);
+    for (int v = 0; v < 4; ++v) w[v] = t[v];
+  }
+  for (int v = 0; v < 4; ++v) out[v] = w[v];
+}
+
+__host__ __device__ __forceinline__ int perimeter(const Geo& g) { return 2 * (g.nx + 2) + 2 * g.ny; }
+
+// p-th cell of the ghost ring: fill U (and the FP32 mirror Uf if given)
+__device__ __forceinline__ void ghost_at(const Geo& g, double* U, float* Uf, int p) {
+  const int row = g.nx + 2;
+  int i, j;
+  if (p < row) { i = p - 1; j = -1; }
+  else if (p < 2 * row) { i = p - row - 1; j = g.ny; }
+  else if (p < 2 * row + g.ny) { i = -1; j = p - 2 * row; }
+  else if (p < 2 * row + 2 * g.ny) { i = g.nx; j = p - 2 * row - g.ny; }
+  else return;
+  double w[4];
+  ghost_cell(g, U, i, j, w);
+  for (int v = 0; v < 4; ++v) {
+    U[ci(g, v, i, j)] = w[v];
+    if (Uf) Uf[ci(g, v, i, j)] = (float)w[v];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// reconstruction of cell (i, j); U is the padded cell-average array in the
+// compute type, Wx/Wy the face point values; writes coef[5][4][ny][nx]
+// ---------------------------------------------------------------------------
+template <class R, class TW>
+__device__ __forceinline__ void recon_cell(const Geo& g, const R* __restrict__ U, const TW* __restrict__ Wx,
+                                           const TW* __restrict__ Wy, R* __restrict__ coef, int i, int j, R dx,
+                                           R dy, R weps, R wC, R gm1) {
+  const int nx = g.nx, ny = g.ny;
+  const size_t fxp = (size_t)ny * (nx + 1), fyp = (size_t)(ny + 1) * nx;
+  R a[4][5];
+  R cbar[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const R cc = U[ci(g, v, i, j)];
+    cbar[v] = cc;
+    const TW* wx = Wx + (size_t)v * 2 * fxp + (size_t)j * (nx + 1);
+    const TW* wy = Wy + (size_t)v * 2 * fyp;
+    recon_var<R>(cc, U[ci(g, v, i + 1, j)], U[ci(g, v, i - 1, j)], U[ci(g, v, i, j + 1)], U[ci(g, v, i, j - 1)],
+                 R(wx[i + 1]), R(wx[fxp + i + 1]), R(wx[i]), R(wx[fxp + i]), R(wy[(size_t)(j + 1) * nx + i]),
+                 R(wy[fyp + (size_t)(j + 1) * nx + i]), R(wy[(size_t)j * nx + i]), R(wy[fyp + (size_t)j * nx + i]),
+                 dx, dy, weps, wC, a[v]);
+  }
+  // positivity: rho and p at the four face centres, else the constant average
+  bool bad = false;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    R w[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const R x = f == 0 ? R(0.5) * dx : (f == 1 ? -R(0.5) * dx : R(0));
+      const R y = f == 2 ? R(0.5) * dy : (f == 3 ? -R(0.5) * dy : R(0));
+      w[v] = cbar[v] + a[v][0] * x + a[v][1] * y + a[v][2] * R(0.5) * (x * x - dx * dx / R(12)) +
+             a[v][3] * R(0.5) * (y * y - dy * dy / R(12)) + a[v][4] * x * y;
+    }
+    const R p = gm1 * (w[3] - R(0.5) * (w[1] * w[1] + w[2] * w[2]) / w[0]);
+    if (!(w[0] > R(0)) || !(p > R(0))) bad = true;
+  }
+  const size_t N = (size_t)nx * ny, o = (size_t)j * nx + i;
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) coef[(size_t)(k * 4 + v) * N + o] = bad ? R(0) : a[v][k];
+}
+
+// ---------------------------------------------------------------------------
+// face evolution
+// ---------------------------------------------------------------------------
+// face-frame slot of physical variable v (y-faces swap the momenta)
+template <int AX> __device__ __forceinline__ int slot(int v) { return AX == 0 ? v : (v == 1 ? 2 : (v == 2 ? 1 : v)); }
+
+// value and derivatives of cell (i, j)'s polynomial at the centre of its face
+// on side s (+1: the face at +h_n/2, -1: at -h_n/2), in the face frame of axis AX
+template <int AX, class R>
+__device__ __forceinline__ void side_state(const Geo& g, const R* __restrict__ U, const R* __restrict__ coef,
+                                           int i, int j, int s, R hn, R ht, FaceState<R>& S) {
+  const size_t N = (size_t)g.nx * g.ny, o = (size_t)j * g.nx + i;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const R c = U[ci(g, v, i, j)];
+    const R a2 = coef[(size_t)(0 * 4 + v) * N + o], a3 = coef[(size_t)(1 * 4 + v) * N + o];
+    const R a4 = coef[(size_t)(2 * 4 + v) * N + o], a5 = coef[(size_t)(3 * 4 + v) * N + o];
+    const R a6 = coef[(size_t)(4 * 4 + v) * N + o];
+    const R an = AX == 0 ? a2 : a3, at = AX == 0 ? a3 : a2;
+    const R ann = AX == 0 ? a4 : a5, att = AX == 0 ? a5 : a4;
+    const int k = slot<AX>(v);
+    const R sh = R(s) * R(0.5) * hn;
+    S.w[0][k] = c + an * sh + ann * hn * hn / R(12) - att * ht * ht / R(24);
+    S.w[1][k] = an + ann * sh;
+    S.w[2][k] = at + a6 * sh;
+    S.w[3][k] = ann;
+    S.w[4][k] = a6;
+    S.w[5][k] = att;
+  }
+}
+
+// Inputs of one face, fetched on demand by face_evolution
+template <int AX, class R>
+struct GridFaceSource {
+  const Geo* g;
+  const R* U;
+  const R* coef;
+  int i, j;            // face index (x-faces: i in [0, nx]; y-faces: j in [0, ny])
+  int cl, cr;          // the two cells along the normal, after periodic wrap
+  int img_lo, img_hi;  // boundary image on the low / high side: 0 none, else the BC kind
+  R hn, ht, gamma, uwt_lo, Tw_lo, uwt_hi, Tw_hi;
+
+  __device__ __forceinline__ int cx(int n) const { return AX == 0 ? n : i; }
+  __device__ __forceinline__ int cy(int n) const { return AX == 0 ? j : n; }
+
+  __device__ __forceinline__ void image(int kind, R uwt, R Tw, const FaceState<R>& in, FaceState<R>& out) const {
+    if (kind == GKS_BC_OUTFLOW) out = in;
+    else wall_image<R>(kind, gamma, uwt, Tw, in, out);
+  }
+
+  bool first_order;  // constant states (cell averages) for the positivity fallback
+
+  // the average of cell n (along the normal) as a constant face state
+  __device__ __forceinline__ void const_state(int n, FaceState<R>& S) const {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      S.w[0][slot<AX>(v)] = U[ci(*g, v, cx(n), cy(n))];
+#pragma unroll
+      for (int d = 1; d < 6; ++d) S.w[d][v] = R(0);
+    }
+  }
+
+  __device__ __forceinline__ void side(int k, FaceState<R>& S) const {
+    if (first_order) {
+      if (k == 0) {
+        if (img_lo) {
+          FaceState<R> in;
+          const_state(cr, in);
+          image(img_lo, uwt_lo, Tw_lo, in, S);
+        } else {
+          const_state(cl, S);
+        }
+      } else {
+        if (img_hi) {
+          FaceState<R> in;
+          const_state(cl, in);
+          image(img_hi, uwt_hi, Tw_hi, in, S);
+        } else {
+          const_state(cr, S);
+        }
+      }
+      return;
+    }
+    if (k == 0) {
+      if (img_lo) {
+        FaceState<R> in;
+        side_state<AX>(*g, U, coef, cx(cr), cy(cr), -1, hn, ht, in);
+        image(img_lo, uwt_lo, Tw_lo, in, S);
+      } else {
+        side_state<AX>(*g, U, coef, cx(cl), cy(cl), +1, hn, ht, S);
+      }
+    } else {
+      if (img_hi) {
+        FaceState<R> in;
+        side_state<AX>(*g, U, coef, cx(cl), cy(cl), +1, hn, ht, in);
+        image(img_hi, uwt_hi, Tw_hi, in, S);
+      } else {
+        side_state<AX>(*g, U, coef, cx(cr), cy(cr), -1, hn, ht, S);
+      }
+    }
+  }
+
+  // six cell averages around the face (ghost ring included), face frame
+  __device__ __forceinline__ void avg(R a[2][3][4]) const {
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int ii = AX == 0 ? i - 1 + m : i - 1 + k;
+        const int jj = AX == 0 ? j - 1 + k : j - 1 + m;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) a[m][k][slot<AX>(v)] = U[ci(*g, v, ii, jj)];
+      }
+  }
+};
+
+// per-launch constants of the face routine for axis AX of grid g
+template <class R>
+__host__ __device__ inline FaceConst<R> grid_face_const(const Geo& g, int axis) {
+  FaceParams P;
+  P.gamma = g.gamma; P.mu = g.mu; P.Pr = g.Pr; P.tau_eps = g.tau_eps; P.tau_C = g.tau_C;
+  P.dn = axis == 0 ? g.dx : g.dy;
+  P.dtan = axis == 0 ? g.dy : g.dx;
+  return face_const<R>(P);
+}
+
+// the evolution at face (i, j) of axis AX: flux F and new point values Wn
+template <int AX, class R, class TW>
+__device__ __forceinline__ void flux_face(const Geo& g, const FaceConst<R>& C, const R* U, const R* __restrict__ coef,
+                                          TW* __restrict__ Wn, R* __restrict__ F, int i, int j, R dt) {
+  const int nx = g.nx, ny = g.ny;
+  const int fx = AX == 0 ? nx + 1 : nx, fy = AX == 0 ? ny : ny + 1;
+  GridFaceSource<AX, R> src;
+  src.g = &g;
+  src.U = U;
+  src.coef = coef;
+  src.i = i;
+  src.j = j;
+  const int f = AX == 0 ? i : j;     // face index along the normal
+  const int nf = AX == 0 ? nx : ny;  // faces 0 and nf are on the boundary
+  const int lo_side = AX == 0 ? 0 : 2, hi_side = lo_side + 1;
+  src.cl = f - 1;
+  src.cr = f;
+  src.img_lo = src.img_hi = 0;
+  if (f == 0) {
+    if (g.bc.kind[lo_side] == GKS_BC_PERIODIC) src.cl = nf - 1;
+    else src.img_lo = g.bc.kind[lo_side];
+  }
+  if (f == nf) {
+    if (g.bc.kind[hi_side] == GKS_BC_PERIODIC) src.cr = 0;
+    else src.img_hi = g.bc.kind[hi_side];
+  }
+  src.hn = C.dn;
+  src.ht = C.dtan;
+  src.gamma = C.gamma;
+  src.uwt_lo = R(wall_t_velocity(g.bc, lo_side));
+  src.Tw_lo = R(g.bc.Tw[lo_side]);
+  src.uwt_hi = R(wall_t_velocity(g.bc, hi_side));
+  src.Tw_hi = R(g.bc.Tw[hi_side]);
+  src.first_order = false;
+
+  R Fl[4], Wm[4], Wp[4];
+  face_evolution<R>(C, src, dt, Fl, Wm, Wp);
+
+  const size_t nfaces = (size_t)fx * fy, o = (size_t)j * fx + i;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int k = slot<AX>(v);
+    F[(size_t)v * nfaces + o] = Fl[k];
+    Wn[(size_t)(v * 2 + 0) * nfaces + o] = TW(Wm[k]);
+    Wn[(size_t)(v * 2 + 1) * nfaces + o] = TW(Wp[k]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// update, CFL bound of the new state, physical check
+// ---------------------------------------------------------------------------
+// inverse CFL bound max((|U|+c)/dx, (|V|+c)/dy) (and the viscous rate) of a state;
+// ok = rho > 0 and p > 0.  The bound itself is 1/inverse.
+template <class R>
+__device__ __forceinline__ R inv_bound(const Geo& g, const R w[4], bool& ok) {
+  const R ir = R(1) / w[0];
+  const R u = w[1] * ir, v = w[2] * ir;
+  const R p = R(g.gamma - 1.0) * (w[3] - R(0.5) * (w[1] * u + w[2] * v));
+  ok = w[0] > R(0) && p > R(0);
+  const R c = sqrt(R(g.gamma) * p * ir);
+  R inv = fmax((fabs(u) + c) * R(1.0 / g.dx), (fabs(v) + c) * R(1.0 / g.dy));
+  if (g.viscous_dt && g.mu > 0.0) {
+    const double h = fmin(g.dx, g.dy);
+    inv = fmax(inv, R(2.0 * g.mu * fmax(4.0 / 3.0, g.gamma / g.Pr) / (h * h)) * ir);
+  }
+  return inv;
+}
+
+// block maximum of inv, then the atomic minimum of the bound 1/inv.  Every
+// thread of the block must call it.
+template <class R>
+__device__ __forceinline__ void block_bound_to(R inv, unsigned long long* slot) {
+  __shared__ R red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) inv = fmax(inv, __shfl_xor_sync(0xffffffffu, inv, o));
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = t & 31, warp = t >> 5;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+  if (lane == 0) red[warp] = inv;
+  __syncthreads();
+  if (warp == 0) {
+    inv = lane < nw ? red[lane] : R(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) inv = fmax(inv, __shfl_xor_sync(0xffffffffu, inv, o));
+    if (lane == 0 && inv > R(0)) atomicMin(slot, dbits(1.0 / (double)inv));
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// positivity fallback: the collisionless (tau -> infinity) evolution of the
+// two cell averages at face (i, j) of axis AX -- flux dt (rho_l <u psi>_{u>0} +
+// rho_r <u psi>_{u<0}) and point values U0 -- in the physical frame
+// ---------------------------------------------------------------------------
+template <int AX, class R>
+__device__ __forceinline__ void kfvs_face(const Geo& g, const R* U, R gm1, R K, int i, int j, R dt, R F[4],
+                                          R W[4]) {
+  GridFaceSource<AX, R> src;
+  src.g = &g;
+  src.U = U;
+  src.coef = nullptr;
+  src.i = i;
+  src.j = j;
+  const int f = AX == 0 ? i : j, nf = AX == 0 ? g.nx : g.ny;
+  const int lo_side = AX == 0 ? 0 : 2, hi_side = lo_side + 1;
+  src.cl = f - 1;
+  src.cr = f;
+  src.img_lo = src.img_hi = 0;
+  if (f == 0) {
+    if (g.bc.kind[lo_side] == GKS_BC_PERIODIC) src.cl = nf - 1;
+    else src.img_lo = g.bc.kind[lo_side];
+  }
+  if (f == nf) {
+    if (g.bc.kind[hi_side] == GKS_BC_PERIODIC) src.cr = 0;
+    else src.img_hi = g.bc.kind[hi_side];
+  }
+  src.gamma = R(g.gamma);
+  src.uwt_lo = R(wall_t_velocity(g.bc, lo_side));
+  src.Tw_lo = R(g.bc.Tw[lo_side]);
+  src.uwt_hi = R(wall_t_velocity(g.bc, hi_side));
+  src.Tw_hi = R(g.bc.Tw[hi_side]);
+  src.first_order = true;
+  R Ff[4] = {R(0), R(0), R(0), R(0)}, Wf[4] = {R(0), R(0), R(0), R(0)};
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    FaceState<R> S;
+    src.side(k, S);
+    R rho, u, v, p;
+    prim(S.w[0], gm1, rho, u, v, p);
+    Moments<R, 4, 3> m;
+    moments(u, v, R(0.5) * rho / p, K, k == 0 ? +1 : -1, m);
+    R a[4], b[4];
+    psi_mom<0, 0>(m, a);
+    psi_mom<1, 0>(m, b);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      Wf[q] += rho * a[q];
+      Ff[q] += dt * rho * b[q];
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    F[v] = Ff[slot<AX>(v)];
+    W[v] = Wf[slot<AX>(v)];
+  }
+}
+
+// positivity fallback: is face (i, j) of axis AX next to a marked cell?
+template <int AX>
+__device__ __forceinline__ bool face_needs_fix(const Geo& g, const unsigned char* bad, int i, int j) {
+  const int f = AX == 0 ? i : j, nf = AX == 0 ? g.nx : g.ny;
+  const int lo_side = AX == 0 ? 0 : 2;
+  int a = f - 1, b = f;
+  if (f == 0) a = g.bc.kind[lo_side] == GKS_BC_PERIODIC ? nf - 1 : -1;
+  if (f == nf) b = g.bc.kind[lo_side + 1] == GKS_BC_PERIODIC ? 0 : -1;
+  const int c0 = a < 0 ? -1 : (AX == 0 ? j * g.nx + a : a * g.nx + i);
+  const int c1 = b < 0 ? -1 : (AX == 0 ? j * g.nx + b : b * g.nx + i);
+  return (c0 >= 0 && bad[c0]) || (c1 >= 0 && bad[c1]);
+}
+
+// Eq. finite for cell (i, j) into Un (and the FP32 mirror Ufn if given); returns
+// the inverse CFL bound of the new state, 0 with bad = true if it is not
+// physical.  pass 1 takes every face flux from Fx/Fy; pass 2 replaces the faces
+// next to cells marked in pass 1 by the collisionless flux; pass 3 replaces
+// every face.  Replaced faces also get their point values in Wxn/Wyn, written
+// by one cell each (its west and south faces, and the east / north faces of
+// the last column / row).
+template <class R, class TW>
+__device__ __forceinline__ R update_cell(const Geo& g, const double* __restrict__ U, double* __restrict__ Un,
+                                         float* __restrict__ Ufn, const R* __restrict__ Ur, const R* __restrict__ Fx,
+                                         const R* __restrict__ Fy, TW* __restrict__ Wxn, TW* __restrict__ Wyn,
+                                         const unsigned char* __restrict__ marked, int pass, R dt, int i, int j,
+                                         bool& bad) {
+  const int nx = g.nx, ny = g.ny;
+  const size_t nfx = (size_t)ny * (nx + 1), nfy = (size_t)(ny + 1) * nx;
+  const double idx = 1.0 / g.dx, idy = 1.0 / g.dy;
+  // the four face fluxes: west, east, south, north
+  R f[4][4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    f[0][v] = Fx[v * nfx + (size_t)j * (nx + 1) + i];
+    f[1][v] = Fx[v * nfx + (size_t)j * (nx + 1) + i + 1];
+    f[2][v] = Fy[v * nfy + (size_t)j * nx + i];
+    f[3][v] = Fy[v * nfy + (size_t)(j + 1) * nx + i];
+  }
+  if (pass > 1) {
+    const R gm1 = R(g.gamma - 1.0), K = R((4.0 - 2.0 * g.gamma) / (g.gamma - 1.0));
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      const int fi = i + (q == 1), fj = j + (q == 3);
+      const bool x = q < 2;
+      const bool redo = pass == 3 || (x ? face_needs_fix<0>(g, marked, fi, fj) : face_needs_fix<1>(g, marked, fi, fj));
+      if (!redo) continue;
+      R W[4];
+      if (x) kfvs_face<0, R>(g, Ur, gm1, K, fi, fj, dt, f[q], W);
+      else kfvs_face<1, R>(g, Ur, gm1, K, fi, fj, dt, f[q], W);
+      const bool owner = q == 0 || q == 2 || (q == 1 && i == nx - 1) || (q == 3 && j == ny - 1);
+      if (owner) {
+        TW* Wn = x ? Wxn : Wyn;
+        const size_t nf = x ? nfx : nfy;
+        const size_t o = x ? (size_t)fj * (nx + 1) + fi : (size_t)fj * nx + fi;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          Wn[(size_t)(v * 2 + 0) * nf + o] = TW(W[v]);
+          Wn[(size_t)(v * 2 + 1) * nf + o] = TW(W[v]);
+        }
+      }
+    }
+  }
+  double w[4];
+  R wr[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    // Eq. finite in FP64: differences of the (possibly FP32) face fluxes are exact in
+    // FP64, so the face fluxes telescope and the update stays conservative
+    w[v] = U[ci(g, v, i, j)] + ((double)f[0][v] - (double)f[1][v]) * idx + ((double)f[2][v] - (double)f[3][v]) * idy;
+    Un[ci(g, v, i, j)] = w[v];
+    wr[v] = R(w[v]);
+    if (Ufn) Ufn[ci(g, v, i, j)] = (float)wr[v];
+  }
+  bool ok;
+  R inv = inv_bound<R>(g, wr, ok);
+  bad = !ok || !isfinite(w[0]) || !isfinite(w[1]) || !isfinite(w[2]) || !isfinite(w[3]) || !(inv < R(INFINITY));
+  return bad ? R(0) : inv;
+}
+
+}  // namespace gks

@@ -56,10 +56,12 @@ namespace gks {
 template <> struct Prec<opc::Num<0>> {
   static constexpr double series_below = Prec<double>::series_below;
   static constexpr int series_terms = Prec<double>::series_terms;
+  static constexpr double tie = Prec<double>::tie;
 };
 template <> struct Prec<opc::Num<1>> {
   static constexpr double series_below = Prec<float>::series_below;
   static constexpr int series_terms = Prec<float>::series_terms;
+  static constexpr double tie = Prec<float>::tie;
 };
 }  // namespace gks
 

@@ -32,6 +32,11 @@ class gks_options(ctypes.Structure):
                 ("tau_eps", ctypes.c_double), ("tau_C", ctypes.c_double), ("viscous_dt", ctypes.c_int)]
 
 
+class gks_grid_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("Lx", ctypes.c_double), ("Ly", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("mu", ctypes.c_double), ("bc", gks_bc * 4)]
+
+
 class GKSError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
@@ -76,6 +81,30 @@ def load(path: str | None = None):
     L.gks_step_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, D, D, D, D, D, ctypes.POINTER(gks_bc),
                                    ctypes.POINTER(gks_options), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, D, D,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _dp, ctypes.c_void_p]
+    B = ctypes.c_void_p
+    LL = ctypes.POINTER(ctypes.c_longlong)
+    L.gks_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(gks_grid_desc), ctypes.POINTER(gks_options),
+                                   ctypes.c_void_p, ctypes.POINTER(B)]
+    L.gks_batch_set_state.argtypes = [B, ctypes.c_int, _dp, _dp, _dp, D]
+    L.gks_batch_get_state.argtypes = [B, ctypes.c_int, _dp, _dp, _dp, _dp, LL]
+    L.gks_batch_step.argtypes = [B, ctypes.c_int, D]
+    L.gks_batch_sync.argtypes = [B, LL, LL]
+    L.gks_batch_grid_info.argtypes = [B, ctypes.c_int, _dp, LL, ctypes.POINTER(ctypes.c_int)]
+    L.gks_batch_configure.argtypes = [B, ctypes.c_int, ctypes.c_int]
+    L.gks_batch_autotune.argtypes = [B, D, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_float)]
+    L.gks_batch_set_wait_limit.argtypes = [B, D, ctypes.c_int]
+    L.gks_batch_cells.argtypes = [B]
+    L.gks_batch_cells.restype = ctypes.c_longlong
+    L.gks_batch_launches_per_call.argtypes = [B]
+    L.gks_batch_destroy.argtypes = [B]
+    L.gks_batch_destroy.restype = None
+    L.gks_batch_last_error.argtypes = [B]
+    L.gks_batch_last_error.restype = ctypes.c_char_p
+    for name in ("gks_batch_create", "gks_batch_set_state", "gks_batch_get_state", "gks_batch_step", "gks_batch_sync",
+                 "gks_batch_grid_info", "gks_batch_configure", "gks_batch_autotune", "gks_batch_set_wait_limit",
+                 "gks_batch_launches_per_call"):
+        getattr(L, name).restype = ctypes.c_int
     L.gks_debug_recon.argtypes = [H, _dp]
     L.gks_debug_flux.argtypes = [H, D, _dp, _dp, _dp, _dp]
     for name in ("gks_create", "gks_set_state", "gks_set_state_device", "gks_step", "gks_advance", "gks_sync",
@@ -197,12 +226,12 @@ def gks_launches_per_step(h) -> int:
     return load().gks_launches_per_step(h)
 
 
-KERNEL_NAMES = ["begin", "ghost", "recon", "flux_x", "flux_y", "update", "end"]
+KERNEL_NAMES = ["begin", "ghost", "recon", "flux_x", "flux_y", "update", "update2", "update3", "end"]
 
 
 def gks_profile_step(h, CFL):
     """One step with per-kernel CUDA-event timing; returns {kernel name: ms}."""
-    ms = (ctypes.c_float * 7)()
+    ms = (ctypes.c_float * 9)()
     _check(h, load().gks_profile_step(h, float(CFL), ms))
     return dict(zip(KERNEL_NAMES, list(ms)))
 
@@ -273,6 +302,118 @@ class Solver:
         if self.h:
             gks_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- batched form ----
+
+def _bcheck(b, st):
+    if st != GKS_OK:
+        raise GKSError(st, load().gks_batch_last_error(b).decode() if b else "")
+
+
+def grid_desc(p) -> gks_grid_desc:
+    d = gks_grid_desc()
+    d.nx, d.ny, d.Lx, d.Ly, d.gamma, d.Pr, d.mu = p.nx, p.ny, p.Lx, p.Ly, p.gamma, p.Pr, p.mu
+    bcs = make_bcs(p.bc)
+    for k in range(4):
+        d.bc[k] = bcs[k]
+    return d
+
+
+def gks_batch_create(problems, options=None, stream=None):
+    arr = (gks_grid_desc * len(problems))(*[grid_desc(p) for p in problems])
+    b = ctypes.c_void_p()
+    st = load().gks_batch_create(len(problems), arr, ctypes.byref(options) if options is not None else None,
+                                 ctypes.c_void_p(stream) if stream else None, ctypes.byref(b))
+    _bcheck(None, st)
+    return b
+
+
+def gks_batch_set_state(b, g, U, Wx, Wy, t=0.0):
+    _bcheck(b, load().gks_batch_set_state(b, int(g), _ptr(U), _ptr(Wx), _ptr(Wy), float(t)))
+
+
+def gks_batch_get_state(b, g, U=None, Wx=None, Wy=None):
+    t = ctypes.c_double(0.0)
+    n = ctypes.c_longlong(0)
+    _bcheck(b, load().gks_batch_get_state(b, int(g), _ptr(U), _ptr(Wx), _ptr(Wy), ctypes.byref(t), ctypes.byref(n)))
+    return t.value, n.value
+
+
+def gks_batch_step(b, nsteps, CFL):
+    _bcheck(b, load().gks_batch_step(b, int(nsteps), float(CFL)))
+
+
+def gks_batch_sync(b):
+    lo, hi = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    _bcheck(b, load().gks_batch_sync(b, ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+def gks_batch_grid_info(b, g):
+    t, n, s = ctypes.c_double(0.0), ctypes.c_longlong(0), ctypes.c_int(0)
+    _bcheck(b, load().gks_batch_grid_info(b, int(g), ctypes.byref(t), ctypes.byref(n), ctypes.byref(s)))
+    return t.value, n.value, s.value
+
+
+def gks_batch_configure(b, face_tile_width, blocks_per_sm):
+    _bcheck(b, load().gks_batch_configure(b, int(face_tile_width), int(blocks_per_sm)))
+
+
+def gks_batch_autotune(b, CFL, trial_steps=2):
+    w, k, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_float(0.0)
+    _bcheck(b, load().gks_batch_autotune(b, float(CFL), int(trial_steps), ctypes.byref(w), ctypes.byref(k),
+                                         ctypes.byref(ms)))
+    return w.value, k.value, ms.value
+
+
+def gks_batch_set_wait_limit(b, seconds, test_skip_block=-1):
+    _bcheck(b, load().gks_batch_set_wait_limit(b, float(seconds), int(test_skip_block)))
+
+
+def gks_batch_cells(b) -> int:
+    return load().gks_batch_cells(b)
+
+
+def gks_batch_destroy(b):
+    if b:
+        load().gks_batch_destroy(b)
+
+
+class Batch:
+    """Independent grids (workloads.Problem list) advanced together in one persistent launch."""
+
+    def __init__(self, problems, precision=GKS_FP64, stream=None, **opts):
+        self.problems = list(problems)
+        self.b = gks_batch_create(self.problems, gks_default_options(precision, **opts), stream)
+        for g, p in enumerate(self.problems):
+            gks_batch_set_state(self.b, g, np.ascontiguousarray(p.U), np.ascontiguousarray(p.Wx),
+                                np.ascontiguousarray(p.Wy), 0.0)
+
+    def step(self, nsteps, CFL):
+        gks_batch_step(self.b, nsteps, CFL)
+
+    def sync(self):
+        return gks_batch_sync(self.b)
+
+    def state(self, g):
+        p = self.problems[g]
+        U = np.zeros((4, p.ny, p.nx))
+        Wx = np.zeros((4, 2, p.ny, p.nx + 1))
+        Wy = np.zeros((4, 2, p.ny + 1, p.nx))
+        t, n = gks_batch_get_state(self.b, g, U, Wx, Wy)
+        return U, Wx, Wy, t, n
+
+    def close(self):
+        if self.b:
+            gks_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -226,3 +226,15 @@ def test_nonphysical_state_is_rejected_and_rolled_back():
     assert st == gks.GKS_ENONPHYSICAL
     assert np.array_equal(U, before[0])
     s.close()
+
+
+def test_positivity_fallback_parity():
+    """Seeded near-vacuum Riemann data on which the first-order fallback fires (steps 3 and 5):
+    GPU and oracle take the same steps to roundoff."""
+    quads = [(0.746, -0.312, 0.887, 0.312), (0.827, 0.438, -0.155, 0.861), (1.15, 0.953, 0.354, 0.494),
+             (0.228, -0.698, -0.347, 1.304)]
+    p = wl.riemann_2d(16, 80, quadrants=quads, mu=9.4e-4, Pr=0.72)
+    p.bc = [(wl.BC_PERIODIC, 0.0, 0.0, 1.0)] * 4
+    g, o = _run_both(p, 6)
+    for a, b in zip(g, o):
+        assert _rel_linf(a, b) < 1e-9

@@ -167,3 +167,19 @@ def test_uniform_state_flux_is_euler_flux():
         want = dt * np.array([rho * U, rho * U * U + p, rho * U * V, U * (w[3] + p)])
         np.testing.assert_allclose(F, want, rtol=1e-13)
         np.testing.assert_allclose(Wg, np.array([w, w]), rtol=1e-13)
+
+
+def test_collisionless_face_against_brute_force():
+    """The evolution of the positivity fallback: free transport of the two constant states
+    (the tau -> infinity limit of Eq. integral), f = f0 -- flux dt int u psi f0 and point values
+    int psi f0 by brute-force half-space quadrature."""
+    gamma = 1.4
+    L, R, _ = random_face(21, gamma)
+    P = oracle.params(gamma=gamma, mu=2e-3, Pr=0.72)
+    dt = 0.01
+    F, Wg, dbg = oracle.face_first_order(P, L, R, 0.05, 0.05, dt)
+    dl, dr = bf.dist_from_cons(L[0], gamma, 1), bf.dist_from_cons(R[0], gamma, 2)
+    Fb = dt * (dl.mom4(dl.U_()) + dr.mom4(dr.U_()))
+    Wb = dl.mom4(dl.const(1.0)) + dr.mom4(dr.const(1.0))
+    np.testing.assert_allclose(F, Fb, rtol=1e-12, atol=1e-13 * np.abs(Fb).max())
+    np.testing.assert_allclose(Wg, np.array([Wb, Wb]), rtol=1e-12)
