@@ -71,6 +71,8 @@ def lib():
         L.orc_recon2d.argtypes = [P(Params), ctypes.c_int, ctypes.c_int, D, D, P(BC), dp, dp, dp, dp]
         L.orc_flux2d.argtypes = [P(Params), ctypes.c_int, ctypes.c_int, D, D, P(BC), dp, dp, dp, D,
                                  dp, dp, dp, dp]
+        L.orc_flux2d_faces.argtypes = [P(Params), ctypes.c_int, ctypes.c_int, D, D, P(BC), dp, dp, dp, D,
+                                       ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, dp]
         L.orc_step2d.argtypes = [P(Params), ctypes.c_int, ctypes.c_int, D, D, P(BC), D, D,
                                  ctypes.c_int, dp, dp, dp, dp]
         L.orc_step2d.restype = ctypes.c_int
@@ -199,6 +201,16 @@ def flux2d(P, st: State2D, bc, dt):
     lib().orc_flux2d(ctypes.byref(P), nx, ny, st.Lx, st.Ly, bc, _p(st.U), _p(st.Wx), _p(st.Wy), dt,
                      _p(Fx), _p(Fy), _p(Wxn), _p(Wyn))
     return Fx, Fy, Wxn, Wyn
+
+
+def flux2d_faces(P, st: State2D, bc, dt, faces):
+    """Flux and point values at listed faces [(axis, i, j), ...] of a (large) grid."""
+    fl = np.ascontiguousarray(np.asarray(faces, dtype=np.int32).reshape(-1, 3))
+    n = fl.shape[0]
+    F, W = np.zeros((n, 4)), np.zeros((n, 2, 4))
+    lib().orc_flux2d_faces(ctypes.byref(P), st.nx, st.ny, st.Lx, st.Ly, bc, _p(st.U), _p(st.Wx), _p(st.Wy), dt, n,
+                           fl.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(F), _p(W))
+    return F, W
 
 
 def step2d(P, st: State2D, bc, CFL, dt_max=np.inf, viscous_dt=0):

@@ -111,6 +111,14 @@ void orc_flux2d(const orc_params* P, int nx, int ny, double Lx, double Ly, const
                 const double* U, const double* Wx, const double* Wy, double dt,
                 double* Fx, double* Fy, double* Wx_new, double* Wy_new);
 
+/* The evolution at n listed faces only (faces[3k..3k+2] = axis, i, j; axis 0 =
+ * x-face i between cells i-1 and i of row j, axis 1 = y-face j of column i),
+ * for sampled checks of large grids: F[4k..] the flux, Wg[8k..] the two point
+ * values (state layout order).  The reconstruction is done for the whole grid. */
+void orc_flux2d_faces(const orc_params* P, int nx, int ny, double Lx, double Ly, const orc_bc bc[4],
+                      const double* U, const double* Wx, const double* Wy, double dt, int n, const int* faces,
+                      double* F, double* Wg);
+
 /* One full step in place.  bc order: x-low, x-high, y-low, y-high.  If the
  * update makes cells non-physical, their faces are evolved again with the
  * collisionless first-order flux and the update is redone; if cells are still

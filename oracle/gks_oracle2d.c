@@ -1002,6 +1002,61 @@ static int update_cells(const orc_params* P, int nx, int ny, double dx, double d
   return nbad;
 }
 
+void orc_flux2d_faces(const orc_params* P, int nx, int ny, double Lx, double Ly, const orc_bc bc[4],
+                      const double* U, const double* Wx, const double* Wy, double dt, int n, const int* faces,
+                      double* F, double* Wg) {
+  const double dx = Lx / nx, dy = Ly / ny;
+  double* coef = (double*)malloc(sizeof(double) * 24 * nx * ny);
+  orc_recon2d(P, nx, ny, Lx, Ly, bc, U, Wx, Wy, coef);
+  ghosts G;
+  G.g = (double*)malloc(sizeof(double) * 4 * (nx + 2) * (ny + 2));
+  fill_ghosts(P, nx, ny, bc, U, &G);
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < n; ++k) {
+    const int axis = faces[3 * k], i = faces[3 * k + 1], j = faces[3 * k + 2];
+    double L[6][4], R[6][4], avg[2][3][4], Ff[4], Wf[2][4];
+    const int f = axis == 0 ? i : j, nf = axis == 0 ? nx : ny;
+    const orc_bc* blo = &bc[axis == 0 ? 0 : 2];
+    const orc_bc* bhi = &bc[axis == 0 ? 1 : 3];
+    int cl = f - 1, cr = f;
+    if (f == 0 && blo->kind == ORC_BC_PERIODIC) cl = nf - 1;
+    if (f == nf && bhi->kind == ORC_BC_PERIODIC) cr = 0;
+    const double hn = axis == 0 ? 0.5 * dx : 0.5 * dy;
+    const int ci0 = axis == 0 ? cl : i, cj0 = axis == 0 ? j : cl;
+    const int ci1 = axis == 0 ? cr : i, cj1 = axis == 0 ? j : cr;
+    const double px = axis == 0 ? hn : 0.0, py = axis == 0 ? 0.0 : hn;
+    if (f == 0 && blo->kind != ORC_BC_PERIODIC) {
+      side_state(coef, nx, ny, ci1, cj1, axis, dx, dy, -px, -py, R);
+      orc_bc_image(P, blo->kind, wall_tangent_velocity(blo, axis), blo->T_wall, R, L);
+    } else if (f == nf && bhi->kind != ORC_BC_PERIODIC) {
+      side_state(coef, nx, ny, ci0, cj0, axis, dx, dy, px, py, L);
+      orc_bc_image(P, bhi->kind, wall_tangent_velocity(bhi, axis), bhi->T_wall, L, R);
+    } else {
+      side_state(coef, nx, ny, ci0, cj0, axis, dx, dy, px, py, L);
+      side_state(coef, nx, ny, ci1, cj1, axis, dx, dy, -px, -py, R);
+    }
+    for (int m = 0; m < 2; ++m)
+      for (int t = -1; t <= 1; ++t) {
+        double w[4];
+        for (int v = 0; v < 4; ++v)
+          w[v] = axis == 0 ? G.g[GI(&G, v, j + t, i - 1 + m)] : G.g[GI(&G, v, j - 1 + m, i + t)];
+        to_frame(axis, w, avg[m][t + 1]);
+      }
+    orc_face(P, L, R, avg, axis == 0 ? dx : dy, axis == 0 ? dy : dx, dt, Ff, Wf, NULL);
+    double Fp[4], W0[4], W1[4];
+    to_frame(axis, Ff, Fp);
+    to_frame(axis, Wf[0], W0);
+    to_frame(axis, Wf[1], W1);
+    for (int v = 0; v < 4; ++v) {
+      F[4 * k + v] = Fp[v];
+      Wg[8 * k + v] = W0[v];
+      Wg[8 * k + 4 + v] = W1[v];
+    }
+  }
+  free(G.g);
+  free(coef);
+}
+
 int orc_step2d(const orc_params* P, int nx, int ny, double Lx, double Ly, const orc_bc bc[4],
                double CFL, double dt_max, int viscous_dt, double* U, double* Wx, double* Wy,
                double* dt_out) {
