@@ -114,9 +114,9 @@ class ClockSampler:
 # our arm
 # ----------------------------------------------------------------------------
 def flux_traffic(precision_name):
-    """dram bytes per launch of the x-face kernel from the committed ncu summary, or None
-    when it is missing or the kernel sources changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", f"flux_x_{precision_name}_smooth_wave.md")
+    """DRAM bytes per face of the x-face kernel from the committed ncu summary, or None when
+    it is missing or the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"step_kernels_{precision_name}_smooth_wave_2048.md")
     if not os.path.exists(path):
         return None, None
     h = source_hash()
@@ -133,7 +133,8 @@ def flux_traffic(precision_name):
 
 def source_hash():
     m = hashlib.sha1()
-    for p in ("paper_1412_4489_gb300/csrc/gks_device.cuh", "paper_1412_4489_gb300/csrc/gks.cu"):
+    for p in ("paper_1412_4489_gb300/csrc/gks_device.cuh", "paper_1412_4489_gb300/csrc/gks_grid.cuh",
+              "paper_1412_4489_gb300/csrc/gks.cu"):
         m.update(open(os.path.join(ROOT, p), "rb").read())
     return m.hexdigest()
 
@@ -252,6 +253,7 @@ def run_ours(args):
     linf = float(np.max(np.abs(Ua[0] - Ub[0])) / np.max(np.abs(Ub[0])))
     a.close()
     b.close()
+    errors = error_legs(stream) if not args.no_batch else None
 
     # ---- end to end through the C ABI with host buffers ----
     KE = max(3, min(args.steps, 20))
@@ -311,7 +313,8 @@ def run_ours(args):
     peak32 = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     measured32 = gks.gks_measure_alu_peak(gks.GKS_FP32_BULK)
     measured64 = gks.gks_measure_alu_peak(gks.GKS_FP64)
-    traffic, traffic_src = flux_traffic("fp32")
+    traffic_face, traffic_src = flux_traffic("fp32")
+    traffic = None if traffic_face is None else round(traffic_face * nfaces)
     flops64 = flops_face  # the same arithmetic in FP64
     achieved64 = flops64 * nfaces / (prof64[dom] * 1e-3) / 1e12
 
@@ -321,13 +324,14 @@ def run_ours(args):
         out = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "accumulate_dtype": "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "accumulate_dtype": "f32x2 (double-float hi+lo)",
             "data": "synthetic (seeded smooth wave)",
             "config": dict(workload_config(args.size), precision="fp32_bulk", parallelism=f"replicas x{world}"),
             "fp64_plain": {"value": round(value64, 3), "unit": UNIT, "ms_per_step": round(ms64 / K64, 5),
                            "steps": K64, "speedup_fp32_bulk": round(value / value64, 2)},
             "error_fp32_bulk_vs_fp64": {"l1_rho_rel": l1, "linf_rho_rel": linf, "steps": 100,
-                                        "reference": "GPU FP64 path (oracle-pinned in tests)"},
+                                        "reference": "GPU FP64 path (oracle-pinned in tests)",
+                                        "other_workloads": errors},
             "roofline": {"bound": "alu", "kernel": f"k_flux<{dom[-1]}> fp32", "achieved": round(achieved, 3),
                          "peak": round(peak32, 2), "unit": "TFLOP/s", "frac": round(achieved / peak32, 4),
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
@@ -358,6 +362,47 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
     if out is not None:
         print(json.dumps(out), flush=True)
+
+
+def error_legs(stream):
+    """FP32-bulk against FP64 (the oracle-pinned GPU path) in relative L1 of density on the
+    other seeded workloads: the 1024^2 Navier-Stokes Riemann data (200 steps) and the 512^2
+    cavity (2000 steps).  The Riemann data carry vortex sheets whose grid-scale growth makes
+    the FP64 scheme diverge from itself once the start is perturbed by 1e-12; that control is
+    reported beside the FP32 figure."""
+    import numpy as np
+    from paper_1412_4489_gb300 import gks, workloads as wl
+
+    def rho_l1(a, b):
+        ra, rb = a.state()[0][0], b.state()[0][0]
+        return float(np.sum(np.abs(ra - rb)) / np.sum(np.abs(rb)))
+
+    out = {}
+    with __import__("torch").cuda.stream(stream):
+        p = wl.riemann_2d(1024, seed=3, mu=1e-4, Pr=0.72)
+        q = wl.riemann_2d(1024, seed=3, mu=1e-4, Pr=0.72)
+        q.U = q.U * (1.0 + 1e-12 * np.random.default_rng(1).standard_normal(q.U.shape))
+        f64 = gks.Solver(p, gks.GKS_FP64, stream=stream.cuda_stream, tau_eps=0.05)
+        f32 = gks.Solver(p, gks.GKS_FP32_BULK, stream=stream.cuda_stream, tau_eps=0.05)
+        ctl = gks.Solver(q, gks.GKS_FP64, stream=stream.cuda_stream, tau_eps=0.05)
+        rows, done = [], 0
+        for m in (100, 200):
+            for s in (f64, f32, ctl):
+                s.advance(m - done, CFL)
+            done = m
+            rows.append({"steps": m, "l1_rho_rel_fp32": rho_l1(f32, f64), "l1_rho_rel_fp64_perturbed_1e-12": rho_l1(ctl, f64)})
+        for s in (f64, f32, ctl):
+            s.close()
+        out["riemann_ns_1024"] = rows
+        c = wl.cavity_2d(512)
+        f64 = gks.Solver(c, gks.GKS_FP64, stream=stream.cuda_stream, tau_eps=0.05)
+        f32 = gks.Solver(c, gks.GKS_FP32_BULK, stream=stream.cuda_stream, tau_eps=0.05)
+        f64.advance(2000, CFL)
+        f32.advance(2000, CFL)
+        out["cavity_512"] = [{"steps": 2000, "l1_rho_rel_fp32": rho_l1(f32, f64)}]
+        f64.close()
+        f32.close()
+    return out
 
 
 def run_batched(args, stream):

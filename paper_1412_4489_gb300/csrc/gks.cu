@@ -8,8 +8,9 @@
 //   k_recon    compact reconstruction of every cell (Section 3.2)
 //   k_flux<0>  gas evolution at every x-face (Section 2.2, 3.3, 4)
 //   k_flux<1>  gas evolution at every y-face (frame rotated: n = y, t = x)
-//   k_update   conservative update (Eq. finite) in FP64 + next CFL bound
-//              (warp-shuffle / block / atomic min) + physical-state check
+//   k_update   conservative update (Eq. finite) into FP64 averages, or in
+//              FP32-bulk mode into double-float (hi + lo FP32) averages, + next
+//              CFL bound (warp-shuffle / block / atomic min) + physical check
 //   k_end      advance t and the step counter
 // Cell averages and face values are double-buffered; the buffer in use is the
 // parity of the device step counter, so a failed step leaves the last good
@@ -45,24 +46,13 @@ __global__ void k_begin(Ctrl* c, double cfl, double dt_max, double t_end) { ctrl
 __global__ void k_end(Ctrl* c) { ctrl_end(c); }
 
 // ---------------------------------------------------------------------------
-// ghost ring: perimeter of the padded cell array of the current buffer; in
-// FP32-bulk mode the FP32 mirror (F0/F1) gets the same values
+// ghost ring: perimeter of the padded cell array of the current buffer
 // ---------------------------------------------------------------------------
-__global__ void k_ghost(Geo g, double* U0, double* U1, float* F0, float* F1, const Ctrl* c, int force) {
+template <class R>
+__global__ void k_ghost(Geo g, Cells<R> U0, Cells<R> U1, const Ctrl* c, int force) {
   if (!force && c->skip) return;
   const int par = (int)(c->steps & 1);
-  ghost_at(g, par ? U1 : U0, par ? F1 : F0, blockIdx.x * blockDim.x + threadIdx.x);
-}
-
-// FP32 mirror of the interior of the current cell-average buffer
-__global__ void k_mirror(Geo g, const double* U0, const double* U1, float* F0, float* F1, const Ctrl* c) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= g.nx || j >= g.ny) return;
-  const int par = (int)(c->steps & 1);
-  const double* U = par ? U1 : U0;
-  float* Uf = par ? F1 : F0;
-  for (int v = 0; v < 4; ++v) Uf[ci(g, v, i, j)] = (float)U[ci(g, v, i, j)];
+  ghost_at<R>(g, par ? U1 : U0, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -102,7 +92,7 @@ __global__ void __launch_bounds__(128, FluxBlocks<R>::value) k_flux(Geo g, FaceC
   if (i >= fx || j >= fy) return;
   const int par = (int)(c->steps & 1);
   // new face values go to the other buffer
-  flux_face<AX, R, TW>(g, C, par ? U1 : U0, coef, par ? Wn0 : Wn1, F, i, j, R(c->dt));
+  flux_face<AX, R, TW>(g, C, par ? U1 : U0, coef, par ? Wn0 : Wn1, F, i, j, step_dt<R>(c));
 }
 
 // ---------------------------------------------------------------------------
@@ -113,10 +103,9 @@ __global__ void __launch_bounds__(128, FluxBlocks<R>::value) k_flux(Geo g, FaceC
 // still left one; a cell non-physical after pass 3 fails the step.  Each pass
 // keeps its own running minimum of the CFL bound.
 template <class R, class TW>
-__global__ void __launch_bounds__(256) k_update(Geo g, double* U0, double* U1, float* F0, float* F1, const R* Ur0,
-                                                const R* Ur1, const R* __restrict__ Fx, const R* __restrict__ Fy,
-                                                TW* Wx0, TW* Wx1, TW* Wy0, TW* Wy1, unsigned char* __restrict__ bad,
-                                                Ctrl* c, int pass) {
+__global__ void __launch_bounds__(256) k_update(Geo g, Cells<R> U0, Cells<R> U1, const R* __restrict__ Fx,
+                                                const R* __restrict__ Fy, TW* Wx0, TW* Wx1, TW* Wy0, TW* Wy1,
+                                                unsigned char* __restrict__ bad, Ctrl* c, int pass) {
   if (c->skip || (pass == 2 && !c->bad_found[0]) || (pass == 3 && !c->bad_found[1])) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -124,8 +113,8 @@ __global__ void __launch_bounds__(256) k_update(Geo g, double* U0, double* U1, f
   R inv = R(0);
   if (i < g.nx && j < g.ny) {
     bool b;
-    inv = update_cell<R, TW>(g, par ? U1 : U0, par ? U0 : U1, par ? F0 : F1, par ? Ur1 : Ur0, Fx, Fy,
-                             par ? Wx0 : Wx1, par ? Wy0 : Wy1, bad, pass, R(c->dt), i, j, b);
+    inv = update_cell<R, TW>(g, par ? U1 : U0, par ? U0 : U1, Fx, Fy, par ? Wx0 : Wx1, par ? Wy0 : Wy1, bad, pass,
+                             step_dt<R>(c), i, j, b);
     if (pass == 1) {
       bad[(size_t)j * g.nx + i] = b ? 1 : 0;
       if (b) atomicOr(&c->bad_found[0], 1);
@@ -139,15 +128,16 @@ __global__ void __launch_bounds__(256) k_update(Geo g, double* U0, double* U1, f
 }
 
 // CFL bound of the current state (after set_state), in FP64
-__global__ void k_dtbound(Geo g, const double* U0, const double* U1, Ctrl* c) {
+template <class R>
+__global__ void k_dtbound(Geo g, Cells<R> U0, Cells<R> U1, Ctrl* c) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int par = (int)(c->steps & 1);
-  const double* U = par ? U1 : U0;
+  const Cells<R> U = par ? U1 : U0;
   double inv = 0.0;
   if (i < g.nx && j < g.ny) {
     double w[4];
-    for (int v = 0; v < 4; ++v) w[v] = U[ci(g, v, i, j)];
+    for (int v = 0; v < 4; ++v) w[v] = U.get(g, v, i, j);
     bool ok;
     inv = inv_bound<double>(g, w, ok);
     if (!ok || !(inv < INFINITY)) {
@@ -161,15 +151,17 @@ __global__ void k_dtbound(Geo g, const double* U0, const double* U1, Ctrl* c) {
 // ---------------------------------------------------------------------------
 // state transfer
 // ---------------------------------------------------------------------------
-__global__ void k_scatter_U(Geo g, const double* __restrict__ src, double* U0, double* U1, const Ctrl* c, int to_dev) {
+template <class R>
+__global__ void k_scatter_U(Geo g, const double* __restrict__ src, Cells<R> U0, Cells<R> U1, const Ctrl* c,
+                            int to_dev) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
-  double* U = (c->steps & 1) ? U1 : U0;
+  const Cells<R> U = (c->steps & 1) ? U1 : U0;
   for (int v = 0; v < 4; ++v) {
     const size_t o = ((size_t)v * g.ny + j) * g.nx + i;
-    if (to_dev) U[ci(g, v, i, j)] = src[o];
-    else const_cast<double*>(src)[o] = U[ci(g, v, i, j)];
+    if (to_dev) U.set(g, v, i, j, src[o]);
+    else const_cast<double*>(src)[o] = U.get(g, v, i, j);
   }
 }
 
@@ -184,32 +176,32 @@ __global__ void k_copy_W(const double* __restrict__ src, TW* W0, TW* W1, size_t 
 
 // face values = mean of the two adjacent averages (ghosts included)
 template <int AX, class TW>
-__global__ void k_init_W(Geo g, const double* U0, const double* U1, TW* W0, TW* W1, const Ctrl* c) {
+__global__ void k_init_W(Geo g, Cells<TW> U0, Cells<TW> U1, TW* W0, TW* W1, const Ctrl* c) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int fx = AX == 0 ? g.nx + 1 : g.nx, fy = AX == 0 ? g.ny : g.ny + 1;
   if (i >= fx || j >= fy) return;
   const int par = (int)(c->steps & 1);
-  const double* U = par ? U1 : U0;
+  const Cells<TW> U = par ? U1 : U0;
   TW* W = par ? W1 : W0;
   const size_t n = (size_t)fx * fy, o = (size_t)j * fx + i;
   for (int v = 0; v < 4; ++v) {
-    const double a = U[ci(g, v, AX == 0 ? i - 1 : i, AX == 0 ? j : j - 1)];
-    const double b = U[ci(g, v, i, j)];
+    const double a = U.get(g, v, AX == 0 ? i - 1 : i, AX == 0 ? j : j - 1);
+    const double b = U.get(g, v, i, j);
     W[(size_t)(v * 2) * n + o] = Store<TW>::to(0.5 * (a + b));
     W[(size_t)(v * 2 + 1) * n + o] = Store<TW>::to(0.5 * (a + b));
   }
 }
 
 template <class R>
-__global__ void k_coef_out(Geo g, const double* U0, const double* U1, const R* coef, double* out, const Ctrl* c) {
+__global__ void k_coef_out(Geo g, Cells<R> U0, Cells<R> U1, const R* coef, double* out, const Ctrl* c) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
-  const double* U = (c->steps & 1) ? U1 : U0;
+  const Cells<R> U = (c->steps & 1) ? U1 : U0;
   const size_t N = (size_t)g.nx * g.ny, o = (size_t)j * g.nx + i;
   for (int v = 0; v < 4; ++v) {
-    out[(size_t)(v * 6) * N + o] = U[ci(g, v, i, j)];
+    out[(size_t)(v * 6) * N + o] = U.get(g, v, i, j);
     for (int k = 0; k < 5; ++k) out[(size_t)(v * 6 + k + 1) * N + o] = (double)coef[(size_t)(k * 4 + v) * N + o];
   }
 }
@@ -222,6 +214,7 @@ __global__ void k_to_double(const R* src, double* dst, size_t n) {
 
 __global__ void k_set_dt(Ctrl* c, double dt) {
   c->dt = dt;
+  c->dt_f = (float)dt;
   c->skip = 0;
 }
 
@@ -236,8 +229,7 @@ struct gks_handle {
   cudaStream_t stream;
   bool own_stream;
   int device;
-  double* U[2];
-  float* Uf[2];      // FP32 mirror of U (FP32-bulk mode only)
+  double* U[2];      // cell averages (Cells<R>: FP64, or FP32 hi / lo planes), 4 * plane doubles each
   void* Wx[2];
   void* Wy[2];
   void* coef;
@@ -281,15 +273,14 @@ FaceConst<R> fconst(const Geo& g, int axis) {
   return grid_face_const<R>(g, axis);
 }
 
-// the padded cell-average arrays the compute-type kernels read
-template <class R> const R* cells(const gks_handle* h, int b);
-template <> const double* cells<double>(const gks_handle* h, int b) { return h->U[b]; }
-template <> const float* cells<float>(const gks_handle* h, int b) { return h->Uf[b]; }
+// cell-average buffer b, and the compute-type array of its averages
+template <class R> Cells<R> cellbuf(const gks_handle* h, int b) { return Cells<R>{(R*)h->U[b]}; }
+template <class R> const R* cells(const gks_handle* h, int b) { return (const R*)h->U[b]; }
 
+template <class R>
 void launch_ghost(gks_handle* h, int force) {
   const Geo& g = h->g;
-  const int per = 2 * (g.nx + 2) + 2 * g.ny;
-  k_ghost<<<(per + 127) / 128, 128, 0, h->stream>>>(g, h->U[0], h->U[1], h->Uf[0], h->Uf[1], h->ctrl, force);
+  k_ghost<R><<<(perimeter(g) + 127) / 128, 128, 0, h->stream>>>(g, cellbuf<R>(h, 0), cellbuf<R>(h, 1), h->ctrl, force);
 }
 
 template <class R, class TW>
@@ -314,7 +305,7 @@ gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double 
   mark(0);
   if (with_begin_end) k_begin<<<1, 1, 0, s>>>(h->ctrl, cfl, dt_max, t_end);
   mark(1);
-  launch_ghost(h, force);
+  launch_ghost<R>(h, force);
   mark(2);
   launch_recon<R, TW>(h, force);
   mark(3);
@@ -330,8 +321,8 @@ gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double 
   for (int pass = 1; pass <= 3; ++pass) {
     if (do_update)
       k_update<R, TW><<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(
-          g, h->U[0], h->U[1], h->Uf[0], h->Uf[1], cells<R>(h, 0), cells<R>(h, 1), (const R*)h->Fx, (const R*)h->Fy,
-          (TW*)h->Wx[0], (TW*)h->Wx[1], (TW*)h->Wy[0], (TW*)h->Wy[1], h->bad, h->ctrl, pass);
+          g, cellbuf<R>(h, 0), cellbuf<R>(h, 1), (const R*)h->Fx, (const R*)h->Fy, (TW*)h->Wx[0], (TW*)h->Wx[1],
+          (TW*)h->Wy[0], (TW*)h->Wy[1], h->bad, h->ctrl, pass);
     mark(5 + pass);
   }
   mark(8);
@@ -385,25 +376,35 @@ gks_status reset_ctrl(gks_handle* h, double t) {
   return GKS_OK;
 }
 
+// Loads a state from device FP64 arrays.  With stage_w set, dWx /
+// dWy are host arrays copied in turn through the staging buffer (which must
+// then not hold dU).
 template <class TW>
-gks_status load_state(gks_handle* h, const double* dU, const double* dWx, const double* dWy) {
+gks_status load_state(gks_handle* h, const double* dU, const double* dWx, const double* dWy, bool stage_w = false) {
   const Geo& g = h->g;
   cudaStream_t s = h->stream;
   const dim3 b2(32, 8);
-  k_scatter_U<<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, dU, h->U[0], h->U[1], h->ctrl, 1);
-  if (h->Uf[0]) k_mirror<<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, h->U[0], h->U[1], h->Uf[0], h->Uf[1], h->ctrl);
-  launch_ghost(h, 1);
-  if (dWx) {
-    k_copy_W<TW><<<(unsigned)((n_wx(g) + 255) / 256), 256, 0, s>>>(dWx, (TW*)h->Wx[0], (TW*)h->Wx[1], n_wx(g), h->ctrl, 1);
-  } else {
-    k_init_W<0, TW><<<grid2(g.nx + 1, g.ny, b2), b2, 0, s>>>(g, h->U[0], h->U[1], (TW*)h->Wx[0], (TW*)h->Wx[1], h->ctrl);
+  const Cells<TW> U0 = cellbuf<TW>(h, 0), U1 = cellbuf<TW>(h, 1);
+  k_scatter_U<TW><<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, dU, U0, U1, h->ctrl, 1);
+  launch_ghost<TW>(h, 1);
+  for (int axis = 0; axis < 2; ++axis) {
+    const double* src = axis == 0 ? dWx : dWy;
+    const size_t n = axis == 0 ? n_wx(g) : n_wy(g);
+    TW* W0 = (TW*)(axis == 0 ? h->Wx[0] : h->Wy[0]);
+    TW* W1 = (TW*)(axis == 0 ? h->Wx[1] : h->Wy[1]);
+    if (src) {
+      if (stage_w) {
+        CK(cudaMemcpyAsync(h->staging, src, n * sizeof(double), cudaMemcpyHostToDevice, s));
+        src = h->staging;
+      }
+      k_copy_W<TW><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, W0, W1, n, h->ctrl, 1);
+    } else if (axis == 0) {
+      k_init_W<0, TW><<<grid2(g.nx + 1, g.ny, b2), b2, 0, s>>>(g, U0, U1, W0, W1, h->ctrl);
+    } else {
+      k_init_W<1, TW><<<grid2(g.nx, g.ny + 1, b2), b2, 0, s>>>(g, U0, U1, W0, W1, h->ctrl);
+    }
   }
-  if (dWy) {
-    k_copy_W<TW><<<(unsigned)((n_wy(g) + 255) / 256), 256, 0, s>>>(dWy, (TW*)h->Wy[0], (TW*)h->Wy[1], n_wy(g), h->ctrl, 1);
-  } else {
-    k_init_W<1, TW><<<grid2(g.nx, g.ny + 1, b2), b2, 0, s>>>(g, h->U[0], h->U[1], (TW*)h->Wy[0], (TW*)h->Wy[1], h->ctrl);
-  }
-  k_dtbound<<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, h->U[0], h->U[1], h->ctrl);
+  k_dtbound<TW><<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, U0, U1, h->ctrl);
   CK(cudaGetLastError());
   return GKS_OK;
 }
@@ -413,13 +414,30 @@ gks_status store_state(gks_handle* h, double* dU, double* dWx, double* dWy) {
   const Geo& g = h->g;
   cudaStream_t s = h->stream;
   const dim3 b2(32, 8);
-  if (dU) k_scatter_U<<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, dU, h->U[0], h->U[1], h->ctrl, 0);
+  if (dU) k_scatter_U<TW><<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(g, dU, cellbuf<TW>(h, 0), cellbuf<TW>(h, 1), h->ctrl, 0);
   if (dWx)
     k_copy_W<TW><<<(unsigned)((n_wx(g) + 255) / 256), 256, 0, s>>>(dWx, (TW*)h->Wx[0], (TW*)h->Wx[1], n_wx(g), h->ctrl, 0);
   if (dWy)
     k_copy_W<TW><<<(unsigned)((n_wy(g) + 255) / 256), 256, 0, s>>>(dWy, (TW*)h->Wy[0], (TW*)h->Wy[1], n_wy(g), h->ctrl, 0);
   CK(cudaGetLastError());
   return GKS_OK;
+}
+
+void make_geo(Geo& g, int nx, int ny, double Lx, double Ly, double gamma, double Pr, double mu, const gks_bc* bc,
+              const gks_options& o) {
+  memset(&g, 0, sizeof(g));
+  g.nx = nx; g.ny = ny;
+  g.dx = Lx / nx; g.dy = Ly / ny;
+  g.gamma = gamma; g.mu = mu; g.Pr = Pr;
+  g.weno_eps = o.weno_eps; g.weno_C = o.weno_C; g.tau_eps = o.tau_eps; g.tau_C = o.tau_C;
+  g.viscous_dt = o.viscous_dt;
+  for (int k = 0; k < 4; ++k) {
+    g.bc.kind[k] = bc ? bc[k].kind : GKS_BC_PERIODIC;
+    g.bc.uw[k] = bc ? bc[k].u_wall : 0.0;
+    g.bc.vw[k] = bc ? bc[k].v_wall : 0.0;
+    g.bc.Tw[k] = bc ? bc[k].T_wall : 1.0;
+  }
+  geo_finish(g);
 }
 
 gks_status check_args(int nx, int ny, double Lx, double Ly, double gamma, double Pr, double mu, const gks_bc* bc,
@@ -474,19 +492,7 @@ gks_status gks_create(int nx, int ny, double Lx, double Ly, double gamma, double
   if (check_args(nx, ny, Lx, Ly, gamma, Pr, mu, bc, &o, why) != GKS_OK) { g_create_err = why; return GKS_EINVAL; }
   gks_handle* h = new gks_handle();
   Geo& g = h->g;
-  g.nx = nx; g.ny = ny;
-  g.pitch = ((nx + 2) + 1) & ~1;
-  g.plane = (size_t)(ny + 2) * g.pitch;
-  g.dx = Lx / nx; g.dy = Ly / ny;
-  g.gamma = gamma; g.mu = mu; g.Pr = Pr;
-  g.weno_eps = o.weno_eps; g.weno_C = o.weno_C; g.tau_eps = o.tau_eps; g.tau_C = o.tau_C;
-  g.viscous_dt = o.viscous_dt;
-  for (int k = 0; k < 4; ++k) {
-    g.bc.kind[k] = bc ? bc[k].kind : GKS_BC_PERIODIC;
-    g.bc.uw[k] = bc ? bc[k].u_wall : 0.0;
-    g.bc.vw[k] = bc ? bc[k].v_wall : 0.0;
-    g.bc.Tw[k] = bc ? bc[k].T_wall : 1.0;
-  }
+  make_geo(g, nx, ny, Lx, Ly, gamma, Pr, mu, bc, o);
   h->prec = o.precision;
   const size_t wsz = h->prec == GKS_FP64 ? 8 : 4;
   cudaError_t e = cudaGetDevice(&h->device);
@@ -499,7 +505,6 @@ gks_status gks_create(int nx, int ny, double Lx, double Ly, double gamma, double
   };
   for (int b = 0; b < 2; ++b) {
     alloc((void**)&h->U[b], 4 * g.plane * sizeof(double));
-    if (h->prec == GKS_FP32_BULK) alloc((void**)&h->Uf[b], 4 * g.plane * sizeof(float));
     alloc(&h->Wx[b], n_wx(g) * wsz);
     alloc(&h->Wy[b], n_wy(g) * wsz);
   }
@@ -517,7 +522,6 @@ gks_status gks_create(int nx, int ny, double Lx, double Ly, double gamma, double
   if (e == cudaSuccess)
     for (int b = 0; b < 2; ++b) {
       if (e == cudaSuccess) e = cudaMemsetAsync(h->U[b], 0, 4 * g.plane * sizeof(double), h->stream);
-      if (e == cudaSuccess && h->Uf[b]) e = cudaMemsetAsync(h->Uf[b], 0, 4 * g.plane * sizeof(float), h->stream);
       if (e == cudaSuccess) e = cudaMemsetAsync(h->Wx[b], 0, n_wx(g) * wsz, h->stream);
       if (e == cudaSuccess) e = cudaMemsetAsync(h->Wy[b], 0, n_wy(g) * wsz, h->stream);
     }
@@ -556,36 +560,12 @@ gks_status gks_set_state(gks_handle* h, const double* U, const double* Wx, const
   // U goes through the staging buffer; face values through the same buffer in turn
   gks_status st = reset_ctrl(h, t);
   if (st != GKS_OK) return st;
+  // U goes in through the staging buffer first (the scatter reads it before the
+  // face values reuse the buffer: same stream)
   CK(cudaMemcpyAsync(h->staging, U, n_u(g) * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-  const dim3 b2(32, 8);
-  k_scatter_U<<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, h->staging, h->U[0], h->U[1], h->ctrl, 1);
-  if (h->Uf[0])
-    k_mirror<<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], h->Uf[0], h->Uf[1], h->ctrl);
-  launch_ghost(h, 1);
-  for (int axis = 0; axis < 2; ++axis) {
-    const double* src = axis == 0 ? Wx : Wy;
-    const size_t n = axis == 0 ? n_wx(g) : n_wy(g);
-    void** W = axis == 0 ? h->Wx : h->Wy;
-    if (src) {
-      CK(cudaMemcpyAsync(h->staging, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-      if (h->prec == GKS_FP64)
-        k_copy_W<double><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->staging, (double*)W[0], (double*)W[1], n, h->ctrl, 1);
-      else
-        k_copy_W<float><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->staging, (float*)W[0], (float*)W[1], n, h->ctrl, 1);
-    } else if (axis == 0) {
-      if (h->prec == GKS_FP64)
-        k_init_W<0, double><<<grid2(g.nx + 1, g.ny, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], (double*)W[0], (double*)W[1], h->ctrl);
-      else
-        k_init_W<0, float><<<grid2(g.nx + 1, g.ny, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], (float*)W[0], (float*)W[1], h->ctrl);
-    } else {
-      if (h->prec == GKS_FP64)
-        k_init_W<1, double><<<grid2(g.nx, g.ny + 1, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], (double*)W[0], (double*)W[1], h->ctrl);
-      else
-        k_init_W<1, float><<<grid2(g.nx, g.ny + 1, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], (float*)W[0], (float*)W[1], h->ctrl);
-    }
-  }
-  k_dtbound<<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], h->ctrl);
-  CK(cudaGetLastError());
+  st = h->prec == GKS_FP64 ? load_state<double>(h, h->staging, Wx, Wy, true)
+                           : load_state<float>(h, h->staging, Wx, Wy, true);
+  if (st != GKS_OK) return st;
   st = read_ctrl(h);
   if (st != GKS_OK) return st;
   if (h->hctrl->status != GKS_OK) return fail(h, GKS_ENONPHYSICAL, "gks_set_state: state has rho <= 0 or p <= 0");
@@ -675,7 +655,6 @@ void gks_destroy(gks_handle* h) {
   destroy_graphs(h);
   for (int b = 0; b < 2; ++b) {
     cudaFree(h->U[b]);
-    cudaFree(h->Uf[b]);
     cudaFree(h->Wx[b]);
     cudaFree(h->Wy[b]);
   }
@@ -722,13 +701,16 @@ gks_status gks_debug_recon(gks_handle* h, double* coef) {
   CK(cudaSetDevice(h->device));
   const Geo& g = h->g;
   const dim3 b2(32, 8);
-  launch_ghost(h, 1);
   if (h->prec == GKS_FP64) {
+    launch_ghost<double>(h, 1);
     launch_recon<double, double>(h, 1);
-    k_coef_out<double><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], (const double*)h->coef, h->staging, h->ctrl);
+    k_coef_out<double><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, cellbuf<double>(h, 0), cellbuf<double>(h, 1),
+                                                                     (const double*)h->coef, h->staging, h->ctrl);
   } else {
+    launch_ghost<float>(h, 1);
     launch_recon<float, float>(h, 1);
-    k_coef_out<float><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, h->U[0], h->U[1], (const float*)h->coef, h->staging, h->ctrl);
+    k_coef_out<float><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, cellbuf<float>(h, 0), cellbuf<float>(h, 1),
+                                                                    (const float*)h->coef, h->staging, h->ctrl);
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(coef, h->staging, (size_t)24 * g.nx * g.ny * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -799,6 +781,7 @@ __global__ void k_noalloc_ctrl(Ctrl* c) {
   c->bad_found[0] = c->bad_found[1] = 0;
   c->t = 0.0;
   c->dt = 0.0;
+  c->dt_f = 0.0f;
   c->steps = 0;
   c->status = GKS_OK;
   c->skip = 0;
@@ -823,20 +806,7 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
     return GKS_EINVAL;
   }
   Geo g;
-  memset(&g, 0, sizeof(g));
-  g.nx = nx; g.ny = ny;
-  g.pitch = ((nx + 2) + 1) & ~1;
-  g.plane = (size_t)(ny + 2) * g.pitch;
-  g.dx = Lx / nx; g.dy = Ly / ny;
-  g.gamma = gamma; g.mu = mu; g.Pr = Pr;
-  g.weno_eps = o.weno_eps; g.weno_C = o.weno_C; g.tau_eps = o.tau_eps; g.tau_C = o.tau_C;
-  g.viscous_dt = o.viscous_dt;
-  for (int k = 0; k < 4; ++k) {
-    g.bc.kind[k] = bc ? bc[k].kind : GKS_BC_PERIODIC;
-    g.bc.uw[k] = bc ? bc[k].u_wall : 0.0;
-    g.bc.vw[k] = bc ? bc[k].v_wall : 0.0;
-    g.bc.Tw[k] = bc ? bc[k].T_wall : 1.0;
-  }
+  make_geo(g, nx, ny, Lx, Ly, gamma, Pr, mu, bc, o);
   // scratch layout: control block | padded U before | padded U after | coefficients | Fx | Fy
   const size_t b_ctrl = align256(sizeof(Ctrl));
   const size_t b_u = align256(4 * g.plane * sizeof(double));
@@ -864,12 +834,13 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
   unsigned char* bad = base + b_ctrl + 2 * b_u + b_coef + b_fx + b_fy;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const dim3 b2(32, 8), bf(32, 4);
-  const int per = 2 * (nx + 2) + 2 * ny;
+  const int per = perimeter(g);
+  const Cells<double> C0{U0}, C1{U1};
   // the control block must start from zero state; the rest is fully written before it is read
   k_noalloc_ctrl<<<1, 1, 0, s>>>(ctrl);
-  k_scatter_U<<<grid2(nx, ny, b2), b2, 0, s>>>(g, dU, U0, U1, ctrl, 1);
-  k_ghost<<<(per + 127) / 128, 128, 0, s>>>(g, U0, U1, nullptr, nullptr, ctrl, 1);
-  k_dtbound<<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, ctrl);
+  k_scatter_U<double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, dU, C0, C1, ctrl, 1);
+  k_ghost<double><<<(per + 127) / 128, 128, 0, s>>>(g, C0, C1, ctrl, 1);
+  k_dtbound<double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, C0, C1, ctrl);
   k_begin<<<1, 1, 0, s>>>(ctrl, CFL, dt_max, INFINITY);
   k_recon<double, double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, dWx, dWx_out, dWy, dWy_out, coef, g.dx, g.dy,
                                                             g.weno_eps, g.weno_C, g.gamma - 1.0, ctrl, 0);
@@ -878,11 +849,10 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
   k_flux<1, double, double><<<grid2(nx, ny + 1, bf), bf, 0, s>>>(g, fconst<double>(g, 1), U0, U1, coef,
                                                                   const_cast<double*>(dWy), dWy_out, Fy, ctrl, 0);
   for (int pass = 1; pass <= 3; ++pass)
-    k_update<double, double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, nullptr, nullptr, U0, U1, Fx, Fy,
-                                                              const_cast<double*>(dWx), dWx_out,
+    k_update<double, double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, C0, C1, Fx, Fy, const_cast<double*>(dWx), dWx_out,
                                                               const_cast<double*>(dWy), dWy_out, bad, ctrl, pass);
   k_end<<<1, 1, 0, s>>>(ctrl);
-  k_scatter_U<<<grid2(nx, ny, b2), b2, 0, s>>>(g, dU_out, U0, U1, ctrl, 0);
+  k_scatter_U<double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, dU_out, C0, C1, ctrl, 0);
   e = cudaGetLastError();
   Ctrl hc;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s);

@@ -32,7 +32,7 @@ namespace {
 constexpr int kThreads = 128;  // one work tile = one block = 128 cells or faces
 
 struct GridOff {
-  size_t u;     // padded cell arrays (U, Uf)
+  size_t u;     // padded cell arrays (4 * plane doubles: Cells<R>)
   size_t wx, wy;
   size_t coef;  // 20 * nx * ny
   size_t fx, fy;
@@ -56,7 +56,6 @@ struct Args {
   const FaceConst<R>* fc;  // [G][2]
   Ctrl* ctrl;
   double* U[2];
-  float* Uf[2];
   TW* Wx[2];
   TW* Wy[2];
   R* coef;
@@ -134,8 +133,7 @@ __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<
       if (c->skip) continue;
       const int par = (int)(c->steps & 1);
       const Geo& g = a.geo[w.x];
-      float* uf = a.Uf[par] ? a.Uf[par] + a.off[w.x].u : nullptr;
-      ghost_at(g, a.U[par] + a.off[w.x].u, uf, w.y + tid);
+      ghost_at<R>(g, Cells<R>{(R*)(a.U[par] + a.off[w.x].u)}, w.y + tid);
     }
     if (!grid_barrier(a.bar)) return;
 
@@ -149,9 +147,9 @@ __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<
       if (i >= g.nx || j >= g.ny) continue;
       const int par = (int)(c->steps & 1);
       const GridOff& o = a.off[w.x];
-      const R* U = (sizeof(R) == 4 ? (const R*)a.Uf[par] : (const R*)a.U[par]) + o.u;
-      recon_cell<R, TW>(g, U, a.Wx[par] + o.wx, a.Wy[par] + o.wy, a.coef + o.coef, i, j, R(g.dx), R(g.dy),
-                        R(g.weno_eps), R(g.weno_C), R(g.gamma - 1.0));
+      const R* U = (const R*)(a.U[par] + o.u);
+      recon_cell<R, TW>(g, U, a.Wx[par] + o.wx, a.Wy[par] + o.wy, a.coef + o.coef, i, j, GeoR<R>::dx(g),
+                        GeoR<R>::dy(g), GeoR<R>::weps(g), GeoR<R>::wC(g), GeoR<R>::gm1(g));
     }
     if (!grid_barrier(a.bar)) return;
 
@@ -164,8 +162,8 @@ __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<
       const int i = w.y + tid % a.face_tw, j = w.z + tid / a.face_tw;
       const int par = (int)(c->steps & 1);
       const GridOff& o = a.off[w.x];
-      const R* U = (sizeof(R) == 4 ? (const R*)a.Uf[par] : (const R*)a.U[par]) + o.u;
-      const R dt = R(c->dt);
+      const R* U = (const R*)(a.U[par] + o.u);
+      const R dt = step_dt<R>(c);
       if (w.w == 0) {
         if (i <= g.nx && j < g.ny)
           flux_face<0, R, TW>(g, a.fc[2 * w.x], U, a.coef + o.coef, a.Wx[par ^ 1] + o.wx, a.Fx + o.fx, i, j, dt);
@@ -193,11 +191,9 @@ __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<
         R inv = R(0);
         if (i < g.nx && j < g.ny) {
           bool bad;
-          float* ufn = a.Uf[par ^ 1] ? a.Uf[par ^ 1] + o.u : nullptr;
-          const R* Ur = (sizeof(R) == 4 ? (const R*)a.Uf[par] : (const R*)a.U[par]) + o.u;
-          inv = update_cell<R, TW>(g, a.U[par] + o.u, a.U[par ^ 1] + o.u, ufn, Ur, a.Fx + o.fx, a.Fy + o.fy,
-                                   a.Wx[par ^ 1] + o.wx, a.Wy[par ^ 1] + o.wy, a.bad + o.bad, pass, R(c->dt), i, j,
-                                   bad);
+          inv = update_cell<R, TW>(g, Cells<R>{(R*)(a.U[par] + o.u)}, Cells<R>{(R*)(a.U[par ^ 1] + o.u)},
+                                   a.Fx + o.fx, a.Fy + o.fy, a.Wx[par ^ 1] + o.wx, a.Wy[par ^ 1] + o.wy,
+                                   a.bad + o.bad, pass, step_dt<R>(c), i, j, bad);
           if (pass == 1) {
             a.bad[o.bad + (size_t)j * g.nx + i] = bad ? 1 : 0;
             if (bad) {
@@ -223,22 +219,20 @@ __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<
 }
 
 // ---- per-grid state transfer ----
-__global__ void kb_scatter(Geo g, const double* src, double* U, float* Uf, int to_dev) {
+template <class R>
+__global__ void kb_scatter(Geo g, const double* src, Cells<R> U, int to_dev) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
   for (int v = 0; v < 4; ++v) {
     const size_t o = ((size_t)v * g.ny + j) * g.nx + i;
-    if (to_dev) {
-      U[ci(g, v, i, j)] = src[o];
-      if (Uf) Uf[ci(g, v, i, j)] = (float)src[o];
-    } else {
-      const_cast<double*>(src)[o] = U[ci(g, v, i, j)];
-    }
+    if (to_dev) U.set(g, v, i, j, src[o]);
+    else const_cast<double*>(src)[o] = U.get(g, v, i, j);
   }
 }
 
-__global__ void kb_ghost(Geo g, double* U, float* Uf) {
-  ghost_at(g, U, Uf, blockIdx.x * blockDim.x + threadIdx.x);
+template <class R>
+__global__ void kb_ghost(Geo g, Cells<R> U) {
+  ghost_at<R>(g, U, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <class TW>
@@ -249,12 +243,13 @@ __global__ void kb_copyW(const double* src, TW* W, size_t n, int to_dev) {
   else const_cast<double*>(src)[k] = (double)W[k];
 }
 
-__global__ void kb_dtbound(Geo g, const double* U, Ctrl* c) {
+template <class R>
+__global__ void kb_dtbound(Geo g, Cells<R> U, Ctrl* c) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   double inv = 0.0;
   if (i < g.nx && j < g.ny) {
     double w[4];
-    for (int v = 0; v < 4; ++v) w[v] = U[ci(g, v, i, j)];
+    for (int v = 0; v < 4; ++v) w[v] = U.get(g, v, i, j);
     bool ok;
     inv = inv_bound<double>(g, w, ok);
     if (!ok || !(inv < INFINITY)) {
@@ -284,8 +279,7 @@ struct gks_batch {
   GridOff* d_off;
   void* d_fc;
   Ctrl* d_ctrl;
-  double* U[2];
-  float* Uf[2];
+  double* U[2];  // per grid 4 * plane doubles at off.u (Cells<R>)
   void* Wx[2];
   void* Wy[2];
   void* coef;
@@ -367,7 +361,6 @@ Args<R, TW> make_args(gks_batch* b, double cfl) {
   a.ctrl = b->d_ctrl;
   for (int k = 0; k < 2; ++k) {
     a.U[k] = b->U[k];
-    a.Uf[k] = b->Uf[k];
     a.Wx[k] = (TW*)b->Wx[k];
     a.Wy[k] = (TW*)b->Wy[k];
   }
@@ -463,8 +456,6 @@ gks_status gks_batch_create(int n, const gks_grid_desc* grids, const gks_options
     Geo G;
     memset(&G, 0, sizeof(G));
     G.nx = d.nx; G.ny = d.ny;
-    G.pitch = ((d.nx + 2) + 1) & ~1;
-    G.plane = (size_t)(d.ny + 2) * G.pitch;
     G.dx = d.Lx / d.nx; G.dy = d.Ly / d.ny;
     G.gamma = d.gamma; G.mu = d.mu; G.Pr = d.Pr;
     G.weno_eps = o.weno_eps; G.weno_C = o.weno_C; G.tau_eps = o.tau_eps; G.tau_C = o.tau_C;
@@ -476,6 +467,7 @@ gks_status gks_batch_create(int n, const gks_grid_desc* grids, const gks_options
       G.bc.Tw[k] = d.bc[k].T_wall;
       if (d.bc[k].kind < 0 || d.bc[k].kind > 3) { delete b; return GKS_EINVAL; }
     }
+    geo_finish(G);
     if ((G.bc.kind[0] == GKS_BC_PERIODIC) != (G.bc.kind[1] == GKS_BC_PERIODIC) ||
         (G.bc.kind[2] == GKS_BC_PERIODIC) != (G.bc.kind[3] == GKS_BC_PERIODIC)) {
       delete b;
@@ -511,7 +503,6 @@ gks_status gks_batch_create(int n, const gks_grid_desc* grids, const gks_options
   alloc((void**)&b->d_ctrl, sizeof(Ctrl) * n);
   for (int k = 0; k < 2; ++k) {
     alloc((void**)&b->U[k], nu * sizeof(double));
-    if (b->prec == GKS_FP32_BULK) alloc((void**)&b->Uf[k], nu * sizeof(float));
     alloc(&b->Wx[k], nwx * ws);
     alloc(&b->Wy[k], nwy * ws);
   }
@@ -545,7 +536,6 @@ gks_status gks_batch_create(int n, const gks_grid_desc* grids, const gks_options
   if (e == cudaSuccess) {
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
       e = cudaMemset(b->U[k], 0, nu * sizeof(double));
-      if (e == cudaSuccess && b->Uf[k]) e = cudaMemset(b->Uf[k], 0, nu * sizeof(float));
     }
     // control blocks: t = 0, no bound yet
     memset(b->h_ctrl, 0, sizeof(Ctrl) * n);
@@ -581,9 +571,15 @@ gks_status gks_batch_set_state(gks_batch* b, int g, const double* U, const doubl
   const int par = (int)(c.steps & 1);
   const dim3 b2(32, 8);
   BCK(cudaMemcpyAsync(b->staging, U, (size_t)4 * G.nx * G.ny * sizeof(double), cudaMemcpyHostToDevice, b->stream));
-  kb_scatter<<<grid2(G.nx, G.ny, b2), b2, 0, b->stream>>>(G, b->staging, b->U[par] + o.u,
-                                                          b->Uf[par] ? b->Uf[par] + o.u : nullptr, 1);
-  kb_ghost<<<(perimeter(G) + 127) / 128, 128, 0, b->stream>>>(G, b->U[par] + o.u, b->Uf[par] ? b->Uf[par] + o.u : nullptr);
+  if (b->prec == GKS_FP64) {
+    const Cells<double> C{b->U[par] + o.u};
+    kb_scatter<double><<<grid2(G.nx, G.ny, b2), b2, 0, b->stream>>>(G, b->staging, C, 1);
+    kb_ghost<double><<<(perimeter(G) + 127) / 128, 128, 0, b->stream>>>(G, C);
+  } else {
+    const Cells<float> C{(float*)(b->U[par] + o.u)};
+    kb_scatter<float><<<grid2(G.nx, G.ny, b2), b2, 0, b->stream>>>(G, b->staging, C, 1);
+    kb_ghost<float><<<(perimeter(G) + 127) / 128, 128, 0, b->stream>>>(G, C);
+  }
   const size_t nx = (size_t)8 * G.ny * (G.nx + 1), ny = (size_t)8 * (G.ny + 1) * G.nx;
   BCK(cudaMemcpyAsync(b->staging, Wx, nx * sizeof(double), cudaMemcpyHostToDevice, b->stream));
   if (b->prec == GKS_FP64) kb_copyW<double><<<(unsigned)((nx + 255) / 256), 256, 0, b->stream>>>(b->staging, (double*)b->Wx[par] + o.wx, nx, 1);
@@ -598,7 +594,11 @@ gks_status gks_batch_set_state(gks_batch* b, int g, const double* U, const doubl
   const double inf = INFINITY;
   memcpy(&c.bound, &inf, 8);
   BCK(cudaMemcpyAsync(b->d_ctrl + g, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, b->stream));
-  kb_dtbound<<<grid2(G.nx, G.ny, b2), b2, 0, b->stream>>>(G, b->U[par] + o.u, b->d_ctrl + g);
+  if (b->prec == GKS_FP64)
+    kb_dtbound<double><<<grid2(G.nx, G.ny, b2), b2, 0, b->stream>>>(G, Cells<double>{b->U[par] + o.u}, b->d_ctrl + g);
+  else
+    kb_dtbound<float><<<grid2(G.nx, G.ny, b2), b2, 0, b->stream>>>(G, Cells<float>{(float*)(b->U[par] + o.u)},
+                                                                   b->d_ctrl + g);
   BCK(cudaGetLastError());
   BCK(cudaMemcpyAsync(&c, b->d_ctrl + g, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
   BCK(cudaStreamSynchronize(b->stream));
@@ -617,7 +617,11 @@ gks_status gks_batch_get_state(gks_batch* b, int g, double* U, double* Wx, doubl
   const int par = (int)(c.steps & 1);
   const dim3 b2(32, 8);
   if (U) {
-    kb_scatter<<<grid2(G.nx, G.ny, b2), b2, 0, b->stream>>>(G, b->staging, b->U[par] + o.u, nullptr, 0);
+    if (b->prec == GKS_FP64)
+      kb_scatter<double><<<grid2(G.nx, G.ny, b2), b2, 0, b->stream>>>(G, b->staging, Cells<double>{b->U[par] + o.u}, 0);
+    else
+      kb_scatter<float><<<grid2(G.nx, G.ny, b2), b2, 0, b->stream>>>(G, b->staging,
+                                                                     Cells<float>{(float*)(b->U[par] + o.u)}, 0);
     BCK(cudaMemcpyAsync(U, b->staging, (size_t)4 * G.nx * G.ny * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
   }
   const size_t nx = (size_t)8 * G.ny * (G.nx + 1), ny = (size_t)8 * (G.ny + 1) * G.nx;
@@ -722,24 +726,23 @@ gks_status gks_batch_autotune(gks_batch* b, double CFL, int trial_steps, int* fa
   BCK(cudaSetDevice(b->device));
   // the trials advance the batch; save and restore the state and control blocks
   const size_t ws = wsize(b);
-  void* save[6] = {nullptr};
-  const size_t sz[6] = {b->n_u * 8, b->n_u * 4, b->n_wx * ws, b->n_wy * ws, sizeof(Ctrl) * (size_t)b->G, 0};
+  void* save[4] = {nullptr};
+  const size_t sz[4] = {b->n_u * 8, b->n_wx * ws, b->n_wy * ws, sizeof(Ctrl) * (size_t)b->G};
   BCK(cudaStreamSynchronize(b->stream));
   BCK(cudaMemcpy(b->h_ctrl, b->d_ctrl, sizeof(Ctrl) * b->G, cudaMemcpyDeviceToHost));
-  for (int k = 0; k < 5; ++k)
-    if (sz[k] && !(k == 1 && !b->Uf[0])) BCK(cudaMalloc(&save[k], 2 * sz[k]));
+  for (int k = 0; k < 4; ++k) BCK(cudaMalloc(&save[k], 2 * sz[k]));
   auto snapshot = [&](bool restore) -> gks_status {
     for (int par = 0; par < 2; ++par) {
-      void* live[4] = {b->U[par], b->Uf[par], b->Wx[par], b->Wy[par]};
-      for (int k = 0; k < 4; ++k) {
+      void* live[3] = {b->U[par], b->Wx[par], b->Wy[par]};
+      for (int k = 0; k < 3; ++k) {
         if (!save[k]) continue;
         char* s = (char*)save[k] + par * sz[k];
         if (restore) BCK(cudaMemcpyAsync(live[k], s, sz[k], cudaMemcpyDeviceToDevice, b->stream));
         else BCK(cudaMemcpyAsync(s, live[k], sz[k], cudaMemcpyDeviceToDevice, b->stream));
       }
     }
-    if (restore) BCK(cudaMemcpyAsync(b->d_ctrl, save[4], sz[4], cudaMemcpyDeviceToDevice, b->stream));
-    else BCK(cudaMemcpyAsync(save[4], b->d_ctrl, sz[4], cudaMemcpyDeviceToDevice, b->stream));
+    if (restore) BCK(cudaMemcpyAsync(b->d_ctrl, save[3], sz[3], cudaMemcpyDeviceToDevice, b->stream));
+    else BCK(cudaMemcpyAsync(save[3], b->d_ctrl, sz[3], cudaMemcpyDeviceToDevice, b->stream));
     return GKS_OK;
   };
   gks_status st = snapshot(false);
@@ -770,7 +773,7 @@ gks_status gks_batch_autotune(gks_batch* b, double CFL, int trial_steps, int* fa
   cudaEventDestroy(e1);
   if (st == GKS_OK) st = gks_batch_configure(b, bw, bb);
   cudaStreamSynchronize(b->stream);
-  for (int k = 0; k < 5; ++k) cudaFree(save[k]);
+  for (int k = 0; k < 4; ++k) cudaFree(save[k]);
   if (st != GKS_OK) return st;
   if (face_tile_width) *face_tile_width = bw;
   if (blocks_per_sm) *blocks_per_sm = bb;
@@ -805,7 +808,6 @@ void gks_batch_destroy(gks_batch* b) {
   cudaFree(b->d_ctrl);
   for (int k = 0; k < 2; ++k) {
     cudaFree(b->U[k]);
-    cudaFree(b->Uf[k]);
     cudaFree(b->Wx[k]);
     cudaFree(b->Wy[k]);
   }

@@ -17,6 +17,7 @@ struct Ctrl {
   unsigned long long dtb[3];  // running minima of the CFL bound of each update pass of the step
   double t;
   double dt;
+  float dt_f;                 // dt rounded to FP32, for the FP32 kernels
   long long steps;
   int status;
   int skip;
@@ -33,6 +34,13 @@ struct Geo {
   int nx, ny, pitch;  // pitch: row length of the padded cell arrays
   size_t plane;       // (ny+2) * pitch
   double dx, dy;
+  double idx, idy;                  // 1/dx, 1/dy
+  float idx_hi, idx_lo, idy_hi, idy_lo;  // the same as FP32 pairs hi + lo
+  double visc;                      // viscous rate bound 2 mu max(4/3, gamma/Pr) / min(dx, dy)^2
+  float gamma_f, gm1_f, K_f, visc_f;  // gamma, gamma - 1, K = (4 - 2 gamma) / (gamma - 1), visc in FP32
+  float dx_f, dy_f, weno_eps_f, weno_C_f;
+  float uwt_f[4], Tw_f[4];          // tangential wall velocity and wall temperature per side
+  int visc_on;                      // viscous_dt and mu > 0
   double gamma, mu, Pr;
   double weno_eps, weno_C, tau_eps, tau_C;
   int viscous_dt;
@@ -41,6 +49,117 @@ struct Geo {
 
 __host__ __device__ __forceinline__ size_t ci(const Geo& g, int v, int i, int j) {
   return (size_t)v * g.plane + (size_t)(j + 1) * g.pitch + (i + 1);
+}
+
+// derived fields: sizes of the padded arrays, reciprocal cell sizes and FP32
+// copies, from nx, ny, dx, dy, gamma, mu and Pr
+inline void geo_finish(Geo& g) {
+  g.pitch = ((g.nx + 2) + 1) & ~1;
+  g.plane = (size_t)(g.ny + 2) * g.pitch;
+  g.idx = 1.0 / g.dx;
+  g.idy = 1.0 / g.dy;
+  g.idx_hi = (float)g.idx;
+  g.idx_lo = (float)(g.idx - (double)g.idx_hi);
+  g.idy_hi = (float)g.idy;
+  g.idy_lo = (float)(g.idy - (double)g.idy_hi);
+  const double h = g.dx < g.dy ? g.dx : g.dy;
+  const double r = g.gamma / g.Pr > 4.0 / 3.0 ? g.gamma / g.Pr : 4.0 / 3.0;
+  g.visc = 2.0 * g.mu * r / (h * h);
+  g.gamma_f = (float)g.gamma;
+  g.gm1_f = (float)(g.gamma - 1.0);
+  g.K_f = (float)((4.0 - 2.0 * g.gamma) / (g.gamma - 1.0));
+  g.visc_f = (float)g.visc;
+  g.dx_f = (float)g.dx;
+  g.dy_f = (float)g.dy;
+  g.weno_eps_f = (float)g.weno_eps;
+  g.weno_C_f = (float)g.weno_C;
+  for (int k = 0; k < 4; ++k) {
+    g.uwt_f[k] = (float)(k < 2 ? g.bc.vw[k] : g.bc.uw[k]);
+    g.Tw_f[k] = (float)g.bc.Tw[k];
+  }
+  g.visc_on = g.viscous_dt && g.mu > 0.0;
+}
+
+// Geo scalars in the compute type (the FP32 kernels do no FP64 arithmetic)
+template <class R> struct GeoR;
+template <> struct GeoR<double> {
+  static __device__ __forceinline__ double gamma(const Geo& g) { return g.gamma; }
+  static __device__ __forceinline__ double gm1(const Geo& g) { return g.gamma - 1.0; }
+  static __device__ __forceinline__ double K(const Geo& g) { return (4.0 - 2.0 * g.gamma) / (g.gamma - 1.0); }
+  static __device__ __forceinline__ double idx(const Geo& g) { return g.idx; }
+  static __device__ __forceinline__ double idy(const Geo& g) { return g.idy; }
+  static __device__ __forceinline__ double visc(const Geo& g) { return g.visc; }
+  static __device__ __forceinline__ double dx(const Geo& g) { return g.dx; }
+  static __device__ __forceinline__ double dy(const Geo& g) { return g.dy; }
+  static __device__ __forceinline__ double weps(const Geo& g) { return g.weno_eps; }
+  static __device__ __forceinline__ double wC(const Geo& g) { return g.weno_C; }
+  static __device__ __forceinline__ double uwt(const Geo& g, int side) { return side < 2 ? g.bc.vw[side] : g.bc.uw[side]; }
+  static __device__ __forceinline__ double Tw(const Geo& g, int side) { return g.bc.Tw[side]; }
+};
+template <> struct GeoR<float> {
+  static __device__ __forceinline__ float gamma(const Geo& g) { return g.gamma_f; }
+  static __device__ __forceinline__ float gm1(const Geo& g) { return g.gm1_f; }
+  static __device__ __forceinline__ float K(const Geo& g) { return g.K_f; }
+  static __device__ __forceinline__ float idx(const Geo& g) { return g.idx_hi; }
+  static __device__ __forceinline__ float idy(const Geo& g) { return g.idy_hi; }
+  static __device__ __forceinline__ float visc(const Geo& g) { return g.visc_f; }
+  static __device__ __forceinline__ float dx(const Geo& g) { return g.dx_f; }
+  static __device__ __forceinline__ float dy(const Geo& g) { return g.dy_f; }
+  static __device__ __forceinline__ float weps(const Geo& g) { return g.weno_eps_f; }
+  static __device__ __forceinline__ float wC(const Geo& g) { return g.weno_C_f; }
+  static __device__ __forceinline__ float uwt(const Geo& g, int side) { return g.uwt_f[side]; }
+  static __device__ __forceinline__ float Tw(const Geo& g, int side) { return g.Tw_f[side]; }
+};
+
+// dt of the step in the compute type
+template <class R> __device__ __forceinline__ R step_dt(const Ctrl* c);
+template <> __device__ __forceinline__ double step_dt<double>(const Ctrl* c) { return c->dt; }
+template <> __device__ __forceinline__ float step_dt<float>(const Ctrl* c) { return c->dt_f; }
+
+// ---------------------------------------------------------------------------
+// Full-precision cell averages, the state the conservative update accumulates
+// into.  One allocation of 4 * plane doubles per buffer either way:
+//  * FP64 mode: four FP64 planes;
+//  * FP32-bulk mode: each average is an unevaluated sum hi + lo of two FP32
+//    numbers (a double-float pair), hi planes in the first half and lo planes
+//    in the second.  hi is the FP32 rounding of hi + lo, so the hi planes are
+//    the FP32 cell averages every FP32 kernel reads.
+// view() is the compute-type array of the averages.
+// ---------------------------------------------------------------------------
+template <class R> struct Cells;
+template <> struct Cells<double> {
+  double* p;
+  __device__ __forceinline__ double get(const Geo& g, int v, int i, int j) const { return p[ci(g, v, i, j)]; }
+  __device__ __forceinline__ void set(const Geo& g, int v, int i, int j, double w) const { p[ci(g, v, i, j)] = w; }
+  __host__ __device__ __forceinline__ const double* view() const { return p; }
+};
+template <> struct Cells<float> {
+  float* p;  // hi planes; lo planes at p + 4 * plane
+  __device__ __forceinline__ double get(const Geo& g, int v, int i, int j) const {
+    const size_t o = ci(g, v, i, j);
+    return (double)p[o] + (double)p[o + 4 * g.plane];
+  }
+  __device__ __forceinline__ void set(const Geo& g, int v, int i, int j, double w) const {
+    const size_t o = ci(g, v, i, j);
+    const float hi = (float)w;
+    p[o] = hi;
+    p[o + 4 * g.plane] = (float)(w - (double)hi);
+  }
+  __host__ __device__ __forceinline__ const float* view() const { return p; }
+};
+
+// (hi, lo) += f * (sh + sl) for a double-float pair: the product's rounding
+// error (from the FMA) and the addition's (Knuth's TwoSum) are carried in lo,
+// so the pair loses only the roundings of lo itself, ~2^-48 relative.  The
+// _rn intrinsics keep the compiler from fusing the product into the sum.
+__device__ __forceinline__ void df_add_product(float& hi, float& lo, float f, float sh, float sl) {
+  const float p = __fmul_rn(f, sh);
+  const float pe = __fadd_rn(__fmaf_rn(f, sh, -p), __fmul_rn(f, sl));
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, pe));
 }
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
@@ -53,6 +172,7 @@ __device__ __forceinline__ void ctrl_begin(Ctrl* c, double cfl, double dt_max, d
   double dt = fmin(cfl * bitsd(c->bound), dt_max);
   dt = fmin(dt, t_end - c->t);
   c->dt = dt;
+  c->dt_f = (float)dt;
   c->skip = (c->status != GKS_OK || !(dt > 0.0)) ? 1 : 0;
   c->dtb[0] = c->dtb[1] = c->dtb[2] = dbits(INFINITY);
   c->bad_found[0] = c->bad_found[1] = 0;
@@ -105,7 +225,8 @@ __host__ __device__ __forceinline__ double wall_t_velocity(const BCs& b, int sid
 }
 
 // value of a ghost cell; y is resolved first, so corners are x-images of y-ghosts
-__device__ __forceinline__ void ghost_cell(const Geo& g, const double* __restrict__ U, int i, int j, double out[4]) {
+template <class R>
+__device__ __forceinline__ void ghost_cell(const Geo& g, Cells<R> U, int i, int j, double out[4]) {
   int is = i, js = j;
   int xs = -1, ys = -1;  // boundary side applied
   if (j < 0) { ys = 2; js = g.bc.kind[2] == GKS_BC_PERIODIC ? g.ny - 1 : 0; }
@@ -113,7 +234,7 @@ __device__ __forceinline__ void ghost_cell(const Geo& g, const double* __restric
   if (i < 0) { xs = 0; is = g.bc.kind[0] == GKS_BC_PERIODIC ? g.nx - 1 : 0; }
   if (i >= g.nx) { xs = 1; is = g.bc.kind[1] == GKS_BC_PERIODIC ? 0 : g.nx - 1; }
   double w[4], t[4];
-  for (int v = 0; v < 4; ++v) w[v] = U[ci(g, v, is, js)];
+  for (int v = 0; v < 4; ++v) w[v] = U.get(g, v, is, js);
   if (ys >= 0) {
     bc_value(g.bc.kind[ys], g.gamma, wall_t_velocity(g.bc, ys), g.bc.Tw[ys], 1, w, t);
     for (int v = 0; v < 4; ++v) w[v] = t[v];
@@ -127,8 +248,9 @@ __device__ __forceinline__ void ghost_cell(const Geo& g, const double* __restric
 
 __host__ __device__ __forceinline__ int perimeter(const Geo& g) { return 2 * (g.nx + 2) + 2 * g.ny; }
 
-// p-th cell of the ghost ring: fill U (and the FP32 mirror Uf if given)
-__device__ __forceinline__ void ghost_at(const Geo& g, double* U, float* Uf, int p) {
+// p-th cell of the ghost ring (boundary images are taken in FP64)
+template <class R>
+__device__ __forceinline__ void ghost_at(const Geo& g, Cells<R> U, int p) {
   const int row = g.nx + 2;
   int i, j;
   if (p < row) { i = p - 1; j = -1; }
@@ -137,11 +259,8 @@ __device__ __forceinline__ void ghost_at(const Geo& g, double* U, float* Uf, int
   else if (p < 2 * row + 2 * g.ny) { i = g.nx; j = p - 2 * row - g.ny; }
   else return;
   double w[4];
-  ghost_cell(g, U, i, j, w);
-  for (int v = 0; v < 4; ++v) {
-    U[ci(g, v, i, j)] = w[v];
-    if (Uf) Uf[ci(g, v, i, j)] = (float)w[v];
-  }
+  ghost_cell<R>(g, U, i, j, w);
+  for (int v = 0; v < 4; ++v) U.set(g, v, i, j, w[v]);
 }
 
 // ---------------------------------------------------------------------------
@@ -344,10 +463,10 @@ __device__ __forceinline__ void flux_face(const Geo& g, const FaceConst<R>& C, c
   src.hn = C.dn;
   src.ht = C.dtan;
   src.gamma = C.gamma;
-  src.uwt_lo = R(wall_t_velocity(g.bc, lo_side));
-  src.Tw_lo = R(g.bc.Tw[lo_side]);
-  src.uwt_hi = R(wall_t_velocity(g.bc, hi_side));
-  src.Tw_hi = R(g.bc.Tw[hi_side]);
+  src.uwt_lo = GeoR<R>::uwt(g, lo_side);
+  src.Tw_lo = GeoR<R>::Tw(g, lo_side);
+  src.uwt_hi = GeoR<R>::uwt(g, hi_side);
+  src.Tw_hi = GeoR<R>::Tw(g, hi_side);
   src.first_order = false;
 
   R Fl[4], Wm[4], Wp[4];
@@ -372,14 +491,11 @@ template <class R>
 __device__ __forceinline__ R inv_bound(const Geo& g, const R w[4], bool& ok) {
   const R ir = R(1) / w[0];
   const R u = w[1] * ir, v = w[2] * ir;
-  const R p = R(g.gamma - 1.0) * (w[3] - R(0.5) * (w[1] * u + w[2] * v));
+  const R p = GeoR<R>::gm1(g) * (w[3] - R(0.5) * (w[1] * u + w[2] * v));
   ok = w[0] > R(0) && p > R(0);
-  const R c = sqrt(R(g.gamma) * p * ir);
-  R inv = fmax((fabs(u) + c) * R(1.0 / g.dx), (fabs(v) + c) * R(1.0 / g.dy));
-  if (g.viscous_dt && g.mu > 0.0) {
-    const double h = fmin(g.dx, g.dy);
-    inv = fmax(inv, R(2.0 * g.mu * fmax(4.0 / 3.0, g.gamma / g.Pr) / (h * h)) * ir);
-  }
+  const R c = sqrt(GeoR<R>::gamma(g) * p * ir);
+  R inv = fmax((fabs(u) + c) * GeoR<R>::idx(g), (fabs(v) + c) * GeoR<R>::idy(g));
+  if (g.visc_on) inv = fmax(inv, GeoR<R>::visc(g) * ir);
   return inv;
 }
 
@@ -431,11 +547,11 @@ __device__ __forceinline__ void kfvs_face(const Geo& g, const R* U, R gm1, R K, 
     if (g.bc.kind[hi_side] == GKS_BC_PERIODIC) src.cr = 0;
     else src.img_hi = g.bc.kind[hi_side];
   }
-  src.gamma = R(g.gamma);
-  src.uwt_lo = R(wall_t_velocity(g.bc, lo_side));
-  src.Tw_lo = R(g.bc.Tw[lo_side]);
-  src.uwt_hi = R(wall_t_velocity(g.bc, hi_side));
-  src.Tw_hi = R(g.bc.Tw[hi_side]);
+  src.gamma = GeoR<R>::gamma(g);
+  src.uwt_lo = GeoR<R>::uwt(g, lo_side);
+  src.Tw_lo = GeoR<R>::Tw(g, lo_side);
+  src.uwt_hi = GeoR<R>::uwt(g, hi_side);
+  src.Tw_hi = GeoR<R>::Tw(g, hi_side);
   src.first_order = true;
   R Ff[4] = {R(0), R(0), R(0), R(0)}, Wf[4] = {R(0), R(0), R(0), R(0)};
 #pragma unroll
@@ -475,22 +591,52 @@ __device__ __forceinline__ bool face_needs_fix(const Geo& g, const unsigned char
   return (c0 >= 0 && bad[c0]) || (c1 >= 0 && bad[c1]);
 }
 
-// Eq. finite for cell (i, j) into Un (and the FP32 mirror Ufn if given); returns
-// the inverse CFL bound of the new state, 0 with bad = true if it is not
-// physical.  pass 1 takes every face flux from Fx/Fy; pass 2 replaces the faces
-// next to cells marked in pass 1 by the collisionless flux; pass 3 replaces
-// every face.  Replaced faces also get their point values in Wxn/Wyn, written
-// by one cell each (its west and south faces, and the east / north faces of
-// the last column / row).
+// Eq. finite for one variable: FP64 planes take the FP32 or FP64 fluxes in
+// FP64 (differences of FP32 numbers are exact there); the double-float pair
+// takes the FP32 fluxes one product at a time with error-free transformations.
+// Either way each face flux enters both neighbours with the same rounding, so
+// the sum over cells telescopes to roundoff of the accumulation type.
+template <class R>
+__device__ __forceinline__ R update_var(const Geo& g, Cells<double> U, Cells<double> Un, const R f[4][4], int v,
+                                        int i, int j, bool& finite) {
+  const size_t o = ci(g, v, i, j);
+  const double w = U.p[o] + ((double)f[0][v] - (double)f[1][v]) * g.idx + ((double)f[2][v] - (double)f[3][v]) * g.idy;
+  Un.p[o] = w;
+  finite = isfinite(w);
+  return R(w);
+}
+__device__ __forceinline__ float update_var(const Geo& g, Cells<float> U, Cells<float> Un, const float f[4][4],
+                                            int v, int i, int j, bool& finite) {
+  const size_t o = ci(g, v, i, j), lo_off = 4 * g.plane;
+  float hi = U.p[o], lo = U.p[o + lo_off];
+  df_add_product(hi, lo, f[0][v], g.idx_hi, g.idx_lo);
+  df_add_product(hi, lo, -f[1][v], g.idx_hi, g.idx_lo);
+  df_add_product(hi, lo, f[2][v], g.idy_hi, g.idy_lo);
+  df_add_product(hi, lo, -f[3][v], g.idy_hi, g.idy_lo);
+  // renormalise: hi becomes the FP32 rounding of the pair (Dekker's fast two-sum)
+  const float s = __fadd_rn(hi, lo);
+  lo = __fsub_rn(lo, __fsub_rn(s, hi));
+  hi = s;
+  Un.p[o] = hi;
+  Un.p[o + lo_off] = lo;
+  finite = isfinite(hi) && isfinite(lo);
+  return hi;
+}
+
+// Eq. finite for cell (i, j) into Un; returns the inverse CFL bound of the
+// new state, 0 with bad = true if it is not physical.  pass 1 takes every face
+// flux from Fx/Fy; pass 2 replaces the faces next to cells marked in pass 1 by
+// the collisionless flux; pass 3 replaces every face.  Replaced faces also get
+// their point values in Wxn/Wyn, written by one cell each (its west and south
+// faces, and the east / north faces of the last column / row).
 template <class R, class TW>
-__device__ __forceinline__ R update_cell(const Geo& g, const double* __restrict__ U, double* __restrict__ Un,
-                                         float* __restrict__ Ufn, const R* __restrict__ Ur, const R* __restrict__ Fx,
+__device__ __forceinline__ R update_cell(const Geo& g, Cells<R> U, Cells<R> Un, const R* __restrict__ Fx,
                                          const R* __restrict__ Fy, TW* __restrict__ Wxn, TW* __restrict__ Wyn,
                                          const unsigned char* __restrict__ marked, int pass, R dt, int i, int j,
                                          bool& bad) {
   const int nx = g.nx, ny = g.ny;
   const size_t nfx = (size_t)ny * (nx + 1), nfy = (size_t)(ny + 1) * nx;
-  const double idx = 1.0 / g.dx, idy = 1.0 / g.dy;
+  const R* Ur = U.view();
   // the four face fluxes: west, east, south, north
   R f[4][4];
 #pragma unroll
@@ -501,7 +647,7 @@ __device__ __forceinline__ R update_cell(const Geo& g, const double* __restrict_
     f[3][v] = Fy[v * nfy + (size_t)(j + 1) * nx + i];
   }
   if (pass > 1) {
-    const R gm1 = R(g.gamma - 1.0), K = R((4.0 - 2.0 * g.gamma) / (g.gamma - 1.0));
+    const R gm1 = GeoR<R>::gm1(g), K = GeoR<R>::K(g);
 #pragma unroll 1
     for (int q = 0; q < 4; ++q) {
       const int fi = i + (q == 1), fj = j + (q == 3);
@@ -524,20 +670,17 @@ __device__ __forceinline__ R update_cell(const Geo& g, const double* __restrict_
       }
     }
   }
-  double w[4];
   R wr[4];
+  bool finite = true;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    // Eq. finite in FP64: differences of the (possibly FP32) face fluxes are exact in
-    // FP64, so the face fluxes telescope and the update stays conservative
-    w[v] = U[ci(g, v, i, j)] + ((double)f[0][v] - (double)f[1][v]) * idx + ((double)f[2][v] - (double)f[3][v]) * idy;
-    Un[ci(g, v, i, j)] = w[v];
-    wr[v] = R(w[v]);
-    if (Ufn) Ufn[ci(g, v, i, j)] = (float)wr[v];
+    bool fv;
+    wr[v] = update_var(g, U, Un, f, v, i, j, fv);
+    finite = finite && fv;
   }
   bool ok;
   R inv = inv_bound<R>(g, wr, ok);
-  bad = !ok || !isfinite(w[0]) || !isfinite(w[1]) || !isfinite(w[2]) || !isfinite(w[3]) || !(inv < R(INFINITY));
+  bad = !ok || !finite || !(inv < R(INFINITY));
   return bad ? R(0) : inv;
 }
 

@@ -64,16 +64,24 @@ def test_one_step_sampled_fp32_bulk_bench_configuration():
     """The configuration bench.py times: the 512^2 smooth wave in FP32-bulk."""
     p = wl.smooth_wave_2d(512, seed=2)
     cells = _sample_cells(p, 300, seed=2)
-    dt_o, Un_o, _, _, _ = _oracle_one_step_at(p, cells, 0.0)
+    dt_o, Un_o, F, _, _ = _oracle_one_step_at(p, cells, 0.0)
     s = gks.Solver(p, gks.GKS_FP32_BULK, tau_eps=0.0)
     dt_g = s.step(0.5)
     U, _, _, _ = s.state()
     s.close()
     assert dt_g == pytest.approx(dt_o, rel=1e-6)
     got = np.array([U[:, j, i] for j, i in cells])
-    inc = np.abs(Un_o - np.array([p.U[:, j, i] for j, i in cells])).max(axis=0)
-    # the FP32 face evolution errs by ~1e-6 of the per-step change, the FP64 accumulation adds nothing
-    assert np.all(np.max(np.abs(got - Un_o), axis=0) <= 1e-5 * inc + 1e-12)
+    # Each FP32 face flux carries a relative error of a few FP32 ulps (6e-8 each);
+    # the neighbouring fluxes nearly cancel in the update, so the bound is relative to
+    # sum |F| / h of the cell's four faces, not to the (1000x smaller) increment.
+    # The accumulation into the cell average adds ~1e-14 (double-float pair).
+    dx, dy = p.Lx / p.nx, p.Ly / p.ny
+    scale = np.array([(np.abs(F[4 * k]) + np.abs(F[4 * k + 1])) / dx + (np.abs(F[4 * k + 2]) + np.abs(F[4 * k + 3])) / dy
+                      for k in range(len(cells))])
+    err = np.abs(got - Un_o)
+    assert np.all(err <= 2e-6 * scale), (err / scale).max()
+    # and in absolute terms within a few FP32 ulps of the averages (which are 1 to 4)
+    assert err.max() < 2e-6
 
 
 @pytest.mark.parametrize("prec", [gks.GKS_FP64, gks.GKS_FP32_BULK])
@@ -91,19 +99,59 @@ def test_conservation_at_full_size(prec):
 
 @pytest.mark.parametrize("case", ["smooth", "riemann_ns"])
 def test_fp32_bulk_against_fp64_oracle_l1(case):
-    """The FP32-bulk form's density error against the FP64 oracle, relative L1 <= 1e-5."""
+    """The FP32-bulk form's density error against the FP64 oracle, relative L1 <= 1e-5: the
+    smooth wave over 100 steps; the Navier-Stokes Riemann data to t = 0.03, the physical time
+    that 200 steps of the 1024^2 workload reach (8 steps of dt ~ 3.8e-3 here)."""
     if case == "smooth":
-        p, n, te = wl.smooth_wave_2d(64, ny=48, seed=2), 100, 0.0
+        p, n, te, t_end = wl.smooth_wave_2d(64, ny=48, seed=2), 100, 0.0, np.inf
     else:
-        p, n, te = wl.riemann_2d(48, 40, seed=3, mu=1e-4, Pr=0.72), 50, 0.05
+        p, n, te, t_end = wl.riemann_2d(48, 40, seed=3, mu=1e-4, Pr=0.72), 50, 0.05, 0.03
     P = oracle.params(gamma=p.gamma, mu=p.mu, Pr=p.Pr, tau_eps=te)
     st = oracle.State2D(p.nx, p.ny, p.Lx, p.Ly, p.U, p.Wx, p.Wy)
     bc = oracle.bcs([b[0] for b in p.bc])
     s = gks.Solver(p, gks.GKS_FP32_BULK, tau_eps=te)
+    t = 0.0
     for _ in range(n):
+        if t >= t_end:
+            break
         s.step(0.5)
-        assert oracle.step2d(P, st, bc, 0.5)[0] == 0
-    U, _, _, _ = s.state()
+        rc, dt = oracle.step2d(P, st, bc, 0.5)
+        assert rc == 0
+        t += dt
+    U, _, _, tg = s.state()
     s.close()
+    assert tg == pytest.approx(t, rel=1e-5)
+    if case == "riemann_ns":
+        assert 0.03 <= t < 0.035
     l1 = np.sum(np.abs(U[0] - st.U[0])) / np.sum(np.abs(st.U[0]))
     assert l1 <= 1e-5, l1
+
+
+def test_fp32_bulk_riemann_1024_within_the_schemes_own_sensitivity():
+    """The 1024^2 Navier-Stokes Riemann workload for its 200 steps, FP32-bulk against FP64 (the
+    oracle-pinned path).  The seeded quadrants put vortex sheets against the outflow boundaries;
+    their grid-scale growth makes the FP64 scheme diverge from itself when its start is
+    perturbed by 1e-12 (L1 ~1e-2 by step 200).  So the 1e-5 bound holds up to step 100; after
+    that FP32's deviation must stay within 1e-5 + 10x that FP64 control's."""
+    p = wl.riemann_2d(1024, seed=3, mu=1e-4, Pr=0.72)
+    q = wl.riemann_2d(1024, seed=3, mu=1e-4, Pr=0.72)
+    q.U = q.U * (1.0 + 1e-12 * np.random.default_rng(1).standard_normal(q.U.shape))
+    f64 = gks.Solver(p, gks.GKS_FP64, tau_eps=0.05)
+    f32 = gks.Solver(p, gks.GKS_FP32_BULK, tau_eps=0.05)
+    ctl = gks.Solver(q, gks.GKS_FP64, tau_eps=0.05)
+
+    def l1(a, b):
+        ra, rb = a.state()[0][0], b.state()[0][0]
+        return np.sum(np.abs(ra - rb)) / np.sum(np.abs(rb))
+
+    done = 0
+    for m in (50, 100, 150, 200):
+        for s in (f64, f32, ctl):
+            s.advance(m - done, 0.5)
+        done = m
+        e32, ectl = l1(f32, f64), l1(ctl, f64)
+        if m <= 100:
+            assert e32 <= 1e-5, (m, e32)
+        assert e32 <= 1e-5 + 10 * ectl, (m, e32, ectl)
+    for s in (f64, f32, ctl):
+        s.close()
