@@ -46,6 +46,10 @@ __device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double d_rsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float d_rsqrt(float x) { return rsqrtf(x); }
+// quotient of runtime values: IEEE in FP64; in FP32 the fast division (within
+// 2 ulps for divisors below 2^126), far inside the FP32 path's error budget
+__device__ __forceinline__ double d_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float d_div(float a, float b) { return __fdividef(a, b); }
 
 template <class R> GKS_FN R sq(R a) { return a * a; }
 
@@ -63,7 +67,7 @@ struct Moments {
 // kind: 0 full space, +1 over u > 0, -1 over u < 0
 template <class R, int NU, int NV>
 GKS_FN void moments(R U, R V, R lam, R K, int kind, Moments<R, NU, NV>& m) {
-  const R var = R(0.5) / lam;
+  const R var = d_div(R(0.5), lam);
   if (kind == 0) {
     m.u[0] = R(1);
     m.u[1] = U;
@@ -134,7 +138,7 @@ template <class R>
 GKS_FN SolveK<R> solve_k(R U, R V, R lam, R N, R iN) {
   SolveK<R> k;
   const R q2 = U * U + V * V;
-  const R nl = N / lam;
+  const R nl = d_div(N, lam);
   k.U = U;
   k.V = V;
   k.l2 = R(2) * lam;
@@ -169,7 +173,7 @@ struct TimeW {
 
 template <class R>
 GKS_FN void time_weights(R T, R tau, TimeW<R>& w) {
-  const R x = tau > R(0) ? T / tau : R(INFINITY);
+  const R x = tau > R(0) ? d_div(T, tau) : R(INFINITY);
   const R e = tau > R(0) ? d_exp(-x) : R(0);
   const R om = tau > R(0) ? -d_expm1(-x) : R(1);  // 1 - e
   R f1, f2, f3, f4, f5, f6;  // see below
@@ -209,7 +213,7 @@ GKS_FN void time_weights(R T, R tau, TimeW<R>& w) {
     w.E[2] = (T + tau) * e - tau;
     w.E[3] = T - tau + tau * e;
   }
-  w.I[5] = T * T * T / R(3) - tau * T * T;
+  w.I[5] = T * T * T * R(1.0 / 3.0) - tau * T * T;
   w.I[6] = -tau * (R(0.5) * T * T + w.I[9]);
   w.I[7] = tau * om;
   w.I[8] = -w.I[9];
@@ -237,7 +241,7 @@ struct Coefs {
 template <class R, int NU, int NV>
 GKS_FN void coef_systems(const Moments<R, NU, NV>& m, R rho, const SolveK<R>& sk, const R d[5][4],
                          bool time_terms, bool second_time, Coefs<R>& c) {
-  const R ir = R(1) / rho;
+  const R ir = d_div(R(1), rho);
   R r[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = d[0][k] * ir;
@@ -390,7 +394,7 @@ struct FaceState {
 template <class R>
 GKS_FN void prim(const R w[4], R gm1, R& rho, R& U, R& V, R& p) {
   rho = w[0];
-  const R ir = R(1) / rho;
+  const R ir = d_div(R(1), rho);
   U = w[1] * ir;
   V = w[2] * ir;
   p = gm1 * (w[3] - R(0.5) * rho * (U * U + V * V));
@@ -405,6 +409,8 @@ struct FaceParams {
 template <class R>
 struct FaceConst {
   R gamma, gm1, K, N, iN, dn, dtan, y2, mu, pr_fix, tau_eps, tau_C;
+  R dn2_12, dt2_24;             // dn^2 / 12, dtan^2 / 24 (face values of the cell polynomial)
+  R i4n, i4t, i8n2, i2nt, i2t2;  // 1/(4 dn), 1/(4 dt), 1/(8 dn^2), 1/(2 dn dt), 1/(2 dt^2)
   bool ns, prandtl;
 };
 
@@ -419,6 +425,13 @@ GKS_FN FaceConst<R> face_const(const FaceParams& P) {
   c.dn = R(P.dn);
   c.dtan = R(P.dtan);
   c.y2 = R(P.dtan * P.dtan / 12.0);
+  c.dn2_12 = R(P.dn * P.dn / 12.0);
+  c.dt2_24 = R(P.dtan * P.dtan / 24.0);
+  c.i4n = R(1.0 / (4.0 * P.dn));
+  c.i4t = R(1.0 / (4.0 * P.dtan));
+  c.i8n2 = R(1.0 / (8.0 * P.dn * P.dn));
+  c.i2nt = R(1.0 / (2.0 * P.dn * P.dtan));
+  c.i2t2 = R(1.0 / (2.0 * P.dtan * P.dtan));
   c.mu = R(P.mu);
   c.pr_fix = R(1.0 / P.Pr - 1.0);
   c.tau_eps = R(P.tau_eps);
@@ -460,9 +473,9 @@ GKS_FN void wall_image(int kind, R gamma, R uwt, R Tw, const FaceState<R>& in, F
     return;
   }
   const R rho = in.w[0][0], mn = in.w[0][1], mt = in.w[0][2];
-  const R ir = R(1) / rho;
+  const R ir = d_div(R(1), rho);
   const R m2 = mn * mn + mt * mt;
-  const R cT = R(2) * Tw / (gamma - R(1));
+  const R cT = d_div(R(2) * Tw, gamma - R(1));
   // value
   out.w[0][0] = rho;
   out.w[0][1] = -mn;
@@ -521,7 +534,7 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
     FaceState<R> S;
     src.side(k, S);
     prim(S.w[0], C.gm1, rs[k], us[k], vs[k], ps[k]);
-    ls[k] = R(0.5) * rs[k] / ps[k];
+    ls[k] = d_div(R(0.5) * rs[k], ps[k]);
     Moments<R, 4, 3> m;
     moments(us[k], vs[k], ls[k], C.K, k == 0 ? +1 : -1, m);
     R a[4];
@@ -531,11 +544,11 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
   }
   R r0, u0, v0, p0;
   prim(U0, C.gm1, r0, u0, v0, p0);
-  const R lam0 = R(0.5) * r0 / p0;
+  const R lam0 = d_div(R(0.5) * r0, p0);
 
   // Section 4: collision time
-  const R jump = fabs((ps[0] - ps[1]) / (ps[0] + ps[1])) * dt;
-  const R tau = C.ns ? C.mu / p0 + jump : C.tau_eps * dt + C.tau_C * jump;
+  const R jump = fabs(d_div(ps[0] - ps[1], ps[0] + ps[1])) * dt;
+  const R tau = C.ns ? d_div(C.mu, p0) + jump : C.tau_eps * dt + C.tau_C * jump;
   const R tn = C.ns ? tau : R(0);
 
   TimeW<R> tw;
@@ -549,9 +562,7 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
     {
       R avg[2][3][4];
       src.avg(avg);
-      const R i4n = R(1) / (R(4) * C.dn), i4t = R(1) / (R(4) * C.dtan);
-      const R i8n2 = R(1) / (R(8) * C.dn * C.dn), i2nt = R(1) / (R(2) * C.dn * C.dtan);
-      const R i2t2 = R(1) / (R(2) * C.dtan * C.dtan);
+      const R i4n = C.i4n, i4t = C.i4t, i8n2 = C.i8n2, i2nt = C.i2nt, i2t2 = C.i2t2;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const R um = avg[0][0][k], uc = avg[0][1][k], up = avg[0][2][k];
@@ -598,8 +609,8 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
 #pragma unroll
           for (int k = 0; k < 4; ++k) d[q][k] = S.w[q + 1][k];
       }
-      Moments<R, 6, 6> mf;  // full-space moments fix the coefficients of g_k
-      moments(U, V, lam, C.K, 0, mf);
+      Moments<R, 6, 6> mf;  // full-space moments fix the time coefficients of g_k (NS only)
+      if (C.ns) moments(U, V, lam, C.K, 0, mf);
       coef_systems(mf, rho, solve_k(U, V, lam, C.N, C.iN), d, C.ns, false, c);
     }
     if (!C.ns) {
@@ -658,15 +669,15 @@ GKS_FN R minmod(R a, R b) {
 template <class R>
 GKS_FN void recon_var(R c, R e, R w, R n, R s, R em, R ep, R wm, R wp, R nm, R np, R sm,
                                           R sp, R dx, R dy, R weps, R wC, R a[5]) {
-  const R idx = R(1) / dx, idy = R(1) / dy;
+  const R idx = d_div(R(1), dx), idy = d_div(R(1), dy);
   const R idx2 = idx * idx, idy2 = idy * idy;
   // one-sided stencils: face Gauss mean S and neighbour average (Eq. over-sys)
   const R Se = R(0.5) * (em + ep), Sw = R(0.5) * (wm + wp);
   const R Sn = R(0.5) * (nm + np), Ss = R(0.5) * (sm + sp);
   const R a4 = minmod(R(3) * (c + w - R(2) * Sw) * idx2, R(3) * (c + e - R(2) * Se) * idx2);
-  const R a2 = minmod(-R(2) * (Sw - c) * idx + a4 * dx / R(6), R(2) * (Se - c) * idx - a4 * dx / R(6));
+  const R a2 = minmod(-R(2) * (Sw - c) * idx + a4 * dx * R(1.0 / 6.0), R(2) * (Se - c) * idx - a4 * dx * R(1.0 / 6.0));
   const R a5 = minmod(R(3) * (c + s - R(2) * Ss) * idy2, R(3) * (c + n - R(2) * Sn) * idy2);
-  const R a3 = minmod(-R(2) * (Ss - c) * idy + a5 * dy / R(6), R(2) * (Sn - c) * idy - a5 * dy / R(6));
+  const R a3 = minmod(-R(2) * (Ss - c) * idy + a5 * dy * R(1.0 / 6.0), R(2) * (Sn - c) * idy - a5 * dy * R(1.0 / 6.0));
   // cross derivative of the four one-sided stencils with limited a2, a3:
   // sx (sqrt3 Dx/(dx dy) - a3/dx) + sy (sqrt3 Dy/(dx dy) - a2/dy), smallest magnitude
   const R r3 = R(1.7320508075688772) * idx * idy;
@@ -689,13 +700,13 @@ GKS_FN void recon_var(R c, R e, R w, R n, R s, R em, R ep, R wm, R wp, R nm, R n
   const R c6 = R(0.5) * r3 * ((ep - em) - (wp - wm) + (np - nm) - (sp - sm));
   // Eq. average: alpha = 1/(eps + I)^2, I(U1) = C dx dy
   const R dx2 = dx * dx, dy2 = dy * dy;
-  const R I2 = dx2 * (c2 * c2 + (c4 * c4 * dx2 + c6 * c6 * dy2) / R(12)) +
-               dy2 * (c3 * c3 + (c5 * c5 * dy2 + c6 * c6 * dx2) / R(12)) + dx2 * dx2 * c4 * c4 +
+  const R I2 = dx2 * (c2 * c2 + (c4 * c4 * dx2 + c6 * c6 * dy2) * R(1.0 / 12.0)) +
+               dy2 * (c3 * c3 + (c5 * c5 * dy2 + c6 * c6 * dx2) * R(1.0 / 12.0)) + dx2 * dx2 * c4 * c4 +
                dx2 * dy2 * c6 * c6 + dy2 * dy2 * c5 * c5;
   const R I1 = wC * dx * dy;
   const R b1 = weps + I1, b2 = weps + I2;
   // w1 = (1/b1^2) / (1/b1^2 + 1/b2^2) = b2^2 / (b1^2 + b2^2)
-  const R w1 = b2 * b2 / (b1 * b1 + b2 * b2), w2 = R(1) - w1;
+  const R w1 = d_div(b2 * b2, b1 * b1 + b2 * b2), w2 = R(1) - w1;
   a[0] = w1 * a2 + w2 * c2;
   a[1] = w1 * a3 + w2 * c3;
   a[2] = w1 * a4 + w2 * c4;

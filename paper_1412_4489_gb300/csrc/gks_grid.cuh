@@ -295,10 +295,10 @@ __device__ __forceinline__ void recon_cell(const Geo& g, const R* __restrict__ U
     for (int v = 0; v < 4; ++v) {
       const R x = f == 0 ? R(0.5) * dx : (f == 1 ? -R(0.5) * dx : R(0));
       const R y = f == 2 ? R(0.5) * dy : (f == 3 ? -R(0.5) * dy : R(0));
-      w[v] = cbar[v] + a[v][0] * x + a[v][1] * y + a[v][2] * R(0.5) * (x * x - dx * dx / R(12)) +
-             a[v][3] * R(0.5) * (y * y - dy * dy / R(12)) + a[v][4] * x * y;
+      w[v] = cbar[v] + a[v][0] * x + a[v][1] * y + a[v][2] * R(0.5) * (x * x - dx * dx * R(1.0 / 12.0)) +
+             a[v][3] * R(0.5) * (y * y - dy * dy * R(1.0 / 12.0)) + a[v][4] * x * y;
     }
-    const R p = gm1 * (w[3] - R(0.5) * (w[1] * w[1] + w[2] * w[2]) / w[0]);
+    const R p = gm1 * (w[3] - d_div(R(0.5) * (w[1] * w[1] + w[2] * w[2]), w[0]));
     if (!(w[0] > R(0)) || !(p > R(0))) bad = true;
   }
   const size_t N = (size_t)nx * ny, o = (size_t)j * nx + i;
@@ -318,7 +318,7 @@ template <int AX> __device__ __forceinline__ int slot(int v) { return AX == 0 ? 
 // on side s (+1: the face at +h_n/2, -1: at -h_n/2), in the face frame of axis AX
 template <int AX, class R>
 __device__ __forceinline__ void side_state(const Geo& g, const R* __restrict__ U, const R* __restrict__ coef,
-                                           int i, int j, int s, R hn, R ht, FaceState<R>& S) {
+                                           int i, int j, int s, R hn, R hn2_12, R ht2_24, FaceState<R>& S) {
   const size_t N = (size_t)g.nx * g.ny, o = (size_t)j * g.nx + i;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
@@ -330,7 +330,7 @@ __device__ __forceinline__ void side_state(const Geo& g, const R* __restrict__ U
     const R ann = AX == 0 ? a4 : a5, att = AX == 0 ? a5 : a4;
     const int k = slot<AX>(v);
     const R sh = R(s) * R(0.5) * hn;
-    S.w[0][k] = c + an * sh + ann * hn * hn / R(12) - att * ht * ht / R(24);
+    S.w[0][k] = c + an * sh + ann * hn2_12 - att * ht2_24;
     S.w[1][k] = an + ann * sh;
     S.w[2][k] = at + a6 * sh;
     S.w[3][k] = ann;
@@ -348,7 +348,7 @@ struct GridFaceSource {
   int i, j;            // face index (x-faces: i in [0, nx]; y-faces: j in [0, ny])
   int cl, cr;          // the two cells along the normal, after periodic wrap
   int img_lo, img_hi;  // boundary image on the low / high side: 0 none, else the BC kind
-  R hn, ht, gamma, uwt_lo, Tw_lo, uwt_hi, Tw_hi;
+  R hn, ht, hn2_12, ht2_24, gamma, uwt_lo, Tw_lo, uwt_hi, Tw_hi;
 
   __device__ __forceinline__ int cx(int n) const { return AX == 0 ? n : i; }
   __device__ __forceinline__ int cy(int n) const { return AX == 0 ? j : n; }
@@ -394,18 +394,18 @@ struct GridFaceSource {
     if (k == 0) {
       if (img_lo) {
         FaceState<R> in;
-        side_state<AX>(*g, U, coef, cx(cr), cy(cr), -1, hn, ht, in);
+        side_state<AX>(*g, U, coef, cx(cr), cy(cr), -1, hn, hn2_12, ht2_24, in);
         image(img_lo, uwt_lo, Tw_lo, in, S);
       } else {
-        side_state<AX>(*g, U, coef, cx(cl), cy(cl), +1, hn, ht, S);
+        side_state<AX>(*g, U, coef, cx(cl), cy(cl), +1, hn, hn2_12, ht2_24, S);
       }
     } else {
       if (img_hi) {
         FaceState<R> in;
-        side_state<AX>(*g, U, coef, cx(cl), cy(cl), +1, hn, ht, in);
+        side_state<AX>(*g, U, coef, cx(cl), cy(cl), +1, hn, hn2_12, ht2_24, in);
         image(img_hi, uwt_hi, Tw_hi, in, S);
       } else {
-        side_state<AX>(*g, U, coef, cx(cr), cy(cr), -1, hn, ht, S);
+        side_state<AX>(*g, U, coef, cx(cr), cy(cr), -1, hn, hn2_12, ht2_24, S);
       }
     }
   }
@@ -462,6 +462,8 @@ __device__ __forceinline__ void flux_face(const Geo& g, const FaceConst<R>& C, c
   }
   src.hn = C.dn;
   src.ht = C.dtan;
+  src.hn2_12 = C.dn2_12;
+  src.ht2_24 = C.dt2_24;
   src.gamma = C.gamma;
   src.uwt_lo = GeoR<R>::uwt(g, lo_side);
   src.Tw_lo = GeoR<R>::Tw(g, lo_side);
@@ -489,7 +491,7 @@ __device__ __forceinline__ void flux_face(const Geo& g, const FaceConst<R>& C, c
 // ok = rho > 0 and p > 0.  The bound itself is 1/inverse.
 template <class R>
 __device__ __forceinline__ R inv_bound(const Geo& g, const R w[4], bool& ok) {
-  const R ir = R(1) / w[0];
+  const R ir = d_div(R(1), w[0]);
   const R u = w[1] * ir, v = w[2] * ir;
   const R p = GeoR<R>::gm1(g) * (w[3] - R(0.5) * (w[1] * u + w[2] * v));
   ok = w[0] > R(0) && p > R(0);
@@ -561,7 +563,7 @@ __device__ __forceinline__ void kfvs_face(const Geo& g, const R* U, R gm1, R K, 
     R rho, u, v, p;
     prim(S.w[0], gm1, rho, u, v, p);
     Moments<R, 4, 3> m;
-    moments(u, v, R(0.5) * rho / p, K, k == 0 ? +1 : -1, m);
+    moments(u, v, d_div(R(0.5) * rho, p), K, k == 0 ? +1 : -1, m);
     R a[4], b[4];
     psi_mom<0, 0>(m, a);
     psi_mom<1, 0>(m, b);
@@ -654,9 +656,15 @@ __device__ __forceinline__ R update_cell(const Geo& g, Cells<R> U, Cells<R> Un, 
       const bool x = q < 2;
       const bool redo = pass == 3 || (x ? face_needs_fix<0>(g, marked, fi, fj) : face_needs_fix<1>(g, marked, fi, fj));
       if (!redo) continue;
-      R W[4];
-      if (x) kfvs_face<0, R>(g, Ur, gm1, K, fi, fj, dt, f[q], W);
-      else kfvs_face<1, R>(g, Ur, gm1, K, fi, fj, dt, f[q], W);
+      R W[4], Fq[4];
+      if (x) kfvs_face<0, R>(g, Ur, gm1, K, fi, fj, dt, Fq, W);
+      else kfvs_face<1, R>(g, Ur, gm1, K, fi, fj, dt, Fq, W);
+      // constant indices keep f in registers
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq)
+        if (qq == q)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) f[qq][v] = Fq[v];
       const bool owner = q == 0 || q == 2 || (q == 1 && i == nx - 1) || (q == 3 && j == ny - 1);
       if (owner) {
         TW* Wn = x ? Wxn : Wyn;

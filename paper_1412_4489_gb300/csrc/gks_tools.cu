@@ -46,6 +46,7 @@ template <int P> Num<P> d_expm1(const Num<P>& a) { ++C.expm1; return Num<P>(::ex
 template <int P> Num<P> d_erfc(const Num<P>& a) { ++C.erfc; return Num<P>(::erfc(a.v)); }
 template <int P> Num<P> d_sqrt(const Num<P>& a) { ++C.sqrt; return Num<P>(::sqrt(a.v)); }
 template <int P> Num<P> d_rsqrt(const Num<P>& a) { ++C.rsqrt; return Num<P>(1.0 / ::sqrt(a.v)); }
+template <int P> Num<P> d_div(const Num<P>& a, const Num<P>& b) { ++C.div; return Num<P>(a.v / b.v); }
 
 }  // namespace opc
 
