@@ -4,12 +4,12 @@
 Workload: the 2D Euler smooth wave of Section 4.1's analogue on the periodic square
 [0, 2]^2 at 512 x 512 cells (rho = 1 + 0.2 sin(pi (x + y) + phi), U = V = 1, p = 1,
 gamma = 1.4, CFL 0.5, seeded phi), the largest grid of its convergence sweep.  One
-step = ghost fill + compact reconstruction + face evolution on every x- and y-face +
-conservative update + CFL dt reduction, all in the library's CUDA kernels.
+step = compact reconstruction + face evolution on every x- and y-face + conservative
+update with the ghost fill + CFL dt reduction, all in the library's CUDA kernels.
 
-The headline form is FP32-bulk (reconstruction, face evolution and face values in
-FP32; cell averages, update and dt in FP64); the plain FP64 form and the L1 density
-difference between the two are reported in the same line.
+The headline form is FP32-bulk (everything in FP32, the cell averages kept as
+double-float hi + lo pairs updated with compensated arithmetic); the plain FP64 form
+and the L1 density difference between the two are reported in the same line.
 
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the
 solver's stream, with a 256 MiB write between steps to flush L2 (the state is smaller

@@ -168,9 +168,10 @@ int gks_launches_per_step(const gks_handle* h);
 
 /* Takes one step like gks_step(h, CFL, +inf, NULL) with CUDA events recorded on
  * the handle's stream between its kernels, and writes the duration in ms of
- * each of the nine kernels to ms[0..8], in launch order: begin, ghost fill,
- * reconstruction, x-face evolution, y-face evolution, update, the two update
- * passes of the positivity fallback (no work unless a cell needed it), end.
+ * each of the seven kernels to ms[0..6], in launch order: reconstruction (which
+ * also opens the step), x-face evolution, y-face evolution, update (which also
+ * refreshes the ghost ring), the two update passes of the positivity fallback
+ * (no work unless a cell needed it), end.
  * Synchronous; returns the status of the step. */
 gks_status gks_profile_step(gks_handle* h, double CFL, float* ms);
 

@@ -1,17 +1,19 @@
 // GB300 (sm_103a) kernels and C ABI of the compact third-order gas-kinetic
 // scheme (Pan & Xu, arXiv:1412.4489).  See include/gks.h for the interface.
 //
-// One step = six launches on the handle's stream, all reading a device-resident
+// One step = seven launches on the handle's stream, all reading a device-resident
 // control block so that the sequence can be captured once in a CUDA graph:
-//   k_begin    dt = min(CFL * dt_cfl, dt_max, t_end - t) from the running min
-//   k_ghost    one-cell ghost ring of the cell averages (boundary conditions)
-//   k_recon    compact reconstruction of every cell (Section 3.2)
+//   k_recon    dt = min(CFL * dt_cfl, dt_max, t_end - t) from the running min
+//              (block 0), and the compact reconstruction of every cell (Section 3.2)
 //   k_flux<0>  gas evolution at every x-face (Section 2.2, 3.3, 4)
 //   k_flux<1>  gas evolution at every y-face (frame rotated: n = y, t = x)
 //   k_update   conservative update (Eq. finite) into FP64 averages, or in
-//              FP32-bulk mode into double-float (hi + lo FP32) averages, + next
-//              CFL bound (warp-shuffle / block / atomic min) + physical check
+//              FP32-bulk mode into double-float (hi + lo FP32) averages, the
+//              ghost cells that are images of the updated cells, the next CFL
+//              bound (warp-shuffle / block / atomic min) and the physical check;
+//              three passes, the second and third only for the positivity fallback
 //   k_end      advance t and the step counter
+// The ghost ring of a newly set state is filled by k_ghost.
 // Cell averages and face values are double-buffered; the buffer in use is the
 // parity of the device step counter, so a failed step leaves the last good
 // state in place.
@@ -32,7 +34,7 @@ using namespace gks;
 
 namespace {
 
-constexpr int kLaunchesPerStep = 9;
+constexpr int kLaunchesPerStep = 7;
 
 template <class T> struct Store;
 template <> struct Store<double> { static __device__ __forceinline__ double to(double x) { return x; } };
@@ -41,8 +43,6 @@ template <> struct Store<float> { static __device__ __forceinline__ float to(dou
 // ---------------------------------------------------------------------------
 // control kernels
 // ---------------------------------------------------------------------------
-__global__ void k_begin(Ctrl* c, double cfl, double dt_max, double t_end) { ctrl_begin(c, cfl, dt_max, t_end); }
-
 __global__ void k_end(Ctrl* c) { ctrl_end(c); }
 
 // ---------------------------------------------------------------------------
@@ -58,11 +58,18 @@ __global__ void k_ghost(Geo g, Cells<R> U0, Cells<R> U1, const Ctrl* c, int forc
 // ---------------------------------------------------------------------------
 // reconstruction; U is the padded cell-average array in the compute type
 // ---------------------------------------------------------------------------
+// begin = 1: block 0 also opens the step (ctrl_begin); the other blocks then do
+// not look at the skip flag it sets (coefficients of a skipped step go unused)
 template <class R, class TW>
 __global__ void __launch_bounds__(256) k_recon(Geo g, const R* U0, const R* U1, const TW* Wx0, const TW* Wx1,
                                                const TW* Wy0, const TW* Wy1, R* __restrict__ coef, R dx, R dy,
-                                               R weps, R wC, R gm1, const Ctrl* c, int force) {
-  if (!force && c->skip) return;
+                                               R weps, R wC, R gm1, Ctrl* c, int force, int begin, double cfl,
+                                               double dt_max, double t_end) {
+  if (begin) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) ctrl_begin(c, cfl, dt_max, t_end);
+  } else if (!force && c->skip) {
+    return;
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
@@ -75,7 +82,7 @@ __global__ void __launch_bounds__(256) k_recon(Geo g, const R* U0, const R* U1, 
 // ---------------------------------------------------------------------------
 // resident 128-thread blocks per SM the face kernel is compiled for (register cap)
 #ifndef GKS_FLUX_MINB_F32
-#define GKS_FLUX_MINB_F32 4
+#define GKS_FLUX_MINB_F32 3
 #endif
 template <class R> struct FluxBlocks;
 template <> struct FluxBlocks<double> { static constexpr int value = 1; };
@@ -284,16 +291,18 @@ void launch_ghost(gks_handle* h, int force) {
 }
 
 template <class R, class TW>
-void launch_recon(gks_handle* h, int force) {
+void launch_recon(gks_handle* h, int force, int begin = 0, double cfl = 0, double dt_max = 0, double t_end = 0) {
   const Geo& g = h->g;
   const dim3 b2(32, 8);
   k_recon<R, TW><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(
       g, cells<R>(h, 0), cells<R>(h, 1), (const TW*)h->Wx[0], (const TW*)h->Wx[1], (const TW*)h->Wy[0],
       (const TW*)h->Wy[1], (R*)h->coef, R(g.dx), R(g.dy), R(g.weno_eps), R(g.weno_C), R(g.gamma - 1.0), h->ctrl,
-      force);
+      force, begin, cfl, dt_max, t_end);
 }
 
-// ev (optional, 10 events): recorded before each of the nine kernels and after the last
+// ev (optional, kLaunchesPerStep + 1 events): recorded before each kernel and after the last.
+// with_begin_end = false (face evaluation of the current state for gks_debug_flux):
+// the ghost ring is refreshed first and the step is neither opened nor closed.
 template <class R, class TW>
 gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double t_end, bool with_begin_end,
                                bool do_update, int force, cudaEvent_t* ev = nullptr) {
@@ -302,32 +311,28 @@ gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double 
   auto mark = [&](int k) {
     if (ev) cudaEventRecord(ev[k], s);
   };
+  if (!with_begin_end) launch_ghost<R>(h, force);
   mark(0);
-  if (with_begin_end) k_begin<<<1, 1, 0, s>>>(h->ctrl, cfl, dt_max, t_end);
+  launch_recon<R, TW>(h, force, with_begin_end ? 1 : 0, cfl, dt_max, t_end);
   mark(1);
-  launch_ghost<R>(h, force);
-  mark(2);
-  launch_recon<R, TW>(h, force);
-  mark(3);
   const dim3 b2(32, 8), bf(32, 4);
   k_flux<0, R, TW><<<grid2(g.nx + 1, g.ny, bf), bf, 0, s>>>(g, fconst<R>(g, 0), cells<R>(h, 0), cells<R>(h, 1),
                                                              (const R*)h->coef, (TW*)h->Wx[0], (TW*)h->Wx[1],
                                                              (R*)h->Fx, h->ctrl, force);
-  mark(4);
+  mark(2);
   k_flux<1, R, TW><<<grid2(g.nx, g.ny + 1, bf), bf, 0, s>>>(g, fconst<R>(g, 1), cells<R>(h, 0), cells<R>(h, 1),
                                                              (const R*)h->coef, (TW*)h->Wy[0], (TW*)h->Wy[1],
                                                              (R*)h->Fy, h->ctrl, force);
-  mark(5);
+  mark(3);
   for (int pass = 1; pass <= 3; ++pass) {
     if (do_update)
       k_update<R, TW><<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(
           g, cellbuf<R>(h, 0), cellbuf<R>(h, 1), (const R*)h->Fx, (const R*)h->Fy, (TW*)h->Wx[0], (TW*)h->Wx[1],
           (TW*)h->Wy[0], (TW*)h->Wy[1], h->bad, h->ctrl, pass);
-    mark(5 + pass);
+    mark(3 + pass);
   }
-  mark(8);
   if (with_begin_end) k_end<<<1, 1, 0, s>>>(h->ctrl);
-  mark(9);
+  mark(7);
   CK(cudaGetLastError());
   return GKS_OK;
 }
@@ -672,18 +677,18 @@ void gks_destroy(gks_handle* h) {
 const char* gks_last_error(const gks_handle* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
 
 gks_status gks_profile_step(gks_handle* h, double CFL, float* ms) {
-  if (!h || !ms || !(CFL > 0)) return fail(h, GKS_EINVAL, "gks_profile_step: CFL > 0 and ms[9] required");
+  if (!h || !ms || !(CFL > 0)) return fail(h, GKS_EINVAL, "gks_profile_step: CFL > 0 and ms[7] required");
   CK(cudaSetDevice(h->device));
-  cudaEvent_t ev[10];
-  for (int k = 0; k < 10; ++k) CK(cudaEventCreate(&ev[k]));
+  cudaEvent_t ev[kLaunchesPerStep + 1];
+  for (int k = 0; k <= kLaunchesPerStep; ++k) CK(cudaEventCreate(&ev[k]));
   gks_status st = h->prec == GKS_FP64 ? launch_step_kernels<double, double>(h, CFL, INFINITY, INFINITY, true, true, 0, ev)
                                       : launch_step_kernels<float, float>(h, CFL, INFINITY, INFINITY, true, true, 0, ev);
   if (st == GKS_OK) {
-    cudaError_t e = cudaEventSynchronize(ev[9]);
-    for (int k = 0; k < 9 && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
+    cudaError_t e = cudaEventSynchronize(ev[kLaunchesPerStep]);
+    for (int k = 0; k < kLaunchesPerStep && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
     if (e != cudaSuccess) st = fail(h, GKS_ECUDA, std::string("gks_profile_step: ") + cudaGetErrorString(e));
   }
-  for (int k = 0; k < 10; ++k) cudaEventDestroy(ev[k]);
+  for (int k = 0; k <= kLaunchesPerStep; ++k) cudaEventDestroy(ev[k]);
   if (st != GKS_OK) return st;
   st = read_ctrl(h);
   if (st != GKS_OK) return st;
@@ -841,9 +846,9 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
   k_scatter_U<double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, dU, C0, C1, ctrl, 1);
   k_ghost<double><<<(per + 127) / 128, 128, 0, s>>>(g, C0, C1, ctrl, 1);
   k_dtbound<double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, C0, C1, ctrl);
-  k_begin<<<1, 1, 0, s>>>(ctrl, CFL, dt_max, INFINITY);
   k_recon<double, double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, dWx, dWx_out, dWy, dWy_out, coef, g.dx, g.dy,
-                                                            g.weno_eps, g.weno_C, g.gamma - 1.0, ctrl, 0);
+                                                            g.weno_eps, g.weno_C, g.gamma - 1.0, ctrl, 0, 1, CFL,
+                                                            dt_max, INFINITY);
   k_flux<0, double, double><<<grid2(nx + 1, ny, bf), bf, 0, s>>>(g, fconst<double>(g, 0), U0, U1, coef,
                                                                   const_cast<double*>(dWx), dWx_out, Fx, ctrl, 0);
   k_flux<1, double, double><<<grid2(nx, ny + 1, bf), bf, 0, s>>>(g, fconst<double>(g, 1), U0, U1, coef,

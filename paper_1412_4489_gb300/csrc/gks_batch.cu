@@ -3,11 +3,10 @@
 // cooperative kernel per call, captured once in a CUDA graph and replayed.
 //
 // Inside the kernel every step runs its phases over flat work lists of
-// 128-element tiles drawn from all grids (per-grid dt, ghost rings,
-// reconstruction, face evolution of x- and y-faces, update + CFL minimum, and
-// -- only when some cell's update was not physical -- the first-order faces of
-// the positivity fallback and the second update), separated by a device-wide
-// barrier.  The barrier is a
+// 128-element tiles drawn from all grids (per-grid dt, reconstruction, face
+// evolution of x- and y-faces, update + ghost images + CFL minimum, and -- only
+// when some cell's update was not physical -- the passes of the positivity
+// fallback), separated by a device-wide barrier.  The barrier is a
 // counter with a generation word; every wait is bounded in time (globaltimer)
 // and gives up with GKS_ETIMEOUT instead of hanging.  The per-element
 // arithmetic is that of the single-grid kernels (gks_grid.cuh).
@@ -62,10 +61,9 @@ struct Args {
   R* Fx;
   R* Fy;
   unsigned char* bad;
-  const int4* ghost_items;  // (grid, first perimeter index)
   const int4* cell_items;   // (grid, x0, y0, -)
   const int4* face_items;   // (grid, x0, y0, axis)
-  int n_ghost, n_cell, n_face;
+  int n_cell, n_face;
   int cell_tw, face_tw;     // tile widths (heights = 128 / width)
   Barrier* bar;
   double cfl;
@@ -125,17 +123,6 @@ __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<
     if (!grid_barrier(a.bar)) return;
     // every block read the previous step's flags before the barrier above
     if (blockIdx.x == 0 && tid == 0) a.bar->any_bad[0] = a.bar->any_bad[1] = 0;
-
-    // ghost rings
-    for (int it = blockIdx.x; it < a.n_ghost; it += gridDim.x) {
-      const int4 w = a.ghost_items[it];
-      const Ctrl* c = &a.ctrl[w.x];
-      if (c->skip) continue;
-      const int par = (int)(c->steps & 1);
-      const Geo& g = a.geo[w.x];
-      ghost_at<R>(g, Cells<R>{(R*)(a.U[par] + a.off[w.x].u)}, w.y + tid);
-    }
-    if (!grid_barrier(a.bar)) return;
 
     // reconstruction
     for (int it = blockIdx.x; it < a.n_cell; it += gridDim.x) {
@@ -286,10 +273,9 @@ struct gks_batch {
   void* Fx;
   void* Fy;
   unsigned char* bad;
-  int4* d_ghost;
   int4* d_cell;
   int4* d_face;
-  int n_ghost, n_cell, n_face;
+  int n_cell, n_face;
   Barrier* d_bar;
   Ctrl* h_ctrl;  // pinned mirror of all control blocks
   Barrier* h_bar;
@@ -323,11 +309,10 @@ gks_status bfail(gks_batch* b, gks_status s, const std::string& m) {
 size_t wsize(const gks_batch* b) { return b->prec == GKS_FP64 ? 8 : 4; }
 
 gks_status build_items(gks_batch* b) {
-  std::vector<int4> gh, cell, face;
+  std::vector<int4> cell, face;
   const int ch = kThreads / b->cell_tw, fh = kThreads / b->face_tw;
   for (int g = 0; g < b->G; ++g) {
     const Geo& G = b->geo[g];
-    for (int p = 0; p < perimeter(G); p += kThreads) gh.push_back(make_int4(g, p, 0, 0));
     for (int y = 0; y < G.ny; y += ch)
       for (int x = 0; x < G.nx; x += b->cell_tw) cell.push_back(make_int4(g, x, y, 0));
     for (int y = 0; y < G.ny; y += fh)
@@ -335,17 +320,13 @@ gks_status build_items(gks_batch* b) {
     for (int y = 0; y < G.ny + 1; y += fh)
       for (int x = 0; x < G.nx; x += b->face_tw) face.push_back(make_int4(g, x, y, 1));
   }
-  cudaFree(b->d_ghost);
   cudaFree(b->d_cell);
   cudaFree(b->d_face);
-  b->d_ghost = b->d_cell = b->d_face = nullptr;
-  BCK(cudaMalloc(&b->d_ghost, gh.size() * sizeof(int4)));
+  b->d_cell = b->d_face = nullptr;
   BCK(cudaMalloc(&b->d_cell, cell.size() * sizeof(int4)));
   BCK(cudaMalloc(&b->d_face, face.size() * sizeof(int4)));
-  BCK(cudaMemcpy(b->d_ghost, gh.data(), gh.size() * sizeof(int4), cudaMemcpyHostToDevice));
   BCK(cudaMemcpy(b->d_cell, cell.data(), cell.size() * sizeof(int4), cudaMemcpyHostToDevice));
   BCK(cudaMemcpy(b->d_face, face.data(), face.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  b->n_ghost = (int)gh.size();
   b->n_cell = (int)cell.size();
   b->n_face = (int)face.size();
   return GKS_OK;
@@ -368,10 +349,8 @@ Args<R, TW> make_args(gks_batch* b, double cfl) {
   a.Fx = (R*)b->Fx;
   a.Fy = (R*)b->Fy;
   a.bad = b->bad;
-  a.ghost_items = b->d_ghost;
   a.cell_items = b->d_cell;
   a.face_items = b->d_face;
-  a.n_ghost = b->n_ghost;
   a.n_cell = b->n_cell;
   a.n_face = b->n_face;
   a.cell_tw = b->cell_tw;
@@ -815,7 +794,6 @@ void gks_batch_destroy(gks_batch* b) {
   cudaFree(b->Fx);
   cudaFree(b->Fy);
   cudaFree(b->bad);
-  cudaFree(b->d_ghost);
   cudaFree(b->d_cell);
   cudaFree(b->d_face);
   cudaFree(b->d_bar);

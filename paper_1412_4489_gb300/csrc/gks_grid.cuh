@@ -93,6 +93,7 @@ template <> struct GeoR<double> {
   static __device__ __forceinline__ double dy(const Geo& g) { return g.dy; }
   static __device__ __forceinline__ double weps(const Geo& g) { return g.weno_eps; }
   static __device__ __forceinline__ double wC(const Geo& g) { return g.weno_C; }
+  // tangential wall velocity in the face frame: y-component on x-sides, x on y-sides
   static __device__ __forceinline__ double uwt(const Geo& g, int side) { return side < 2 ? g.bc.vw[side] : g.bc.uw[side]; }
   static __device__ __forceinline__ double Tw(const Geo& g, int side) { return g.bc.Tw[side]; }
 };
@@ -118,7 +119,7 @@ template <> __device__ __forceinline__ float step_dt<float>(const Ctrl* c) { ret
 
 // ---------------------------------------------------------------------------
 // Full-precision cell averages, the state the conservative update accumulates
-// into.  One allocation of 4 * plane doubles per buffer either way:
+// into (get / set in FP64; put stores a compute-type value).  One allocation of 4 * plane doubles per buffer either way:
 //  * FP64 mode: four FP64 planes;
 //  * FP32-bulk mode: each average is an unevaluated sum hi + lo of two FP32
 //    numbers (a double-float pair), hi planes in the first half and lo planes
@@ -131,6 +132,7 @@ template <> struct Cells<double> {
   double* p;
   __device__ __forceinline__ double get(const Geo& g, int v, int i, int j) const { return p[ci(g, v, i, j)]; }
   __device__ __forceinline__ void set(const Geo& g, int v, int i, int j, double w) const { p[ci(g, v, i, j)] = w; }
+  __device__ __forceinline__ void put(const Geo& g, int v, int i, int j, double w) const { p[ci(g, v, i, j)] = w; }
   __host__ __device__ __forceinline__ const double* view() const { return p; }
 };
 template <> struct Cells<float> {
@@ -144,6 +146,12 @@ template <> struct Cells<float> {
     const float hi = (float)w;
     p[o] = hi;
     p[o + 4 * g.plane] = (float)(w - (double)hi);
+  }
+  // a value known only in FP32 (ghost images): lo = 0
+  __device__ __forceinline__ void put(const Geo& g, int v, int i, int j, float w) const {
+    const size_t o = ci(g, v, i, j);
+    p[o] = w;
+    p[o + 4 * g.plane] = 0.0f;
   }
   __host__ __device__ __forceinline__ const float* view() const { return p; }
 };
@@ -191,27 +199,28 @@ __device__ __forceinline__ void ctrl_end(Ctrl* c) {
 // ---------------------------------------------------------------------------
 // boundary images of cell averages (ghost ring)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void bc_value(int kind, double gamma, double uwt, double Tw, int axis, const double in[4],
-                                         double out[4]) {
+// in the compute type R: the FP32 kernels read only the FP32 (hi) averages
+template <class R>
+__device__ __forceinline__ void bc_value(int kind, R gamma, R uwt, R Tw, int axis, const R in[4], R out[4]) {
   if (kind == GKS_BC_PERIODIC || kind == GKS_BC_OUTFLOW) {
     for (int k = 0; k < 4; ++k) out[k] = in[k];
     return;
   }
-  double f[4];
+  R f[4];
   f[0] = in[0];
   f[3] = in[3];
   f[1] = axis == 0 ? in[1] : in[2];
   f[2] = axis == 0 ? in[2] : in[1];
-  double o[4];
+  R o[4];
   if (kind == GKS_BC_SLIPWALL) {
     o[0] = f[0]; o[1] = -f[1]; o[2] = f[2]; o[3] = f[3];
   } else {
-    const double rho = f[0], mn = f[1], mt = f[2];
+    const R rho = f[0], mn = f[1], mt = f[2];
     o[0] = rho;
     o[1] = -mn;
-    o[2] = 2.0 * rho * uwt - mt;
-    o[3] = 2.0 * rho * uwt * uwt - 2.0 * uwt * mt + (mn * mn + mt * mt) / rho +
-           2.0 * rho * Tw / (gamma - 1.0) - f[3];
+    o[2] = R(2) * rho * uwt - mt;
+    o[3] = R(2) * rho * uwt * uwt - R(2) * uwt * mt + d_div(mn * mn + mt * mt, rho) +
+           d_div(R(2) * rho * Tw, gamma - R(1)) - f[3];
   }
   out[0] = o[0];
   out[3] = o[3];
@@ -219,34 +228,54 @@ __device__ __forceinline__ void bc_value(int kind, double gamma, double uwt, dou
   out[2] = axis == 0 ? o[2] : o[1];
 }
 
-__host__ __device__ __forceinline__ double wall_t_velocity(const BCs& b, int side) {
-  // tangential wall velocity in the face frame: y-component on x-sides, x on y-sides
-  return side < 2 ? b.vw[side] : b.uw[side];
-}
-
-// value of a ghost cell; y is resolved first, so corners are x-images of y-ghosts
+// value of a ghost cell from the compute-type averages; y is resolved first, so
+// corners are x-images of y-ghosts
 template <class R>
-__device__ __forceinline__ void ghost_cell(const Geo& g, Cells<R> U, int i, int j, double out[4]) {
+__device__ __forceinline__ void ghost_cell(const Geo& g, const R* U, int i, int j, R out[4]) {
   int is = i, js = j;
   int xs = -1, ys = -1;  // boundary side applied
   if (j < 0) { ys = 2; js = g.bc.kind[2] == GKS_BC_PERIODIC ? g.ny - 1 : 0; }
   if (j >= g.ny) { ys = 3; js = g.bc.kind[3] == GKS_BC_PERIODIC ? 0 : g.ny - 1; }
   if (i < 0) { xs = 0; is = g.bc.kind[0] == GKS_BC_PERIODIC ? g.nx - 1 : 0; }
   if (i >= g.nx) { xs = 1; is = g.bc.kind[1] == GKS_BC_PERIODIC ? 0 : g.nx - 1; }
-  double w[4], t[4];
-  for (int v = 0; v < 4; ++v) w[v] = U.get(g, v, is, js);
+  R w[4], t[4];
+  for (int v = 0; v < 4; ++v) w[v] = U[ci(g, v, is, js)];
   if (ys >= 0) {
-    bc_value(g.bc.kind[ys], g.gamma, wall_t_velocity(g.bc, ys), g.bc.Tw[ys], 1, w, t);
+    bc_value<R>(g.bc.kind[ys], GeoR<R>::gamma(g), GeoR<R>::uwt(g, ys), GeoR<R>::Tw(g, ys), 1, w, t);
     for (int v = 0; v < 4; ++v) w[v] = t[v];
   }
   if (xs >= 0) {
-    bc_value(g.bc.kind[xs], g.gamma, wall_t_velocity(g.bc, xs), g.bc.Tw[xs], 0, w, t);
+    bc_value<R>(g.bc.kind[xs], GeoR<R>::gamma(g), GeoR<R>::uwt(g, xs), GeoR<R>::Tw(g, xs), 0, w, t);
     for (int v = 0; v < 4; ++v) w[v] = t[v];
   }
   for (int v = 0; v < 4; ++v) out[v] = w[v];
 }
 
 __host__ __device__ __forceinline__ int perimeter(const Geo& g) { return 2 * (g.nx + 2) + 2 * g.ny; }
+
+// Every ghost cell is the boundary image of exactly one interior cell (the one
+// ghost_cell reads).  ghosts_of_cell refreshes the ghosts whose source is
+// interior cell (i, j) from U, so the update that writes (i, j) also writes
+// them and a step needs no separate ghost pass.
+template <class R>
+__device__ __forceinline__ void ghosts_of_cell(const Geo& g, Cells<R> U, int i, int j) {
+  int gx[3], gy[3], mx = 1, my = 1;
+  gx[0] = i;
+  gy[0] = j;
+  const bool px = g.bc.kind[0] == GKS_BC_PERIODIC, py = g.bc.kind[2] == GKS_BC_PERIODIC;
+  if (i == (px ? g.nx - 1 : 0)) gx[mx++] = -1;
+  if (i == (px ? 0 : g.nx - 1)) gx[mx++] = g.nx;
+  if (j == (py ? g.ny - 1 : 0)) gy[my++] = -1;
+  if (j == (py ? 0 : g.ny - 1)) gy[my++] = g.ny;
+  if (mx == 1 && my == 1) return;
+  for (int a = 0; a < mx; ++a)
+    for (int b = 0; b < my; ++b) {
+      if (a == 0 && b == 0) continue;
+      R w[4];
+      ghost_cell<R>(g, U.view(), gx[a], gy[b], w);
+      for (int v = 0; v < 4; ++v) U.put(g, v, gx[a], gy[b], w[v]);
+    }
+}
 
 // p-th cell of the ghost ring (boundary images are taken in FP64)
 template <class R>
@@ -258,9 +287,9 @@ __device__ __forceinline__ void ghost_at(const Geo& g, Cells<R> U, int p) {
   else if (p < 2 * row + g.ny) { i = -1; j = p - 2 * row; }
   else if (p < 2 * row + 2 * g.ny) { i = g.nx; j = p - 2 * row - g.ny; }
   else return;
-  double w[4];
-  ghost_cell<R>(g, U, i, j, w);
-  for (int v = 0; v < 4; ++v) U.set(g, v, i, j, w[v]);
+  R w[4];
+  ghost_cell<R>(g, U.view(), i, j, w);
+  for (int v = 0; v < 4; ++v) U.put(g, v, i, j, w[v]);
 }
 
 // ---------------------------------------------------------------------------
@@ -625,8 +654,9 @@ __device__ __forceinline__ float update_var(const Geo& g, Cells<float> U, Cells<
   return hi;
 }
 
-// Eq. finite for cell (i, j) into Un; returns the inverse CFL bound of the
-// new state, 0 with bad = true if it is not physical.  pass 1 takes every face
+// Eq. finite for cell (i, j) into Un, and the ghost cells that are images of
+// (i, j); returns the inverse CFL bound of the new state, 0 with bad = true if
+// it is not physical.  pass 1 takes every face
 // flux from Fx/Fy; pass 2 replaces the faces next to cells marked in pass 1 by
 // the collisionless flux; pass 3 replaces every face.  Replaced faces also get
 // their point values in Wxn/Wyn, written by one cell each (its west and south
@@ -686,6 +716,7 @@ __device__ __forceinline__ R update_cell(const Geo& g, Cells<R> U, Cells<R> Un, 
     wr[v] = update_var(g, U, Un, f, v, i, j, fv);
     finite = finite && fv;
   }
+  ghosts_of_cell<R>(g, Un, i, j);
   bool ok;
   R inv = inv_bound<R>(g, wr, ok);
   bad = !ok || !finite || !(inv < R(INFINITY));

@@ -226,12 +226,12 @@ def gks_launches_per_step(h) -> int:
     return load().gks_launches_per_step(h)
 
 
-KERNEL_NAMES = ["begin", "ghost", "recon", "flux_x", "flux_y", "update", "update2", "update3", "end"]
+KERNEL_NAMES = ["recon", "flux_x", "flux_y", "update", "update2", "update3", "end"]
 
 
 def gks_profile_step(h, CFL):
     """One step with per-kernel CUDA-event timing; returns {kernel name: ms}."""
-    ms = (ctypes.c_float * 9)()
+    ms = (ctypes.c_float * len(KERNEL_NAMES))()
     _check(h, load().gks_profile_step(h, float(CFL), ms))
     return dict(zip(KERNEL_NAMES, list(ms)))
 
