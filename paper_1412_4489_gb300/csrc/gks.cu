@@ -43,7 +43,10 @@ template <> struct Store<float> { static __device__ __forceinline__ float to(dou
 // ---------------------------------------------------------------------------
 // control kernels
 // ---------------------------------------------------------------------------
-__global__ void k_end(Ctrl* c) { ctrl_end(c); }
+__global__ void k_end(Ctrl* c) {
+  pdl_enter();
+  ctrl_end(c);
+}
 
 // ---------------------------------------------------------------------------
 // ghost ring: perimeter of the padded cell array of the current buffer
@@ -65,6 +68,7 @@ __global__ void __launch_bounds__(256) k_recon(Geo g, const R* U0, const R* U1, 
                                                const TW* Wy0, const TW* Wy1, R* __restrict__ coef, R dx, R dy,
                                                R weps, R wC, R gm1, Ctrl* c, int force, int begin, double cfl,
                                                double dt_max, double t_end) {
+  pdl_enter();
   if (begin) {
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) ctrl_begin(c, cfl, dt_max, t_end);
   } else if (!force && c->skip) {
@@ -92,6 +96,7 @@ template <int AX, class R, class TW>
 __global__ void __launch_bounds__(128, FluxBlocks<R>::value) k_flux(Geo g, FaceConst<R> C, const R* U0, const R* U1,
                                                                     const R* __restrict__ coef, TW* Wn0, TW* Wn1,
                                                                     R* __restrict__ F, const Ctrl* c, int force) {
+  pdl_enter();
   if (!force && c->skip) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -113,6 +118,7 @@ template <class R, class TW>
 __global__ void __launch_bounds__(256) k_update(Geo g, Cells<R> U0, Cells<R> U1, const R* __restrict__ Fx,
                                                 const R* __restrict__ Fy, TW* Wx0, TW* Wx1, TW* Wy0, TW* Wy1,
                                                 unsigned char* __restrict__ bad, Ctrl* c, int pass) {
+  pdl_enter();
   if (c->skip || (pass == 2 && !c->bad_found[0]) || (pass == 3 && !c->bad_found[1])) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -274,6 +280,22 @@ gks_status fail(gks_handle* h, gks_status s, const std::string& msg) {
 
 dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
 
+// launch of a step kernel; pdl: with programmatic stream serialisation (see pdl_enter)
+template <typename... KArgs, typename... Args>
+cudaError_t launch(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ev (optional, 10 events): recorded before each of the nine kernels and after the last
 template <class R>
 FaceConst<R> fconst(const Geo& g, int axis) {
@@ -291,13 +313,13 @@ void launch_ghost(gks_handle* h, int force) {
 }
 
 template <class R, class TW>
-void launch_recon(gks_handle* h, int force, int begin = 0, double cfl = 0, double dt_max = 0, double t_end = 0) {
+cudaError_t launch_recon(gks_handle* h, int force, int begin = 0, double cfl = 0, double dt_max = 0,
+                         double t_end = 0, bool pdl = false) {
   const Geo& g = h->g;
   const dim3 b2(32, 8);
-  k_recon<R, TW><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(
-      g, cells<R>(h, 0), cells<R>(h, 1), (const TW*)h->Wx[0], (const TW*)h->Wx[1], (const TW*)h->Wy[0],
-      (const TW*)h->Wy[1], (R*)h->coef, R(g.dx), R(g.dy), R(g.weno_eps), R(g.weno_C), R(g.gamma - 1.0), h->ctrl,
-      force, begin, cfl, dt_max, t_end);
+  return launch(pdl, k_recon<R, TW>, grid2(g.nx, g.ny, b2), b2, h->stream, g, cells<R>(h, 0), cells<R>(h, 1),
+         (const TW*)h->Wx[0], (const TW*)h->Wx[1], (const TW*)h->Wy[0], (const TW*)h->Wy[1], (R*)h->coef, R(g.dx),
+         R(g.dy), R(g.weno_eps), R(g.weno_C), R(g.gamma - 1.0), h->ctrl, force, begin, cfl, dt_max, t_end);
 }
 
 // ev (optional, kLaunchesPerStep + 1 events): recorded before each kernel and after the last.
@@ -312,27 +334,33 @@ gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double 
     if (ev) cudaEventRecord(ev[k], s);
   };
   if (!with_begin_end) launch_ghost<R>(h, force);
+  // programmatic dependent launch between the step's kernels, except when events
+  // are recorded between them (per-kernel timing)
+  const bool pdl = ev == nullptr;
+  cudaError_t le = cudaSuccess;
+  auto keep = [&](cudaError_t e) {
+    if (le == cudaSuccess) le = e;
+  };
   mark(0);
-  launch_recon<R, TW>(h, force, with_begin_end ? 1 : 0, cfl, dt_max, t_end);
+  keep(launch_recon<R, TW>(h, force, with_begin_end ? 1 : 0, cfl, dt_max, t_end, pdl));
   mark(1);
   const dim3 b2(32, 8), bf(32, 4);
-  k_flux<0, R, TW><<<grid2(g.nx + 1, g.ny, bf), bf, 0, s>>>(g, fconst<R>(g, 0), cells<R>(h, 0), cells<R>(h, 1),
-                                                             (const R*)h->coef, (TW*)h->Wx[0], (TW*)h->Wx[1],
-                                                             (R*)h->Fx, h->ctrl, force);
+  keep(launch(pdl, k_flux<0, R, TW>, grid2(g.nx + 1, g.ny, bf), bf, s, g, fconst<R>(g, 0), cells<R>(h, 0),
+         cells<R>(h, 1), (const R*)h->coef, (TW*)h->Wx[0], (TW*)h->Wx[1], (R*)h->Fx, (const Ctrl*)h->ctrl, force));
   mark(2);
-  k_flux<1, R, TW><<<grid2(g.nx, g.ny + 1, bf), bf, 0, s>>>(g, fconst<R>(g, 1), cells<R>(h, 0), cells<R>(h, 1),
-                                                             (const R*)h->coef, (TW*)h->Wy[0], (TW*)h->Wy[1],
-                                                             (R*)h->Fy, h->ctrl, force);
+  keep(launch(pdl, k_flux<1, R, TW>, grid2(g.nx, g.ny + 1, bf), bf, s, g, fconst<R>(g, 1), cells<R>(h, 0),
+         cells<R>(h, 1), (const R*)h->coef, (TW*)h->Wy[0], (TW*)h->Wy[1], (R*)h->Fy, (const Ctrl*)h->ctrl, force));
   mark(3);
   for (int pass = 1; pass <= 3; ++pass) {
     if (do_update)
-      k_update<R, TW><<<grid2(g.nx, g.ny, b2), b2, 0, s>>>(
-          g, cellbuf<R>(h, 0), cellbuf<R>(h, 1), (const R*)h->Fx, (const R*)h->Fy, (TW*)h->Wx[0], (TW*)h->Wx[1],
-          (TW*)h->Wy[0], (TW*)h->Wy[1], h->bad, h->ctrl, pass);
+      keep(launch(pdl, k_update<R, TW>, grid2(g.nx, g.ny, b2), b2, s, g, cellbuf<R>(h, 0), cellbuf<R>(h, 1),
+                  (const R*)h->Fx, (const R*)h->Fy, (TW*)h->Wx[0], (TW*)h->Wx[1], (TW*)h->Wy[0], (TW*)h->Wy[1],
+                  h->bad, h->ctrl, pass));
     mark(3 + pass);
   }
-  if (with_begin_end) k_end<<<1, 1, 0, s>>>(h->ctrl);
+  if (with_begin_end) keep(launch(pdl, k_end, dim3(1), dim3(1), s, h->ctrl));
   mark(7);
+  CK(le);
   CK(cudaGetLastError());
   return GKS_OK;
 }

@@ -597,7 +597,9 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
   // ---- kinetic part, Eq. dis2, for both sides ----
 #pragma unroll 1
   for (int side = 0; side < 2; ++side) {
-    const R rho = rs[side], U = us[side], V = vs[side], lam = ls[side];
+    // selects, not indexing: a dynamic index would put these arrays in local memory
+    const R rho = side ? rs[1] : rs[0], U = side ? us[1] : us[0];
+    const R V = side ? vs[1] : vs[0], lam = side ? ls[1] : ls[0];
     Coefs<R> c;
     {
       R d[5][4];

@@ -170,6 +170,16 @@ __device__ __forceinline__ void df_add_product(float& hi, float& lo, float f, fl
   lo = __fadd_rn(lo, __fadd_rn(e, pe));
 }
 
+// Programmatic dependent launch: a step kernel launched with programmatic stream
+// serialisation first waits for its predecessor grid to complete (and its writes
+// to be visible), then lets its own successor be scheduled once every block of
+// this grid is resident, so that launch latency overlaps execution.  Without the
+// launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
 
@@ -259,21 +269,21 @@ __host__ __device__ __forceinline__ int perimeter(const Geo& g) { return 2 * (g.
 // them and a step needs no separate ghost pass.
 template <class R>
 __device__ __forceinline__ void ghosts_of_cell(const Geo& g, Cells<R> U, int i, int j) {
-  int gx[3], gy[3], mx = 1, my = 1;
-  gx[0] = i;
-  gy[0] = j;
   const bool px = g.bc.kind[0] == GKS_BC_PERIODIC, py = g.bc.kind[2] == GKS_BC_PERIODIC;
-  if (i == (px ? g.nx - 1 : 0)) gx[mx++] = -1;
-  if (i == (px ? 0 : g.nx - 1)) gx[mx++] = g.nx;
-  if (j == (py ? g.ny - 1 : 0)) gy[my++] = -1;
-  if (j == (py ? 0 : g.ny - 1)) gy[my++] = g.ny;
-  if (mx == 1 && my == 1) return;
-  for (int a = 0; a < mx; ++a)
-    for (int b = 0; b < my; ++b) {
-      if (a == 0 && b == 0) continue;
+  // candidate x (y) coordinates: the cell's own, the low ghost, the high ghost
+  const bool xl = i == (px ? g.nx - 1 : 0), xh = i == (px ? 0 : g.nx - 1);
+  const bool yl = j == (py ? g.ny - 1 : 0), yh = j == (py ? 0 : g.ny - 1);
+  if (!(xl || xh || yl || yh)) return;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if ((a == 0 && b == 0) || (a == 1 && !xl) || (a == 2 && !xh) || (b == 1 && !yl) || (b == 2 && !yh)) continue;
+      const int gi = a == 0 ? i : (a == 1 ? -1 : g.nx), gj = b == 0 ? j : (b == 1 ? -1 : g.ny);
       R w[4];
-      ghost_cell<R>(g, U.view(), gx[a], gy[b], w);
-      for (int v = 0; v < 4; ++v) U.put(g, v, gx[a], gy[b], w[v]);
+      ghost_cell<R>(g, U.view(), gi, gj, w);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) U.put(g, v, gi, gj, w[v]);
     }
 }
 
