@@ -285,69 +285,128 @@ GKS_FN void coef_systems(const Moments<R, NU, NV>& m, R rho, const SolveK<R>& sk
 
 // The interface distribution grouped by velocity monomial: f = sum over
 // m in {1, u, v, u^2, u v, v^2} of X_m(psi) m g, plus y X'_m for the part
-// linear along the face.  accumulate() adds
-//   flux   += rho sum <X_m m u psi>       (time-integrated weights)
-//   point0 += rho sum <X_m m psi>          (weights at t = dt)
-//   point1 += rho sum <X'_m m psi>         (weights at t = dt, y-linear part)
-//   mean   += rho sum <X_m m psi>          (time-integrated weights; heat flux)
+// linear along the face.  The moments of f are taken by expanding
+// P = sum_m m X_m(psi) into monomials u^a v^b (xi^2)^c first (a + b <= 4 for
+// c = 0, a + b <= 2 for c = 1) and then pairing each monomial with the moment
+// table of g (moments factorise: <u^a v^b xi^2c> = <u^a><v^b><xi^2c>):
+//   flux   += rho <u P psi>           (time-integrated weights)
+//   point0 += rho <P psi>             (weights at t = dt)
+//   point1 += rho <P' psi>            (weights at t = dt, y-linear part)
+//   mean   += rho <P psi>             (time-integrated weights; heat flux)
 template <class R>
 struct Groups {
   R X1[4], Xu[4], Xv[4], Xuu[4], Xuv[4], Xvv[4];
 };
 
+// monomial coefficients: c0[(b, a)] for u^a v^b, a + b <= 4, stored by b then a
+// (offsets 0, 5, 9, 12, 14); c1[(b, a)] for u^a v^b xi^2, a + b <= 2 (offsets 0, 3, 5)
+template <class R>
+struct Poly {
+  R c0[15], c1[6];
+};
+
+GKS_FN constexpr int pidx0(int a, int b) { return (b == 0 ? 0 : b == 1 ? 5 : b == 2 ? 9 : b == 3 ? 12 : 14) + a; }
+GKS_FN constexpr int pidx1(int a, int b) { return (b == 0 ? 0 : b == 1 ? 3 : 5) + a; }
+
+// P of the six groups (FULL) or of the first three only (the y-linear part)
+template <bool FULL, class R>
+GKS_FN void poly_of(const Groups<R>& g, Poly<R>& P) {
+  const R h1 = R(0.5) * g.X1[3], hu = R(0.5) * g.Xu[3], hv = R(0.5) * g.Xv[3];
+  // X (psi) = X0 + X1 u + X2 v + X3 (u^2 + v^2 + xi^2) / 2, times the group's monomial
+  P.c0[pidx0(0, 0)] = g.X1[0];
+  P.c0[pidx0(1, 0)] = g.X1[1] + g.Xu[0];
+  P.c0[pidx0(0, 1)] = g.X1[2] + g.Xv[0];
+  P.c0[pidx0(2, 0)] = h1 + g.Xu[1];
+  P.c0[pidx0(1, 1)] = g.Xu[2] + g.Xv[1];
+  P.c0[pidx0(0, 2)] = h1 + g.Xv[2];
+  P.c0[pidx0(3, 0)] = hu;
+  P.c0[pidx0(2, 1)] = hv;
+  P.c0[pidx0(1, 2)] = hu;
+  P.c0[pidx0(0, 3)] = hv;
+  P.c1[pidx1(0, 0)] = h1;
+  P.c1[pidx1(1, 0)] = hu;
+  P.c1[pidx1(0, 1)] = hv;
+  if (FULL) {
+    const R huu = R(0.5) * g.Xuu[3], huv = R(0.5) * g.Xuv[3], hvv = R(0.5) * g.Xvv[3];
+    P.c0[pidx0(2, 0)] += g.Xuu[0];
+    P.c0[pidx0(1, 1)] += g.Xuv[0];
+    P.c0[pidx0(0, 2)] += g.Xvv[0];
+    P.c0[pidx0(3, 0)] += g.Xuu[1];
+    P.c0[pidx0(2, 1)] += g.Xuu[2] + g.Xuv[1];
+    P.c0[pidx0(1, 2)] += g.Xuv[2] + g.Xvv[1];
+    P.c0[pidx0(0, 3)] += g.Xvv[2];
+    P.c0[pidx0(4, 0)] = huu;
+    P.c0[pidx0(3, 1)] = huv;
+    P.c0[pidx0(2, 2)] = huu + hvv;
+    P.c0[pidx0(1, 3)] = huv;
+    P.c0[pidx0(0, 4)] = hvv;
+    P.c1[pidx1(2, 0)] = huu;
+    P.c1[pidx1(1, 1)] = huv;
+    P.c1[pidx1(0, 2)] = hvv;
+  }
+}
+
+// out += rho <u^SU P psi>, psi = (1, u, v, (u^2 + v^2 + xi^2) / 2); D / D1: the
+// degree of P in (u, v) for c = 0 / c = 1 (4 / 2, or 3 / 1 for the y-linear part)
+template <int SU, int D, int D1, class R, int NU, int NV>
+GKS_FN void poly_moments(const Poly<R>& P, const Moments<R, NU, NV>& m, R rho, R out[4]) {
+  static_assert(D + SU + 2 < NU && D + 2 < NV, "moment table too short");
+  R o0 = R(0), o1 = R(0), o2 = R(0), o3 = R(0);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int Dc = c == 0 ? D : D1;
+    const R xa = c == 0 ? R(1) : m.xi2;    // <xi^2c>
+    const R xb = c == 0 ? m.xi2 : m.xi4;  // <xi^2(c+1)>
+#pragma unroll
+    for (int b = 0; b <= Dc; ++b) {
+      R s0 = R(0), s1 = R(0), s2 = R(0);  // sum_a p u^(a+SU), u^(a+SU+1), u^(a+SU+2) moments
+#pragma unroll
+      for (int a = 0; a <= Dc - b; ++a) {
+        const R p = c == 0 ? P.c0[pidx0(a, b)] : P.c1[pidx1(a, b)];
+        s0 += p * m.u[a + SU];
+        s1 += p * m.u[a + SU + 1];
+        s2 += p * m.u[a + SU + 2];
+      }
+      const R vb = xa * m.v[b];
+      o0 += s0 * vb;
+      o1 += s1 * vb;
+      o2 += s0 * (xa * m.v[b + 1]);
+      o3 += s2 * vb + s0 * (xa * m.v[b + 2] + xb * m.v[b]);
+    }
+  }
+  out[0] += rho * o0;
+  out[1] += rho * o1;
+  out[2] += rho * o2;
+  out[3] += rho * (R(0.5) * o3);
+}
+
 template <class R, int NU, int NV>
 GKS_FN void add_flux(const Groups<R>& g, const Moments<R, NU, NV>& m, R rho, R out[4]) {
-  R t[4], s[4];
-  coef_mom<1, 0>(g.X1, m, s);
-  coef_mom<2, 0>(g.Xu, m, t);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) s[k] += t[k];
-  coef_mom<1, 1>(g.Xv, m, t);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) s[k] += t[k];
-  coef_mom<3, 0>(g.Xuu, m, t);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) s[k] += t[k];
-  coef_mom<2, 1>(g.Xuv, m, t);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) s[k] += t[k];
-  coef_mom<1, 2>(g.Xvv, m, t);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) out[k] += rho * (s[k] + t[k]);
+  Poly<R> P;
+  poly_of<true>(g, P);
+  poly_moments<1, 4, 2>(P, m, rho, out);
 }
 
 template <class R, int NU, int NV>
 GKS_FN void add_point(const Groups<R>& g, const Moments<R, NU, NV>& m, R rho, R out[4]) {
-  R t[4], s[4];
-  coef_mom<0, 0>(g.X1, m, s);
-  coef_mom<1, 0>(g.Xu, m, t);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) s[k] += t[k];
-  coef_mom<0, 1>(g.Xv, m, t);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) s[k] += t[k];
-  coef_mom<2, 0>(g.Xuu, m, t);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) s[k] += t[k];
-  coef_mom<1, 1>(g.Xuv, m, t);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) s[k] += t[k];
-  coef_mom<0, 2>(g.Xvv, m, t);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) out[k] += rho * (s[k] + t[k]);
+  Poly<R> P;
+  poly_of<true>(g, P);
+  poly_moments<0, 4, 2>(P, m, rho, out);
 }
 
 template <class R, int NU, int NV>
-GKS_FN void add_point_linear(const R Y1[4], const R Yu[4], const R Yv[4],
-                                                 const Moments<R, NU, NV>& m, R rho, R out[4]) {
-  R s[4], t[4];
-  coef_mom<0, 0>(Y1, m, s);
-  coef_mom<1, 0>(Yu, m, t);
+GKS_FN void add_point_linear(const R Y1[4], const R Yu[4], const R Yv[4], const Moments<R, NU, NV>& m, R rho,
+                             R out[4]) {
+  Groups<R> g;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) s[k] += t[k];
-  coef_mom<0, 1>(Yv, m, t);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) out[k] += rho * (s[k] + t[k]);
+  for (int k = 0; k < 4; ++k) {
+    g.X1[k] = Y1[k];
+    g.Xu[k] = Yu[k];
+    g.Xv[k] = Yv[k];
+  }
+  Poly<R> P;
+  poly_of<false>(g, P);
+  poly_moments<0, 3, 1>(P, m, rho, out);
 }
 
 // Eq. dis1 grouped: weights W = I (flux, mean) or E (point); y2 = dtan^2/12 is both
