@@ -66,7 +66,7 @@ __global__ void k_ghost(Geo g, Cells<R> U0, Cells<R> U1, const Ctrl* c, int forc
 template <class R, class TW>
 __global__ void __launch_bounds__(256) k_recon(Geo g, const R* U0, const R* U1, const TW* Wx0, const TW* Wx1,
                                                const TW* Wy0, const TW* Wy1, R* __restrict__ coef, R dx, R dy,
-                                               R weps, R wC, R gm1, Ctrl* c, int force, int begin, double cfl,
+                                               R weps, R wC, Ctrl* c, int force, int begin, double cfl,
                                                double dt_max, double t_end) {
   pdl_enter();
   if (begin) {
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) k_recon(Geo g, const R* U0, const R* U1, 
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
   const int par = (int)(c->steps & 1);
-  recon_cell<R, TW>(g, par ? U1 : U0, par ? Wx1 : Wx0, par ? Wy1 : Wy0, coef, i, j, dx, dy, weps, wC, gm1);
+  recon_cell<R, TW>(g, par ? U1 : U0, par ? Wx1 : Wx0, par ? Wy1 : Wy0, coef, i, j, dx, dy, weps, wC);
 }
 
 // ---------------------------------------------------------------------------
@@ -337,7 +337,7 @@ cudaError_t launch_recon(gks_handle* h, int force, int begin = 0, double cfl = 0
   const dim3 b2(32, 8);
   return launch(pdl, k_recon<R, TW>, grid2(g.nx, g.ny, b2), b2, h->stream, g, cells<R>(h, 0), cells<R>(h, 1),
          (const TW*)h->Wx[0], (const TW*)h->Wx[1], (const TW*)h->Wy[0], (const TW*)h->Wy[1], (R*)h->coef, R(g.dx),
-         R(g.dy), R(g.weno_eps), R(g.weno_C), R(g.gamma - 1.0), h->ctrl, force, begin, cfl, dt_max, t_end);
+         R(g.dy), R(g.weno_eps), R(g.weno_C), h->ctrl, force, begin, cfl, dt_max, t_end);
 }
 
 // ev (optional, kLaunchesPerStep + 1 events): recorded before each kernel and after the last.
@@ -894,7 +894,7 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
   k_ghost<double><<<(per + 127) / 128, 128, 0, s>>>(g, C0, C1, ctrl, 1);
   k_dtbound<double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, C0, C1, ctrl);
   k_recon<double, double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, dWx, dWx_out, dWy, dWy_out, coef, g.dx, g.dy,
-                                                            g.weno_eps, g.weno_C, g.gamma - 1.0, ctrl, 0, 1, CFL,
+                                                            g.weno_eps, g.weno_C, ctrl, 0, 1, CFL,
                                                             dt_max, INFINITY);
   k_flux<0, double, double><<<grid2(nx + 1, ny, bf), bf, 0, s>>>(g, fconst<double>(g, 0), U0, U1, coef,
                                                                   const_cast<double*>(dWx), dWx_out, Fx, ctrl, 0);

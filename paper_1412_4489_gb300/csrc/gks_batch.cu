@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<
       const GridOff& o = a.off[w.x];
       const R* U = (const R*)(a.U[par] + o.u);
       recon_cell<R, TW>(g, U, a.Wx[par] + o.wx, a.Wy[par] + o.wy, a.coef + o.coef, i, j, GeoR<R>::dx(g),
-                        GeoR<R>::dy(g), GeoR<R>::weps(g), GeoR<R>::wC(g), GeoR<R>::gm1(g));
+                        GeoR<R>::dy(g), GeoR<R>::weps(g), GeoR<R>::wC(g));
     }
     if (!grid_barrier(a.bar)) return;
 

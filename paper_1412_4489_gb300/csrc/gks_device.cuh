@@ -727,23 +727,50 @@ GKS_FN R minmod(R a, R b) {
   return a * b > R(0) ? (fabs(a) < fabs(b) ? a : b) : R(0);
 }
 
+// Cell-size constants of the reconstruction, formed once per cell (not per variable)
 template <class R>
-GKS_FN void recon_var(R c, R e, R w, R n, R s, R em, R ep, R wm, R wp, R nm, R np, R sm,
-                                          R sp, R dx, R dy, R weps, R wC, R a[5]) {
-  const R idx = d_div(R(1), dx), idy = d_div(R(1), dy);
-  const R idx2 = idx * idx, idy2 = idy * idy;
+struct ReconK {
+  R dx, dy, idx, idy, idx2, idy2, dx6, dy6, r3, dx2, dy2, dx2_12, dy2_12, dx4, dy4, dxy2, weps, I1;
+};
+
+template <class R>
+GKS_FN ReconK<R> recon_k(R dx, R dy, R weps, R wC) {
+  ReconK<R> k;
+  k.dx = dx;
+  k.dy = dy;
+  k.idx = d_div(R(1), dx);
+  k.idy = d_div(R(1), dy);
+  k.idx2 = k.idx * k.idx;
+  k.idy2 = k.idy * k.idy;
+  k.dx6 = dx * R(1.0 / 6.0);
+  k.dy6 = dy * R(1.0 / 6.0);
+  k.r3 = R(1.7320508075688772) * k.idx * k.idy;  // sqrt(3) / (dx dy)
+  k.dx2 = dx * dx;
+  k.dy2 = dy * dy;
+  k.dx2_12 = k.dx2 * R(1.0 / 12.0);
+  k.dy2_12 = k.dy2 * R(1.0 / 12.0);
+  k.dx4 = k.dx2 * k.dx2;
+  k.dy4 = k.dy2 * k.dy2;
+  k.dxy2 = k.dx2 * k.dy2;
+  k.weps = weps;
+  k.I1 = wC * dx * dy;  // I(U1) = C dx dy
+  return k;
+}
+
+template <class R>
+GKS_FN void recon_var(R c, R e, R w, R n, R s, R em, R ep, R wm, R wp, R nm, R np, R sm, R sp,
+                      const ReconK<R>& K, R a[5]) {
   // one-sided stencils: face Gauss mean S and neighbour average (Eq. over-sys)
   const R Se = R(0.5) * (em + ep), Sw = R(0.5) * (wm + wp);
   const R Sn = R(0.5) * (nm + np), Ss = R(0.5) * (sm + sp);
-  const R a4 = minmod(R(3) * (c + w - R(2) * Sw) * idx2, R(3) * (c + e - R(2) * Se) * idx2);
-  const R a2 = minmod(-R(2) * (Sw - c) * idx + a4 * dx * R(1.0 / 6.0), R(2) * (Se - c) * idx - a4 * dx * R(1.0 / 6.0));
-  const R a5 = minmod(R(3) * (c + s - R(2) * Ss) * idy2, R(3) * (c + n - R(2) * Sn) * idy2);
-  const R a3 = minmod(-R(2) * (Ss - c) * idy + a5 * dy * R(1.0 / 6.0), R(2) * (Sn - c) * idy - a5 * dy * R(1.0 / 6.0));
+  const R a4 = minmod(R(3) * (c + w - R(2) * Sw) * K.idx2, R(3) * (c + e - R(2) * Se) * K.idx2);
+  const R a2 = minmod(-R(2) * (Sw - c) * K.idx + a4 * K.dx6, R(2) * (Se - c) * K.idx - a4 * K.dx6);
+  const R a5 = minmod(R(3) * (c + s - R(2) * Ss) * K.idy2, R(3) * (c + n - R(2) * Sn) * K.idy2);
+  const R a3 = minmod(-R(2) * (Ss - c) * K.idy + a5 * K.dy6, R(2) * (Sn - c) * K.idy - a5 * K.dy6);
   // cross derivative of the four one-sided stencils with limited a2, a3:
   // sx (sqrt3 Dx/(dx dy) - a3/dx) + sy (sqrt3 Dy/(dx dy) - a2/dy), smallest magnitude
-  const R r3 = R(1.7320508075688772) * idx * idy;
-  const R xe = r3 * (ep - em) - a3 * idx, xw = r3 * (wp - wm) - a3 * idx;
-  const R yn = r3 * (np - nm) - a2 * idy, ys = r3 * (sp - sm) - a2 * idy;
+  const R xe = K.r3 * (ep - em) - a3 * K.idx, xw = K.r3 * (wp - wm) - a3 * K.idx;
+  const R yn = K.r3 * (np - nm) - a2 * K.idy, ys = K.r3 * (sp - sm) - a2 * K.idy;
   // magnitudes within a relative Prec<R>::tie of the current choice are ties
   // (piecewise constant data give exact ties of opposite sign); the earlier
   // stencil is kept
@@ -756,16 +783,14 @@ GKS_FN void recon_var(R c, R e, R w, R n, R s, R em, R ep, R wm, R wp, R nm, R n
   cand = xe - ys;        // (+, -)
   if (fabs(cand) < fabs(a6) * keep) a6 = cand;
   // central stencil
-  const R c2 = R(0.5) * (e - w) * idx, c4 = (e - R(2) * c + w) * idx2;
-  const R c3 = R(0.5) * (n - s) * idy, c5 = (n - R(2) * c + s) * idy2;
-  const R c6 = R(0.5) * r3 * ((ep - em) - (wp - wm) + (np - nm) - (sp - sm));
+  const R c2 = R(0.5) * (e - w) * K.idx, c4 = (e - R(2) * c + w) * K.idx2;
+  const R c3 = R(0.5) * (n - s) * K.idy, c5 = (n - R(2) * c + s) * K.idy2;
+  const R c6 = R(0.5) * K.r3 * ((ep - em) - (wp - wm) + (np - nm) - (sp - sm));
   // Eq. average: alpha = 1/(eps + I)^2, I(U1) = C dx dy
-  const R dx2 = dx * dx, dy2 = dy * dy;
-  const R I2 = dx2 * (c2 * c2 + (c4 * c4 * dx2 + c6 * c6 * dy2) * R(1.0 / 12.0)) +
-               dy2 * (c3 * c3 + (c5 * c5 * dy2 + c6 * c6 * dx2) * R(1.0 / 12.0)) + dx2 * dx2 * c4 * c4 +
-               dx2 * dy2 * c6 * c6 + dy2 * dy2 * c5 * c5;
-  const R I1 = wC * dx * dy;
-  const R b1 = weps + I1, b2 = weps + I2;
+  const R I2 = K.dx2 * (c2 * c2 + c4 * c4 * K.dx2_12 + c6 * c6 * K.dy2_12) +
+               K.dy2 * (c3 * c3 + c5 * c5 * K.dy2_12 + c6 * c6 * K.dx2_12) + K.dx4 * c4 * c4 +
+               K.dxy2 * c6 * c6 + K.dy4 * c5 * c5;
+  const R b1 = K.weps + K.I1, b2 = K.weps + I2;
   // w1 = (1/b1^2) / (1/b1^2 + 1/b2^2) = b2^2 / (b1^2 + b2^2)
   const R w1 = d_div(b2 * b2, b1 * b1 + b2 * b2), w2 = R(1) - w1;
   a[0] = w1 * a2 + w2 * c2;

@@ -309,37 +309,35 @@ __device__ __forceinline__ void ghost_at(const Geo& g, Cells<R> U, int p) {
 template <class R, class TW>
 __device__ __forceinline__ void recon_cell(const Geo& g, const R* __restrict__ U, const TW* __restrict__ Wx,
                                            const TW* __restrict__ Wy, R* __restrict__ coef, int i, int j, R dx,
-                                           R dy, R weps, R wC, R gm1) {
+                                           R dy, R weps, R wC) {
   const int nx = g.nx, ny = g.ny;
   const size_t fxp = (size_t)ny * (nx + 1), fyp = (size_t)(ny + 1) * nx;
+  const ReconK<R> K = recon_k(dx, dy, weps, wC);
   R a[4][5];
-  R cbar[4];
+  // the polynomial at the four face centres (x = +-dx/2, y = 0 and x = 0, y = +-dy/2):
+  // value = e0 +- a2 dx/2 on x-faces, n0 +- a3 dy/2 on y-faces
+  R ve[4], vw[4], vn[4], vs[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     const R cc = U[ci(g, v, i, j)];
-    cbar[v] = cc;
     const TW* wx = Wx + (size_t)v * 2 * fxp + (size_t)j * (nx + 1);
     const TW* wy = Wy + (size_t)v * 2 * fyp;
     recon_var<R>(cc, U[ci(g, v, i + 1, j)], U[ci(g, v, i - 1, j)], U[ci(g, v, i, j + 1)], U[ci(g, v, i, j - 1)],
                  R(wx[i + 1]), R(wx[fxp + i + 1]), R(wx[i]), R(wx[fxp + i]), R(wy[(size_t)(j + 1) * nx + i]),
                  R(wy[fyp + (size_t)(j + 1) * nx + i]), R(wy[(size_t)j * nx + i]), R(wy[fyp + (size_t)j * nx + i]),
-                 dx, dy, weps, wC, a[v]);
+                 K, a[v]);
+    // U(x, y) = c + a2 x + a3 y + a4 (x^2 - dx^2/12)/2 + a5 (y^2 - dy^2/12)/2 + a6 x y
+    const R e0 = cc + a[v][2] * K.dx2_12 - a[v][3] * R(0.5) * K.dy2_12;
+    const R n0 = cc + a[v][3] * K.dy2_12 - a[v][2] * R(0.5) * K.dx2_12;
+    ve[v] = e0 + a[v][0] * (R(0.5) * dx);
+    vw[v] = e0 - a[v][0] * (R(0.5) * dx);
+    vn[v] = n0 + a[v][1] * (R(0.5) * dy);
+    vs[v] = n0 - a[v][1] * (R(0.5) * dy);
   }
-  // positivity: rho and p at the four face centres, else the constant average
-  bool bad = false;
-#pragma unroll
-  for (int f = 0; f < 4; ++f) {
-    R w[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const R x = f == 0 ? R(0.5) * dx : (f == 1 ? -R(0.5) * dx : R(0));
-      const R y = f == 2 ? R(0.5) * dy : (f == 3 ? -R(0.5) * dy : R(0));
-      w[v] = cbar[v] + a[v][0] * x + a[v][1] * y + a[v][2] * R(0.5) * (x * x - dx * dx * R(1.0 / 12.0)) +
-             a[v][3] * R(0.5) * (y * y - dy * dy * R(1.0 / 12.0)) + a[v][4] * x * y;
-    }
-    const R p = gm1 * (w[3] - d_div(R(0.5) * (w[1] * w[1] + w[2] * w[2]), w[0]));
-    if (!(w[0] > R(0)) || !(p > R(0))) bad = true;
-  }
+  // positivity: rho > 0 and p > 0 (2 rho rho E > |rho u|^2) at the four face centres,
+  // else the constant average
+  auto ok = [](const R w[4]) { return w[0] > R(0) && R(2) * w[0] * w[3] > w[1] * w[1] + w[2] * w[2]; };
+  const bool bad = !(ok(ve) && ok(vw) && ok(vn) && ok(vs));
   const size_t N = (size_t)nx * ny, o = (size_t)j * nx + i;
 #pragma unroll
   for (int k = 0; k < 5; ++k)
