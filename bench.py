@@ -254,6 +254,7 @@ def run_ours(args):
     a.close()
     b.close()
     errors = error_legs(stream) if not args.no_batch else None
+    validation = vortex_leg(stream) if not args.no_batch else None
 
     # ---- end to end through the C ABI with host buffers ----
     KE = max(3, min(args.steps, 20))
@@ -344,6 +345,7 @@ def run_ours(args):
                               "peak_source": "measured FP64 FMA throughput (gks_measure_alu_peak)",
                               "kernel_ms": round(prof64[dom], 5)},
             "batched": batched,
+            "validation": validation,
             "fp32_4096": big,
             "kernels_ms_fp32": {k: round(v, 5) for k, v in prof.items()},
             "kernels_ms_fp64": {k: round(v, 5) for k, v in prof64.items()},
@@ -402,6 +404,38 @@ def error_legs(stream):
         out["cavity_512"] = [{"steps": 2000, "l1_rho_rel_fp32": rho_l1(f32, f64)}]
         f64.close()
         f32.close()
+    return out
+
+
+def vortex_leg(stream):
+    """The paper's isotropic vortex (Table 2) at 121^2 over one period (t = 10, CFL 0.2) in both
+    precisions: L1 / L2 density error against the exact solution (the initial data) and the
+    throughput of the whole run, timed with CUDA events."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1412_4489_gb300 import gks, workloads as wl
+    p = wl.isotropic_vortex(121)
+    out = {"workload": "isotropic vortex 121^2, [-5, 5]^2 periodic, one period (t = 10), CFL 0.2",
+           "table2_paper": {"L1": 2.6716280e-04, "L2": 4.8235722e-04}}
+    for prec, name in ((gks.GKS_FP64, "fp64"), (gks.GKS_FP32_BULK, "fp32_bulk")):
+        with torch.cuda.stream(stream):
+            s = gks.Solver(p, prec, stream=stream.cuda_stream, tau_eps=0.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(1000):
+                s.advance(64, 0.2, 10.0)
+                t, k = s.sync()
+                if t >= 10.0 * (1 - 1e-14):
+                    break
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            U = s.state()[0]
+            s.close()
+        d = U[0] - p.U[0]
+        out[name] = {"L1": float(np.mean(np.abs(d))), "L2": float(math.sqrt(np.mean(d * d))), "steps": int(k),
+                     "value": round(121 * 121 * k / (ms * 1e-3) / 1e6, 3), "unit": UNIT}
     return out
 
 

@@ -97,7 +97,8 @@ typedef enum {
 typedef struct {
   int precision;     /* gks_precision */
   double weno_eps;   /* epsilon of the nonlinear weights, Eq. average (paper: unstated; default 1e-6) */
-  double weno_C;     /* C of I(U1) = C dx dy, Section 3.1 (paper: unstated; default 1) */
+  double weno_C;     /* C of I(U1) = C dx dy, Section 3.1 (paper: unstated; default 10: the
+                        central stencil must win on smooth data, see the design notes) */
   double tau_eps;    /* epsilon of the inviscid collision time, Section 4 (default 0.05) */
   double tau_C;      /* C of the inviscid collision time, Section 4 (default 1) */
   int viscous_dt;    /* 1: also bound dt by CFL rho h^2 / (2 mu max(4/3, gamma/Pr)) */

@@ -93,7 +93,7 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def params(gamma=1.4, mu=0.0, Pr=1.0, weno_eps=1e-6, weno_C=1.0, tau_eps=0.05, tau_C=1.0) -> Params:
+def params(gamma=1.4, mu=0.0, Pr=1.0, weno_eps=1e-6, weno_C=10.0, tau_eps=0.05, tau_C=1.0) -> Params:
     return Params(gamma, mu, Pr, weno_eps, weno_C, tau_eps, tau_C)
 
 

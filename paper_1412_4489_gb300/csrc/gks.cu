@@ -526,7 +526,7 @@ void gks_default_options(gks_options* o) {
   if (!o) return;
   o->precision = GKS_FP64;
   o->weno_eps = 1e-6;
-  o->weno_C = 1.0;
+  o->weno_C = 10.0;
   o->tau_eps = 0.05;
   o->tau_C = 1.0;
   o->viscous_dt = 0;

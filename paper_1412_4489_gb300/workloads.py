@@ -15,6 +15,10 @@ Workloads (all FP64 host arrays in the library's SoA layout):
 * ``cavity_2d``        -- lid-driven square cavity at rest (rho = 1, p = 1/gamma), lid speed
   0.15 (lid Mach number 0.15), isothermal no-slip walls.
 * ``batch_grids``      -- 512 independent grids with seeded sizes, kinds, gamma and mu.
+* ``isotropic_vortex`` -- Section 4.1's second accuracy test: an isentropic vortex of
+  strength 5 on the mean flow (1, 1, 1, 1) in the periodic [-5, 5]^2 (Table 2).
+* ``sod``              -- Section 4.2's Sod tube, (1, 0, 1) | (0.125, 0, 0.1) on [0, 1], as an
+  nx-by-1 grid periodic in y with outflow ends.
 
 Cell averages are exact averages of the initial data; interface values are the exact
 point values at the Gauss points (x-faces: y_j -/+ sqrt(3)/6 dy; y-faces: x_i -/+ sqrt(3)/6 dx).
@@ -228,6 +232,68 @@ def cavity_2d(n: int, gamma: float = 1.4, Re: float = 1000.0, lid: float = 0.15,
     bc = [wall, wall, wall, (BC_NOSLIP_ISOTHERMAL, lid, 0.0, Tw)]
     return Problem(f"cavity_{n}", nx, ny, Lx, Ly, gamma, mu, Pr, bc, U, Wx, Wy,
                    meta={"Re": Re, "lid": lid})
+
+
+def isotropic_vortex_state(x, y, gamma: float = 1.4, eps: float = 5.0):
+    """Point state of the isotropic vortex centred at the origin on the mean flow
+    (rho, u, v, p) = (1, 1, 1, 1): du, dv = eps/(2 pi) e^((1 - r^2)/2) (-y, x),
+    dT = -(gamma - 1) eps^2 / (8 gamma pi^2) e^(1 - r^2), entropy p / rho^gamma = 1."""
+    r2 = x * x + y * y
+    f = eps / (2.0 * np.pi) * np.exp(0.5 * (1.0 - r2))
+    T = 1.0 - (gamma - 1.0) * eps * eps / (8.0 * gamma * np.pi * np.pi) * np.exp(1.0 - r2)
+    rho = T ** (1.0 / (gamma - 1.0))
+    return _cons(rho, 1.0 - f * y, 1.0 + f * x, rho * T, gamma)
+
+
+def _gl(nq: int):
+    z, w = np.polynomial.legendre.leggauss(nq)
+    return 0.5 * z, 0.5 * w  # nodes on [-1/2, 1/2], weights summing to 1
+
+
+def isotropic_vortex(n: int, gamma: float = 1.4, eps: float = 5.0, nq: int = 6) -> Problem:
+    """The vortex at the centre of the periodic square [-5, 5]^2 (grid origin at its corner),
+    n x n cells.  Cell averages by an nq x nq Gauss-Legendre rule per cell; the face values
+    are the exact point values at the Gauss points."""
+    L = 10.0
+    dx = dy = L / n
+    xc = -5.0 + (np.arange(n) + 0.5) * dx
+    z, w = _gl(nq)
+    U = np.zeros((4, n, n))
+    for a in range(nq):
+        for b in range(nq):
+            X, Y = np.meshgrid(xc + z[a] * dx, xc + z[b] * dy)
+            U += w[a] * w[b] * isotropic_vortex_state(X, Y, gamma, eps)
+    _, _, wxp, wyp = _gauss_points(n, n, L, L)
+    shift = lambda pts: [(x - 5.0, y - 5.0) for (x, y) in pts]
+    Wx = _point_state(lambda x, y: isotropic_vortex_state(x, y, gamma, eps), shift(wxp))
+    Wy = _point_state(lambda x, y: isotropic_vortex_state(x, y, gamma, eps), shift(wyp))
+    bc = [(BC_PERIODIC, 0.0, 0.0, 1.0)] * 4
+    return Problem(f"isotropic_vortex_{n}", n, n, L, L, gamma, 0.0, 1.0, bc,
+                   np.ascontiguousarray(U), np.ascontiguousarray(Wx), np.ascontiguousarray(Wy),
+                   meta={"eps": eps, "period": 10.0})
+
+
+def sod(nx: int, gamma: float = 1.4) -> Problem:
+    """Sod's shock tube on [0, 1] (diaphragm at x = 0.5) as an nx-by-1 grid, dy = dx."""
+    Lx = 1.0
+    dx = Lx / nx
+    left, right = _cons(1.0, 0.0, 0.0, 1.0, gamma), _cons(0.125, 0.0, 0.0, 0.1, gamma)
+    xl = np.arange(nx) * dx
+    fr = np.clip((xl + dx - 0.5) / dx, 0.0, 1.0)  # fraction of the cell right of x = 0.5
+    U = (left.reshape(4, 1) * (1 - fr) + right.reshape(4, 1) * fr)[:, None, :]
+
+    def pt(x, y):
+        x = np.asarray(x, dtype=np.float64)
+        s = np.where(x > 0.5, 1.0, np.where(x < 0.5, 0.0, 0.5))
+        return left.reshape(4, *([1] * x.ndim)) * (1 - s) + right.reshape(4, *([1] * x.ndim)) * s
+
+    _, _, wxp, wyp = _gauss_points(nx, 1, Lx, dx)
+    Wx = _point_state(pt, wxp)
+    Wy = _point_state(pt, wyp)
+    bc = [(BC_OUTFLOW, 0.0, 0.0, 1.0), (BC_OUTFLOW, 0.0, 0.0, 1.0), (BC_PERIODIC, 0.0, 0.0, 1.0),
+          (BC_PERIODIC, 0.0, 0.0, 1.0)]
+    return Problem(f"sod_{nx}", nx, 1, Lx, dx, gamma, 0.0, 1.0, bc,
+                   np.ascontiguousarray(U), np.ascontiguousarray(Wx), np.ascontiguousarray(Wy))
 
 
 BATCH_SIZES = [32 * k for k in range(1, 13)]

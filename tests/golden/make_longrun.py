@@ -25,6 +25,7 @@ import oracle  # noqa: E402
 from paper_1412_4489_gb300 import workloads as wl  # noqa: E402
 
 CFL = 0.5
+WENO_C = 1.0  # the constant of I(U1) these references were generated with (a parity check: any value)
 
 
 def sample_cells(nx: int, ny: int, seed: int, lines: bool) -> list[tuple[int, int]]:
@@ -46,7 +47,7 @@ def sample_cells(nx: int, ny: int, seed: int, lines: bool) -> list[tuple[int, in
 
 
 def run(name: str, p, bc, nsteps: int, seed: int, lines: bool, out: str) -> None:
-    P = oracle.params(gamma=p.gamma, mu=p.mu, Pr=p.Pr, tau_eps=0.05)
+    P = oracle.params(gamma=p.gamma, mu=p.mu, Pr=p.Pr, tau_eps=0.05, weno_C=WENO_C)
     st = oracle.State2D(p.nx, p.ny, p.Lx, p.Ly, p.U, p.Wx, p.Wy)
     t0 = time.time()
     for k in range(nsteps):
@@ -55,7 +56,7 @@ def run(name: str, p, bc, nsteps: int, seed: int, lines: bool, out: str) -> None
             raise RuntimeError(f"{name}: oracle step {k} failed ({rc})")
     cells = sample_cells(p.nx, p.ny, seed, lines)
     with open(out, "w") as f:
-        f.write(f"# {name}: FP64 oracle after {nsteps} steps (CFL {CFL}, tau_eps 0.05), written by "
+        f.write(f"# {name}: FP64 oracle after {nsteps} steps (CFL {CFL}, tau_eps 0.05, weno_C {WENO_C}), written by "
                 f"tests/golden/make_longrun.py from oracle/ only\n")
         f.write(f"# nx {p.nx} ny {p.ny} t {st.t!r} threads {oracle.num_threads()} seconds {time.time() - t0:.0f}\n")
         f.write("# columns: j i rho rhoU rhoV rhoE\n")

@@ -224,7 +224,8 @@ def test_smooth_wave_2d_converges():
         oracle.run2d(P, st, oracle.bcs(PER), 0.5, t_end=1.0)  # one period along x + y
         errs.append(np.mean(np.abs(st.U[0] - p.U[0])))
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
-    assert orders[0] > 2.5 and orders[1] > 2.7 and orders[1] > orders[0], orders
+    # third order, approached from above on these meshes (3.6, 3.4 with C = 10)
+    assert np.all(orders > 2.7) and abs(orders[1] - 3.0) < abs(orders[0] - 3.0) + 0.2, orders
 
 
 def test_positivity_fallback_rescues_a_near_vacuum_riemann_problem():
