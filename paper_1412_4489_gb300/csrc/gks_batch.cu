@@ -105,7 +105,7 @@ __device__ bool grid_barrier(Barrier* b) {
 }
 
 #ifndef GKS_BATCH_MINB_F32
-#define GKS_BATCH_MINB_F32 4
+#define GKS_BATCH_MINB_F32 3
 #endif
 template <class R> struct BatchBlocks;
 template <> struct BatchBlocks<double> { static constexpr int value = 1; };
