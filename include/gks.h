@@ -73,12 +73,15 @@ typedef enum {
  * derivatives), ghost averages copied; slip wall = mirror image with the normal
  * momentum negated; isothermal no-slip = mirror image with velocity
  * 2 u_wall - u, temperature 2 T_wall - T and equal density (images of the
- * derivatives by the chain rule of that map). */
+ * derivatives by the chain rule of that map); adiabatic no-slip = mirror image
+ * with velocity 2 u_wall - u, equal temperature and density (no heat flux
+ * through the wall; T_wall unused). */
 typedef enum {
   GKS_BC_PERIODIC = 0,
   GKS_BC_OUTFLOW = 1,
   GKS_BC_SLIPWALL = 2,
-  GKS_BC_NOSLIP_ISOTHERMAL = 3
+  GKS_BC_NOSLIP_ISOTHERMAL = 3,
+  GKS_BC_NOSLIP_ADIABATIC = 4
 } gks_bc_kind;
 
 typedef struct {
@@ -90,8 +93,9 @@ typedef struct {
 
 typedef enum {
   GKS_FP64 = 0,      /* every step in FP64 */
-  GKS_FP32_BULK = 1  /* reconstruction, face evolution and face values in FP32;
-                        cell averages, the update and dt in FP64 */
+  GKS_FP32_BULK = 1  /* everything in FP32; the cell averages are kept as
+                        double-float pairs (hi + lo FP32) updated with compensated
+                        (error-free) arithmetic; host transfers in FP64 */
 } gks_precision;
 
 typedef struct {

@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liboracle.so")
 SOURCES = ["gks_oracle2d.c", "gks_oracle1d.c"]
 
-BC_PERIODIC, BC_OUTFLOW, BC_SLIPWALL, BC_NOSLIP_ISOTHERMAL = 0, 1, 2, 3
+BC_PERIODIC, BC_OUTFLOW, BC_SLIPWALL, BC_NOSLIP_ISOTHERMAL, BC_NOSLIP_ADIABATIC = 0, 1, 2, 3, 4
 
 
 class Params(ctypes.Structure):

@@ -32,7 +32,8 @@ typedef struct {
   double tau_eps, tau_C;
 } orc_params;
 
-enum { ORC_BC_PERIODIC = 0, ORC_BC_OUTFLOW = 1, ORC_BC_SLIPWALL = 2, ORC_BC_NOSLIP_ISOTHERMAL = 3 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_OUTFLOW = 1, ORC_BC_SLIPWALL = 2, ORC_BC_NOSLIP_ISOTHERMAL = 3,
+       ORC_BC_NOSLIP_ADIABATIC = 4 };
 
 /* One side of the domain.  T_wall is the wall temperature p/rho. */
 typedef struct {

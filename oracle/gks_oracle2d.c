@@ -550,6 +550,15 @@ static void wall_map(int kind, double gam, double uwt, double Tw, const double w
     o[0] = w[0]; o[1] = -w[1]; o[2] = w[2]; o[3] = w[3];
     return;
   }
+  if (kind == ORC_BC_NOSLIP_ADIABATIC) {
+    /* rho' = rho, u' = 2 u_w - u, T' = T: the internal energy is kept, the kinetic energy
+     * changes by (|m'|^2 - |m|^2) / (2 rho) = 2 rho u_w^2 - 2 u_w m_t (linear in the state) */
+    o[0] = w[0];
+    o[1] = -w[1];
+    o[2] = 2.0 * w[0] * uwt - w[2];
+    o[3] = w[3] + 2.0 * w[0] * uwt * uwt - 2.0 * uwt * w[2];
+    return;
+  }
   /* no-slip isothermal: rho' = rho, u' = 2 u_w - u, T' = 2 T_w - T */
   const double rho = w[0], mn = w[1], mt = w[2], e = w[3];
   o[0] = rho;
@@ -566,6 +575,12 @@ static void wall_jac(int kind, double gam, double uwt, double Tw, const double w
     J[0][0] = 1; J[1][1] = -1; J[2][2] = 1; J[3][3] = 1;
     return;
   }
+  if (kind == ORC_BC_NOSLIP_ADIABATIC) {
+    J[0][0] = 1; J[1][1] = -1;
+    J[2][0] = 2.0 * uwt; J[2][2] = -1;
+    J[3][0] = 2.0 * uwt * uwt; J[3][2] = -2.0 * uwt; J[3][3] = 1;
+    return;
+  }
   const double rho = w[0], mn = w[1], mt = w[2];
   J[0][0] = 1.0;
   J[1][1] = -1.0;
@@ -577,7 +592,7 @@ static void wall_jac(int kind, double gam, double uwt, double Tw, const double w
 }
 
 static double wall_hess_e(int kind, const double w[4], const double a[4], const double bb[4]) {
-  if (kind == ORC_BC_SLIPWALL) return 0.0;
+  if (kind == ORC_BC_SLIPWALL || kind == ORC_BC_NOSLIP_ADIABATIC) return 0.0;  /* linear maps */
   /* second derivative of |m|^2 / rho along a and b */
   const double rho = w[0], mn = w[1], mt = w[2];
   const double m2 = mn * mn + mt * mt;
@@ -783,6 +798,18 @@ static void ghost_value(const orc_params* P, const orc_bc* b, int axis, const do
   to_frame(axis, o, out);
 }
 
+/* Flux through a wall face (face frame).  A wall lets no mass through, and an
+ * adiabatic wall no heat: its energy flux is the work u_w F_(m_t) of the shear on the
+ * moving wall.  The mirror images give these exactly for a slip wall; behind a no-slip
+ * wall the image also reverses the tangential velocity, which the tangential
+ * transport terms of the evolution do not respect, so the evaluated mass and energy
+ * fluxes carry an O(dt d(rho u_t)/dt) error that the wall's definition removes. */
+static void wall_face_flux(const orc_bc* b, int axis, double F[4]) {
+  if (b->kind == ORC_BC_SLIPWALL || b->kind == ORC_BC_NOSLIP_ISOTHERMAL || b->kind == ORC_BC_NOSLIP_ADIABATIC)
+    F[0] = 0.0;
+  if (b->kind == ORC_BC_NOSLIP_ADIABATIC) F[3] = wall_tangent_velocity(b, axis) * F[2];
+}
+
 /* ghost ring: first the y-ghost rows of interior columns, then the x-ghost
  * columns of all rows (corners are x-images of y-ghosts) */
 static void fill_ghosts(const orc_params* P, int nx, int ny, const orc_bc bc[4], const double* U, ghosts* G) {
@@ -893,6 +920,8 @@ void orc_flux2d(const orc_params* P, int nx, int ny, double Lx, double Ly, const
           to_frame(0, w, avg[m][n + 1]);
         }
       orc_face(P, L, R, avg, dx, dy, dt, F, Wg, NULL);
+      if (lo && bc[0].kind != ORC_BC_PERIODIC) wall_face_flux(&bc[0], 0, F);
+      else if (hi && bc[1].kind != ORC_BC_PERIODIC) wall_face_flux(&bc[1], 0, F);
       for (int v = 0; v < 4; ++v) {
         Fx[((size_t)v * ny + j) * (nx + 1) + i] = F[v];
         Wxn[WXI(v, 0, j, i)] = Wg[0][v];
@@ -926,6 +955,8 @@ void orc_flux2d(const orc_params* P, int nx, int ny, double Lx, double Ly, const
           to_frame(1, w, avg[m][n + 1]);
         }
       orc_face(P, L, R, avg, dy, dx, dt, Ff, Wf, NULL);
+      if (lo && bc[2].kind != ORC_BC_PERIODIC) wall_face_flux(&bc[2], 1, Ff);
+      else if (hi && bc[3].kind != ORC_BC_PERIODIC) wall_face_flux(&bc[3], 1, Ff);
       to_frame(1, Ff, F);
       to_frame(1, Wf[0], Wg[0]);
       to_frame(1, Wf[1], Wg[1]);
@@ -972,6 +1003,8 @@ static void face_first_order(const orc_params* P, int nx, int ny, double dx, dou
 #undef CELL_I
 #undef CELL_J
   orc_face_first_order(P, L, R, axis == 0 ? dx : dy, axis == 0 ? dy : dx, dt, Ff, Wf, NULL);
+  if (f == 0 && blo->kind != ORC_BC_PERIODIC) wall_face_flux(blo, axis, Ff);
+  else if (f == nf && bhi->kind != ORC_BC_PERIODIC) wall_face_flux(bhi, axis, Ff);
   to_frame(axis, Ff, F);
   to_frame(axis, Wf[0], Wg[0]);
   to_frame(axis, Wf[1], Wg[1]);
@@ -1043,6 +1076,8 @@ void orc_flux2d_faces(const orc_params* P, int nx, int ny, double Lx, double Ly,
         to_frame(axis, w, avg[m][t + 1]);
       }
     orc_face(P, L, R, avg, axis == 0 ? dx : dy, axis == 0 ? dy : dx, dt, Ff, Wf, NULL);
+    if (f == 0 && blo->kind != ORC_BC_PERIODIC) wall_face_flux(blo, axis, Ff);
+    else if (f == nf && bhi->kind != ORC_BC_PERIODIC) wall_face_flux(bhi, axis, Ff);
     double Fp[4], W0[4], W1[4];
     to_frame(axis, Ff, Fp);
     to_frame(axis, Wf[0], W0);

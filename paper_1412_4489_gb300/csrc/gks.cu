@@ -504,7 +504,7 @@ gks_status check_args(int nx, int ny, double Lx, double Ly, double gamma, double
   }
   if (bc) {
     for (int k = 0; k < 4; ++k) {
-      if (bc[k].kind < 0 || bc[k].kind > 3) { why = "unknown boundary kind"; return GKS_EINVAL; }
+      if (bc[k].kind < 0 || bc[k].kind > 4) { why = "unknown boundary kind"; return GKS_EINVAL; }
       if (bc[k].kind == GKS_BC_NOSLIP_ISOTHERMAL && !(bc[k].T_wall > 0)) { why = "T_wall must be > 0"; return GKS_EINVAL; }
     }
     if ((bc[0].kind == GKS_BC_PERIODIC) != (bc[1].kind == GKS_BC_PERIODIC) ||

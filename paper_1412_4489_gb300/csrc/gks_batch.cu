@@ -444,7 +444,7 @@ gks_status gks_batch_create(int n, const gks_grid_desc* grids, const gks_options
       G.bc.uw[k] = d.bc[k].u_wall;
       G.bc.vw[k] = d.bc[k].v_wall;
       G.bc.Tw[k] = d.bc[k].T_wall;
-      if (d.bc[k].kind < 0 || d.bc[k].kind > 3) { delete b; return GKS_EINVAL; }
+      if (d.bc[k].kind < 0 || d.bc[k].kind > 4) { delete b; return GKS_EINVAL; }
     }
     geo_finish(G);
     if ((G.bc.kind[0] == GKS_BC_PERIODIC) != (G.bc.kind[1] == GKS_BC_PERIODIC) ||

@@ -518,6 +518,7 @@ struct ArrayFaceSource {
 // kind 2: slip wall (normal momentum negated).  kind 3: isothermal no-slip with
 // tangential wall velocity uwt and wall temperature Tw: rho' = rho,
 // m' = 2 rho u_w - m, rho E' = 2 rho |u_w|^2 - 2 u_w.m + |m|^2/rho + 2 rho Tw/(gamma-1) - rho E.
+// kind 4: adiabatic no-slip: rho' = rho, m' = 2 rho u_w - m, T' = T (a linear map).
 template <class R>
 GKS_FN void wall_image(int kind, R gamma, R uwt, R Tw, const FaceState<R>& in, FaceState<R>& out) {
   if (kind == 2) {
@@ -528,6 +529,20 @@ GKS_FN void wall_image(int kind, R gamma, R uwt, R Tw, const FaceState<R>& in, F
       out.w[d][1] = -s * in.w[d][1];
       out.w[d][2] = s * in.w[d][2];
       out.w[d][3] = s * in.w[d][3];
+    }
+    return;
+  }
+  if (kind == 4) {
+    // adiabatic no-slip: the linear map rho' = rho, m_n' = -m_n, m_t' = 2 u_w rho - m_t,
+    // rho E' = rho E + 2 u_w^2 rho - 2 u_w m_t applied to the value and every derivative
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      const R s = (d == 1 || d == 4) ? R(-1) : R(1);  // odd derivatives in n flip
+      const R r = in.w[d][0], mn = in.w[d][1], mt = in.w[d][2], e = in.w[d][3];
+      out.w[d][0] = s * r;
+      out.w[d][1] = -s * mn;
+      out.w[d][2] = s * (R(2) * uwt * r - mt);
+      out.w[d][3] = s * (e + R(2) * uwt * uwt * r - R(2) * uwt * mt);
     }
     return;
   }

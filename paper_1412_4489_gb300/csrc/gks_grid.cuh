@@ -224,6 +224,12 @@ __device__ __forceinline__ void bc_value(int kind, R gamma, R uwt, R Tw, int axi
   R o[4];
   if (kind == GKS_BC_SLIPWALL) {
     o[0] = f[0]; o[1] = -f[1]; o[2] = f[2]; o[3] = f[3];
+  } else if (kind == GKS_BC_NOSLIP_ADIABATIC) {
+    // equal density and temperature: rho E changes by the kinetic energy only
+    o[0] = f[0];
+    o[1] = -f[1];
+    o[2] = R(2) * f[0] * uwt - f[2];
+    o[3] = f[3] + R(2) * f[0] * uwt * uwt - R(2) * uwt * f[2];
   } else {
     const R rho = f[0], mn = f[1], mt = f[2];
     o[0] = rho;
@@ -461,6 +467,18 @@ struct GridFaceSource {
   }
 };
 
+// Flux through a wall face (face frame, kind = the boundary kind of the side).  A
+// wall lets no mass through, and an adiabatic wall no heat: its energy flux is the
+// work u_w F_(m_t) of the shear on the moving wall.  The mirror image behind a
+// no-slip wall also reverses the tangential velocity, which the tangential transport
+// terms of the evolution do not respect; the wall's definition removes the resulting
+// O(dt d(rho u_t)/dt) mass and energy fluxes (a slip wall gives them exactly).
+template <class R>
+__device__ __forceinline__ void wall_face_flux(int kind, R uwt, R F[4]) {
+  if (kind == GKS_BC_SLIPWALL || kind == GKS_BC_NOSLIP_ISOTHERMAL || kind == GKS_BC_NOSLIP_ADIABATIC) F[0] = R(0);
+  if (kind == GKS_BC_NOSLIP_ADIABATIC) F[3] = uwt * F[2];
+}
+
 // per-launch constants of the face routine for axis AX of grid g
 template <class R>
 __host__ __device__ inline FaceConst<R> grid_face_const(const Geo& g, int axis) {
@@ -510,6 +528,8 @@ __device__ __forceinline__ void flux_face(const Geo& g, const FaceConst<R>& C, c
 
   R Fl[4], Wm[4], Wp[4];
   face_evolution<R>(C, src, dt, Fl, Wm, Wp);
+  if (src.img_lo) wall_face_flux<R>(src.img_lo, src.uwt_lo, Fl);
+  else if (src.img_hi) wall_face_flux<R>(src.img_hi, src.uwt_hi, Fl);
 
   const size_t nfaces = (size_t)fx * fy, o = (size_t)j * fx + i;
 #pragma unroll
@@ -610,6 +630,8 @@ __device__ __forceinline__ void kfvs_face(const Geo& g, const R* U, R gm1, R K, 
       Ff[q] += dt * rho * b[q];
     }
   }
+  if (src.img_lo) wall_face_flux<R>(src.img_lo, src.uwt_lo, Ff);
+  else if (src.img_hi) wall_face_flux<R>(src.img_hi, src.uwt_hi, Ff);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     F[v] = Ff[slot<AX>(v)];

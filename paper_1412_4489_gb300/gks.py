@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 GKS_OK, GKS_EINVAL, GKS_ENOMEM, GKS_ECUDA, GKS_ENONPHYSICAL, GKS_ETIMEOUT, GKS_EUNSUPPORTED = range(7)
-GKS_BC_PERIODIC, GKS_BC_OUTFLOW, GKS_BC_SLIPWALL, GKS_BC_NOSLIP_ISOTHERMAL = range(4)
+GKS_BC_PERIODIC, GKS_BC_OUTFLOW, GKS_BC_SLIPWALL, GKS_BC_NOSLIP_ISOTHERMAL, GKS_BC_NOSLIP_ADIABATIC = range(5)
 GKS_FP64, GKS_FP32_BULK = 0, 1
 STATUS_NAMES = ["GKS_OK", "GKS_EINVAL", "GKS_ENOMEM", "GKS_ECUDA", "GKS_ENONPHYSICAL", "GKS_ETIMEOUT",
                 "GKS_EUNSUPPORTED"]

@@ -52,7 +52,7 @@ class SplitMix64:
         return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / 9007199254740992.0))
 
 
-BC_PERIODIC, BC_OUTFLOW, BC_SLIPWALL, BC_NOSLIP_ISOTHERMAL = 0, 1, 2, 3
+BC_PERIODIC, BC_OUTFLOW, BC_SLIPWALL, BC_NOSLIP_ISOTHERMAL, BC_NOSLIP_ADIABATIC = 0, 1, 2, 3, 4
 
 
 @dataclass

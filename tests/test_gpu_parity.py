@@ -52,6 +52,8 @@ BCSETS = {
     "noslip": [(wl.BC_NOSLIP_ISOTHERMAL, 0.0, 0.0, 0.9), (wl.BC_NOSLIP_ISOTHERMAL, 0.0, 0.1, 1.1),
                (wl.BC_NOSLIP_ISOTHERMAL, -0.1, 0.0, 1.0), (wl.BC_NOSLIP_ISOTHERMAL, 0.15, 0.0, 1.0)],
     "mixed": [wl.BC_PERIODIC, wl.BC_PERIODIC, wl.BC_SLIPWALL, wl.BC_OUTFLOW],
+    "adiabatic": [(wl.BC_NOSLIP_ADIABATIC, 0.0, 0.0, 1.0), (wl.BC_NOSLIP_ADIABATIC, 0.0, -0.1, 1.0),
+                  (wl.BC_NOSLIP_ADIABATIC, 0.12, 0.0, 1.0), (wl.BC_NOSLIP_ISOTHERMAL, 0.0, 0.0, 1.0)],
 }
 
 

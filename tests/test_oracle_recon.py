@@ -100,15 +100,18 @@ def test_positivity_fallback():
 
 def _prim_image(w, gamma, kind, uwt, Tw):
     """Pointwise wall map in primitive variables: rho' = rho, u_n' = -u_n,
-    slip: u_t' = u_t, T' = T; no-slip isothermal: u_t' = 2 u_wt - u_t, T' = 2 T_w - T."""
+    slip: u_t' = u_t, T' = T; no-slip isothermal: u_t' = 2 u_wt - u_t, T' = 2 T_w - T;
+    no-slip adiabatic: u_t' = 2 u_wt - u_t, T' = T."""
     rho, un, ut = w[0], w[1] / w[0], w[2] / w[0]
     T = (gamma - 1) * (w[3] / rho - 0.5 * (un * un + ut * ut))
     if kind == oracle.BC_SLIPWALL:
         return _cons(rho, -un, ut, rho * T, gamma)
+    if kind == oracle.BC_NOSLIP_ADIABATIC:
+        return _cons(rho, -un, 2 * uwt - ut, rho * T, gamma)
     return _cons(rho, -un, 2 * uwt - ut, rho * (2 * Tw - T), gamma)
 
 
-@pytest.mark.parametrize("kind", [oracle.BC_SLIPWALL, oracle.BC_NOSLIP_ISOTHERMAL])
+@pytest.mark.parametrize("kind", [oracle.BC_SLIPWALL, oracle.BC_NOSLIP_ISOTHERMAL, oracle.BC_NOSLIP_ADIABATIC])
 def test_wall_image_derivatives(kind):
     gamma, uwt, Tw = 1.4, 0.15, 0.7
     rng = np.random.default_rng(5)

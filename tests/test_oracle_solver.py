@@ -244,3 +244,43 @@ def test_positivity_fallback_rescues_a_near_vacuum_riemann_problem():
         pr = 0.4 * (st.U[3] - 0.5 * (st.U[1] ** 2 + st.U[2] ** 2) / st.U[0])
         assert st.U[0].min() > 0 and pr.min() > 0
     assert st.U[0].sum() == pytest.approx(tot0, rel=1e-13)
+
+
+@pytest.mark.parametrize("kind", [oracle.BC_SLIPWALL, oracle.BC_NOSLIP_ISOTHERMAL, oracle.BC_NOSLIP_ADIABATIC])
+def test_closed_box_conserves_mass_and_the_adiabatic_energy(kind):
+    """A box closed by four resting walls: no mass crosses a wall face, so the total mass is
+    conserved to roundoff for every wall kind; slip and adiabatic walls also let no energy
+    through (an isothermal wall exchanges heat).  The initial flow runs into the walls."""
+    p = wl.smooth_wave_2d(18, ny=14, seed=4)
+    P = oracle.params(gamma=1.4, mu=2e-3, Pr=0.72, tau_eps=0.05)
+    st = _state(p)
+    bc = oracle.bcs([kind] * 4, [(0.0, 0.0, 0.9)] * 4)
+    tot0 = st.U.sum(axis=(1, 2))
+    for _ in range(25):
+        assert oracle.step2d(P, st, bc, 0.5)[0] == 0
+    tot = st.U.sum(axis=(1, 2))
+    assert abs(tot[0] - tot0[0]) < 1e-13 * tot0[0]
+    if kind != oracle.BC_NOSLIP_ISOTHERMAL:
+        assert abs(tot[3] - tot0[3]) < 1e-13 * tot0[3]
+    else:
+        assert abs(tot[3] - tot0[3]) > 1e-6 * tot0[3]  # heat drawn by the walls at T_w = 0.9 < T
+    # the walls stop the flow that runs into them: momentum is not conserved
+    assert np.all(np.abs(tot[1:3] - tot0[1:3]) > 1e-3 * np.abs(tot0[1:3]))
+
+
+def test_adiabatic_moving_wall_does_work():
+    """A moving adiabatic lid: the energy entering through it equals the work of the shear on
+    the lid, u_w times the tangential momentum entering (no heat through the wall)."""
+    p = wl.cavity_2d(16)
+    P = oracle.params(gamma=1.4, mu=0.01, Pr=0.72)
+    st = _state(p)
+    wall = (0.0, 0.0, 1.0)
+    bc = oracle.bcs([oracle.BC_NOSLIP_ADIABATIC] * 4, [wall, wall, wall, (0.3, 0.0, 1.0)])
+    tot0 = st.U.sum(axis=(1, 2))
+    for _ in range(20):
+        assert oracle.step2d(P, st, bc, 0.5)[0] == 0
+    d = st.U.sum(axis=(1, 2)) - tot0
+    assert abs(d[0]) < 1e-13 * tot0[0]
+    # x-momentum enters through the lid (the only moving wall) and friction on the other walls
+    # removes some; the energy gained is the lid's work, which is positive
+    assert d[3] > 0 and d[1] > 0
