@@ -106,6 +106,11 @@ typedef struct {
   double tau_eps;    /* epsilon of the inviscid collision time, Section 4 (default 0.05) */
   double tau_C;      /* C of the inviscid collision time, Section 4 (default 1) */
   int viscous_dt;    /* 1: also bound dt by CFL rho h^2 / (2 mu max(4/3, gamma/Pr)) */
+  int characteristic;  /* 1: reconstruct in characteristic variables (Section 4: the paper's
+                          choice for flows with discontinuities): x-derivatives from the
+                          variables projected on the eigenvectors of the x-flux Jacobian of
+                          the cell average, y-derivatives likewise, the cross derivative the
+                          mean of both; 0 (default): conservative variables */
 } gks_options;
 
 typedef struct gks_handle gks_handle;

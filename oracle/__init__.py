@@ -25,7 +25,7 @@ BC_PERIODIC, BC_OUTFLOW, BC_SLIPWALL, BC_NOSLIP_ISOTHERMAL, BC_NOSLIP_ADIABATIC 
 class Params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
                 ("weno_eps", ctypes.c_double), ("weno_C", ctypes.c_double),
-                ("tau_eps", ctypes.c_double), ("tau_C", ctypes.c_double)]
+                ("tau_eps", ctypes.c_double), ("tau_C", ctypes.c_double), ("characteristic", ctypes.c_int)]
 
 
 class BC(ctypes.Structure):
@@ -66,6 +66,7 @@ def lib():
         L.orc_bc_image.argtypes = [P(Params), ctypes.c_int, D, D, dp, dp]
         L.orc_face_first_order.argtypes = [P(Params), dp, dp, D, D, D, dp, dp, dp]
         L.orc_recon_cell.argtypes = [P(Params), dp, dp, dp, D, D, dp]
+        L.orc_char_basis.argtypes = [dp, D, dp, dp]
         L.orc_dt2d.argtypes = [P(Params), ctypes.c_int, ctypes.c_int, D, D, dp, D, D, ctypes.c_int]
         L.orc_dt2d.restype = D
         L.orc_recon2d.argtypes = [P(Params), ctypes.c_int, ctypes.c_int, D, D, P(BC), dp, dp, dp, dp]
@@ -93,8 +94,9 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def params(gamma=1.4, mu=0.0, Pr=1.0, weno_eps=1e-6, weno_C=10.0, tau_eps=0.05, tau_C=1.0) -> Params:
-    return Params(gamma, mu, Pr, weno_eps, weno_C, tau_eps, tau_C)
+def params(gamma=1.4, mu=0.0, Pr=1.0, weno_eps=1e-6, weno_C=10.0, tau_eps=0.05, tau_C=1.0,
+           characteristic=0) -> Params:
+    return Params(gamma, mu, Pr, weno_eps, weno_C, tau_eps, tau_C, int(characteristic))
 
 
 def bcs(kinds, walls=None):
@@ -148,6 +150,14 @@ def face_first_order(P, L, R, dn, dtan, dt):
     F, W, dbg = np.zeros(4), np.zeros((2, 4)), np.zeros(64)
     lib().orc_face_first_order(ctypes.byref(P), _p(L), _p(R), dn, dtan, dt, _p(F), _p(W), _p(dbg))
     return F, W, dbg
+
+
+def char_basis(w, gamma=1.4):
+    """(L, R): left (rows) and right (columns) eigenvectors of the x-flux Jacobian at w."""
+    L = np.zeros((4, 4))
+    R = np.zeros((4, 4))
+    lib().orc_char_basis(_p(np.ascontiguousarray(w, dtype=np.float64)), ctypes.c_double(gamma), _p(L), _p(R))
+    return L, R
 
 
 def bc_image(P, kind, u_wall_t, T_wall, inside):

@@ -30,6 +30,8 @@ typedef struct {
   double gamma, mu, Pr;
   double weno_eps, weno_C;
   double tau_eps, tau_C;
+  int characteristic;  /* 1: reconstruct in characteristic variables (Section 4's choice for
+                          flows with discontinuities), 0: conservative variables */
 } orc_params;
 
 enum { ORC_BC_PERIODIC = 0, ORC_BC_OUTFLOW = 1, ORC_BC_SLIPWALL = 2, ORC_BC_NOSLIP_ISOTHERMAL = 3,
@@ -94,6 +96,11 @@ void orc_bc_image(const orc_params* P, int kind, double u_wall_t, double T_wall,
  * coef_out[var][6] = (Ubar, a2, a3, a4, a5, a6). */
 void orc_recon_cell(const orc_params* P, const double nb[5][4], const double fx[4][4],
                     const double fy[4][4], double dx, double dy, double coef_out[4][6]);
+
+/* Eigenvectors of the x-direction flux Jacobian of the 2D Euler equations at the
+ * conservative state w (columns of R, rows of L = R^-1), for the characteristic
+ * reconstruction. */
+void orc_char_basis(const double w[4], double gamma, double L[4][4], double R[4][4]);
 
 /* ---- grid-level entry points ---- */
 

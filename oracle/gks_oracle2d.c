@@ -701,11 +701,92 @@ static void poly_eval(const double a[6], double dx, double dy, double x, double 
   o[5] = a[4];
 }
 
+/* Eigenvectors of the Jacobian dF/dU of the x-flux of the 2D Euler equations at the
+ * conservative state w: columns of R for the eigenvalues u - c, u (entropy), u (shear),
+ * u + c, and L = R^-1 (rows).  With b1 = (gamma-1)/c^2, b2 = b1 (u^2+v^2)/2 and the total
+ * enthalpy H:  r1 = (1, u-c, v, H-uc), r2 = (1, u, v, q^2/2), r3 = (0, 0, 1, v),
+ * r4 = (1, u+c, v, H+uc);  l1 = (b2 + u/c, -b1 u - 1/c, -b1 v, b1)/2,
+ * l2 = (1-b2, b1 u, b1 v, -b1), l3 = (-v, 0, 1, 0), l4 = (b2 - u/c, -b1 u + 1/c, -b1 v, b1)/2. */
+void orc_char_basis(const double w[4], double gam, double L[4][4], double R[4][4]) {
+  const double rho = w[0], u = w[1] / rho, v = w[2] / rho;
+  const double q2 = u * u + v * v;
+  const double p = (gam - 1.0) * (w[3] - 0.5 * rho * q2);
+  const double c = sqrt(gam * p / rho), H = (w[3] + p) / rho;
+  const double b1 = (gam - 1.0) / (c * c), b2 = 0.5 * b1 * q2;
+  const double Rm[4][4] = {{1.0, 1.0, 0.0, 1.0},
+                           {u - c, u, 0.0, u + c},
+                           {v, v, 1.0, v},
+                           {H - u * c, 0.5 * q2, v, H + u * c}};
+  const double Lm[4][4] = {{0.5 * (b2 + u / c), 0.5 * (-b1 * u - 1.0 / c), -0.5 * b1 * v, 0.5 * b1},
+                           {1.0 - b2, b1 * u, b1 * v, -b1},
+                           {-v, 0.0, 1.0, 0.0},
+                           {0.5 * (b2 - u / c), 0.5 * (-b1 * u + 1.0 / c), -0.5 * b1 * v, 0.5 * b1}};
+  memcpy(R, Rm, sizeof(Rm));
+  memcpy(L, Lm, sizeof(Lm));
+}
+
+/* momenta swapped: the y-direction quantities in the x-frame formulas */
+static void swap_uv(const double a[4], double o[4]) {
+  o[0] = a[0]; o[1] = a[2]; o[2] = a[1]; o[3] = a[3];
+}
+
+/* Reconstruction in the characteristic variables of one direction (axis 0: x, 1: y) of the
+ * cell average: every stencil value is projected with L, each characteristic variable is
+ * reconstructed as a scalar, and the coefficients are projected back with R. */
+static void recon_char_axis(const orc_params* P, int axis, const double nb[5][4], const double fx[4][4],
+                            const double fy[4][4], double dx, double dy, double co[4][6]) {
+  double L[4][4], R[4][4], ref[4];
+  if (axis == 0) memcpy(ref, nb[0], sizeof(ref)); else swap_uv(nb[0], ref);
+  orc_char_basis(ref, P->gamma, L, R);
+  /* the 13 stencil vectors, projected */
+  double in[13][4], pr[13][4];
+  for (int k = 0; k < 5; ++k) memcpy(in[k], nb[k], sizeof(in[k]));
+  for (int k = 0; k < 4; ++k) memcpy(in[5 + k], fx[k], sizeof(in[k]));
+  for (int k = 0; k < 4; ++k) memcpy(in[9 + k], fy[k], sizeof(in[k]));
+  for (int k = 0; k < 13; ++k) {
+    double a[4];
+    if (axis == 0) memcpy(a, in[k], sizeof(a)); else swap_uv(in[k], a);
+    for (int r = 0; r < 4; ++r) {
+      pr[k][r] = 0.0;
+      for (int c = 0; c < 4; ++c) pr[k][r] += L[r][c] * a[c];
+    }
+  }
+  double cc[4][6];
+  for (int r = 0; r < 4; ++r)
+    recon_var(P, pr[0][r], pr[1][r], pr[2][r], pr[3][r], pr[4][r], pr[5][r], pr[6][r], pr[7][r],
+              pr[8][r], pr[9][r], pr[10][r], pr[11][r], pr[12][r], dx, dy, cc[r]);
+  for (int m = 0; m < 6; ++m) {
+    double a[4], o[4];
+    for (int r = 0; r < 4; ++r) {
+      a[r] = 0.0;
+      for (int c = 0; c < 4; ++c) a[r] += R[r][c] * cc[c][m];
+    }
+    if (axis == 0) memcpy(o, a, sizeof(o)); else swap_uv(a, o);
+    for (int v = 0; v < 4; ++v) co[v][m] = o[v];
+  }
+}
+
 void orc_recon_cell(const orc_params* P, const double nb[5][4], const double fx[4][4],
                     const double fy[4][4], double dx, double dy, double co[4][6]) {
-  for (int v = 0; v < 4; ++v)
-    recon_var(P, nb[0][v], nb[1][v], nb[2][v], nb[3][v], nb[4][v], fx[0][v], fx[1][v], fx[2][v],
-              fx[3][v], fy[0][v], fy[1][v], fy[2][v], fy[3][v], dx, dy, co[v]);
+  if (P->characteristic) {
+    /* x-derivative coefficients (a2, a4) from the x-characteristic reconstruction, y ones
+     * (a3, a5) from the y-characteristic one, the cross derivative a6 their mean */
+    double cx[4][6], cy[4][6];
+    recon_char_axis(P, 0, nb, fx, fy, dx, dy, cx);
+    recon_char_axis(P, 1, nb, fx, fy, dx, dy, cy);
+    for (int v = 0; v < 4; ++v) {
+      co[v][0] = nb[0][v];
+      co[v][1] = cx[v][1];
+      co[v][2] = cy[v][2];
+      co[v][3] = cx[v][3];
+      co[v][4] = cy[v][4];
+      co[v][5] = 0.5 * (cx[v][5] + cy[v][5]);
+    }
+  } else {
+    for (int v = 0; v < 4; ++v)
+      recon_var(P, nb[0][v], nb[1][v], nb[2][v], nb[3][v], nb[4][v], fx[0][v], fx[1][v], fx[2][v],
+                fx[3][v], fy[0][v], fy[1][v], fy[2][v], fy[3][v], dx, dy, co[v]);
+  }
   /* positivity: a cell whose polynomial gives rho <= 0 or p <= 0 at a face
    * centre falls back to its constant average */
   const double pts[4][2] = {{0.5 * dx, 0}, {-0.5 * dx, 0}, {0, 0.5 * dy}, {0, -0.5 * dy}};

@@ -62,8 +62,9 @@ __global__ void k_ghost(Geo g, Cells<R> U0, Cells<R> U1, const Ctrl* c, int forc
 // reconstruction; U is the padded cell-average array in the compute type
 // ---------------------------------------------------------------------------
 // begin = 1: block 0 also opens the step (ctrl_begin); the other blocks then do
-// not look at the skip flag it sets (coefficients of a skipped step go unused)
-template <class R, class TW>
+// not look at the skip flag it sets (coefficients of a skipped step go unused).
+// CHAR: reconstruction in characteristic variables.
+template <class R, class TW, bool CHAR>
 __global__ void __launch_bounds__(256) k_recon(Geo g, const R* U0, const R* U1, const TW* Wx0, const TW* Wx1,
                                                const TW* Wy0, const TW* Wy1, R* __restrict__ coef, R dx, R dy,
                                                R weps, R wC, Ctrl* c, int force, int begin, double cfl,
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(256) k_recon(Geo g, const R* U0, const R* U1, 
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
   const int par = (int)(c->steps & 1);
-  recon_cell<R, TW>(g, par ? U1 : U0, par ? Wx1 : Wx0, par ? Wy1 : Wy0, coef, i, j, dx, dy, weps, wC);
+  recon_cell<R, TW, CHAR>(g, par ? U1 : U0, par ? Wx1 : Wx0, par ? Wy1 : Wy0, coef, i, j, dx, dy, weps, wC);
 }
 
 // ---------------------------------------------------------------------------
@@ -335,7 +336,8 @@ cudaError_t launch_recon(gks_handle* h, int force, int begin = 0, double cfl = 0
                          double t_end = 0, bool pdl = false) {
   const Geo& g = h->g;
   const dim3 b2(32, 8);
-  return launch(pdl, k_recon<R, TW>, grid2(g.nx, g.ny, b2), b2, h->stream, g, cells<R>(h, 0), cells<R>(h, 1),
+  return launch(pdl, g.characteristic ? k_recon<R, TW, true> : k_recon<R, TW, false>, grid2(g.nx, g.ny, b2), b2,
+                h->stream, g, cells<R>(h, 0), cells<R>(h, 1),
          (const TW*)h->Wx[0], (const TW*)h->Wx[1], (const TW*)h->Wy[0], (const TW*)h->Wy[1], (R*)h->coef, R(g.dx),
          R(g.dy), R(g.weno_eps), R(g.weno_C), h->ctrl, force, begin, cfl, dt_max, t_end);
 }
@@ -482,6 +484,7 @@ void make_geo(Geo& g, int nx, int ny, double Lx, double Ly, double gamma, double
   g.gamma = gamma; g.mu = mu; g.Pr = Pr;
   g.weno_eps = o.weno_eps; g.weno_C = o.weno_C; g.tau_eps = o.tau_eps; g.tau_C = o.tau_C;
   g.viscous_dt = o.viscous_dt;
+  g.characteristic = o.characteristic;
   for (int k = 0; k < 4; ++k) {
     g.bc.kind[k] = bc ? bc[k].kind : GKS_BC_PERIODIC;
     g.bc.uw[k] = bc ? bc[k].u_wall : 0.0;
@@ -499,6 +502,7 @@ gks_status check_args(int nx, int ny, double Lx, double Ly, double gamma, double
   if (!(Pr > 0)) { why = "Pr must be > 0"; return GKS_EINVAL; }
   if (!(mu >= 0)) { why = "mu must be >= 0"; return GKS_EINVAL; }
   if (o->precision != GKS_FP64 && o->precision != GKS_FP32_BULK) { why = "unknown precision"; return GKS_EINVAL; }
+  if (o->characteristic != 0 && o->characteristic != 1) { why = "characteristic must be 0 or 1"; return GKS_EINVAL; }
   if (!(o->weno_eps >= 0) || !(o->weno_C > 0) || !(o->tau_eps >= 0) || !(o->tau_C >= 0)) {
     why = "invalid scheme constants"; return GKS_EINVAL;
   }
@@ -530,6 +534,7 @@ void gks_default_options(gks_options* o) {
   o->tau_eps = 0.05;
   o->tau_C = 1.0;
   o->viscous_dt = 0;
+  o->characteristic = 0;
 }
 
 gks_status gks_create(int nx, int ny, double Lx, double Ly, double gamma, double Pr, double mu, const gks_bc* bc,
@@ -893,7 +898,8 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
   k_scatter_U<double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, dU, C0, C1, ctrl, 1);
   k_ghost<double><<<(per + 127) / 128, 128, 0, s>>>(g, C0, C1, ctrl, 1);
   k_dtbound<double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, C0, C1, ctrl);
-  k_recon<double, double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, U0, U1, dWx, dWx_out, dWy, dWy_out, coef, g.dx, g.dy,
+  (g.characteristic ? k_recon<double, double, true> : k_recon<double, double, false>)<<<grid2(nx, ny, b2), b2, 0, s>>>(
+      g, U0, U1, dWx, dWx_out, dWy, dWy_out, coef, g.dx, g.dy,
                                                             g.weno_eps, g.weno_C, ctrl, 0, 1, CFL,
                                                             dt_max, INFINITY);
   k_flux<0, double, double><<<grid2(nx + 1, ny, bf), bf, 0, s>>>(g, fconst<double>(g, 0), U0, U1, coef,

@@ -135,8 +135,12 @@ __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<
       const int par = (int)(c->steps & 1);
       const GridOff& o = a.off[w.x];
       const R* U = (const R*)(a.U[par] + o.u);
-      recon_cell<R, TW>(g, U, a.Wx[par] + o.wx, a.Wy[par] + o.wy, a.coef + o.coef, i, j, GeoR<R>::dx(g),
-                        GeoR<R>::dy(g), GeoR<R>::weps(g), GeoR<R>::wC(g));
+      if (g.characteristic)
+        recon_cell<R, TW, true>(g, U, a.Wx[par] + o.wx, a.Wy[par] + o.wy, a.coef + o.coef, i, j, GeoR<R>::dx(g),
+                                GeoR<R>::dy(g), GeoR<R>::weps(g), GeoR<R>::wC(g));
+      else
+        recon_cell<R, TW, false>(g, U, a.Wx[par] + o.wx, a.Wy[par] + o.wy, a.coef + o.coef, i, j,
+                                 GeoR<R>::dx(g), GeoR<R>::dy(g), GeoR<R>::weps(g), GeoR<R>::wC(g));
     }
     if (!grid_barrier(a.bar)) return;
 
@@ -439,6 +443,7 @@ gks_status gks_batch_create(int n, const gks_grid_desc* grids, const gks_options
     G.gamma = d.gamma; G.mu = d.mu; G.Pr = d.Pr;
     G.weno_eps = o.weno_eps; G.weno_C = o.weno_C; G.tau_eps = o.tau_eps; G.tau_C = o.tau_C;
     G.viscous_dt = o.viscous_dt;
+    G.characteristic = o.characteristic;
     for (int k = 0; k < 4; ++k) {
       G.bc.kind[k] = d.bc[k].kind;
       G.bc.uw[k] = d.bc[k].u_wall;

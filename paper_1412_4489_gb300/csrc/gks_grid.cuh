@@ -44,6 +44,7 @@ struct Geo {
   double gamma, mu, Pr;
   double weno_eps, weno_C, tau_eps, tau_C;
   int viscous_dt;
+  int characteristic;  // reconstruction in characteristic variables
   BCs bc;
 };
 
@@ -312,27 +313,145 @@ __device__ __forceinline__ void ghost_at(const Geo& g, Cells<R> U, int p) {
 // reconstruction of cell (i, j); U is the padded cell-average array in the
 // compute type, Wx/Wy the face point values; writes coef[5][4][ny][nx]
 // ---------------------------------------------------------------------------
-template <class R, class TW>
+// Eigenvectors of the Jacobian of the x-flux of the 2D Euler equations at the
+// conservative state w: columns of Rv for the eigenvalues u - c, u (entropy), u (shear),
+// u + c, and Lv = Rv^-1 (rows).  With b1 = (gamma-1)/c^2, b2 = b1 q^2/2 and the total
+// enthalpy H: r1 = (1, u-c, v, H-uc), r2 = (1, u, v, q^2/2), r3 = (0, 0, 1, v),
+// r4 = (1, u+c, v, H+uc); l1 = (b2 + u/c, -b1 u - 1/c, -b1 v, b1)/2, l2 = (1-b2, b1 u,
+// b1 v, -b1), l3 = (-v, 0, 1, 0), l4 = (b2 - u/c, -b1 u + 1/c, -b1 v, b1)/2.  Returns false
+// for a non-physical state.
+template <class R>
+__device__ __forceinline__ bool char_basis(const R w[4], R gm1, R gam, R Lv[4][4], R Rv[4][4]) {
+  const R rho = w[0], ir = d_div(R(1), rho);
+  const R u = w[1] * ir, v = w[2] * ir, q2 = u * u + v * v;
+  const R p = gm1 * (w[3] - R(0.5) * rho * q2);
+  if (!(rho > R(0)) || !(p > R(0))) return false;
+  const R c2 = gam * p * ir, c = sqrt(c2), ic = d_div(R(1), c);
+  const R H = (w[3] + p) * ir, b1 = d_div(gm1, c2), b2 = R(0.5) * b1 * q2;
+  const R rv[4][4] = {{R(1), R(1), R(0), R(1)},
+                      {u - c, u, R(0), u + c},
+                      {v, v, R(1), v},
+                      {H - u * c, R(0.5) * q2, v, H + u * c}};
+  const R lv[4][4] = {{R(0.5) * (b2 + u * ic), R(0.5) * (-b1 * u - ic), R(-0.5) * b1 * v, R(0.5) * b1},
+                      {R(1) - b2, b1 * u, b1 * v, -b1},
+                      {-v, R(0), R(1), R(0)},
+                      {R(0.5) * (b2 - u * ic), R(0.5) * (-b1 * u + ic), R(-0.5) * b1 * v, R(0.5) * b1}};
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Rv[r][k] = rv[r][k];
+      Lv[r][k] = lv[r][k];
+    }
+  return true;
+}
+
+// Reconstruction of cell (i, j) from its 13 stencil vectors (the cell and its four
+// neighbours, the eight face Gauss values), all four variables: in conservative
+// variables (CHAR = false), or in characteristic ones: the x-derivative coefficients
+// (a2, a4) from a reconstruction of the variables projected on the eigenvectors of the
+// x-flux Jacobian of the cell average, the y ones (a3, a5) from the y-flux Jacobian's,
+// the cross derivative a6 the mean of both.
+template <bool CHAR, class R>
+__device__ __forceinline__ void recon_vectors(const R in[13][4], const ReconK<R>& K, R gm1, R gam, R a[4][5]) {
+  if (!CHAR) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      recon_var<R>(in[0][v], in[1][v], in[2][v], in[3][v], in[4][v], in[5][v], in[6][v], in[7][v], in[8][v],
+                   in[9][v], in[10][v], in[11][v], in[12][v], K, a[v]);
+    return;
+  }
+#pragma unroll
+  for (int axis = 0; axis < 2; ++axis) {
+    // momenta swapped for the y direction (the x-frame formulas with u <-> v)
+    const int m1 = axis == 0 ? 1 : 2, m2 = axis == 0 ? 2 : 1;
+    R ref[4] = {in[0][0], in[0][m1], in[0][m2], in[0][3]};
+    R Lv[4][4], Rv[4][4];
+    if (!char_basis(ref, gm1, gam, Lv, Rv)) {
+      recon_vectors<false, R>(in, K, gm1, gam, a);
+      return;
+    }
+    R cc[4][5];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      R pr[13];
+#pragma unroll
+      for (int k = 0; k < 13; ++k)
+        pr[k] = Lv[r][0] * in[k][0] + Lv[r][1] * in[k][m1] + Lv[r][2] * in[k][m2] + Lv[r][3] * in[k][3];
+      recon_var<R>(pr[0], pr[1], pr[2], pr[3], pr[4], pr[5], pr[6], pr[7], pr[8], pr[9], pr[10], pr[11], pr[12],
+                   K, cc[r]);
+    }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      // a2, a4 (m = 0, 2) from the x pass; a3, a5 (m = 1, 3) from the y pass; a6 from both
+      if (m == 4 || (axis == 0) == (m == 0 || m == 2)) {
+        R o[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) o[r] = Rv[r][0] * cc[0][m] + Rv[r][1] * cc[1][m] + Rv[r][2] * cc[2][m] + Rv[r][3] * cc[3][m];
+        const R s = m == 4 ? R(0.5) : R(1);
+        const R w4[4] = {o[0], axis == 0 ? o[1] : o[2], axis == 0 ? o[2] : o[1], o[3]};
+#pragma unroll
+        for (int v = 0; v < 4; ++v) a[v][m] = (m == 4 && axis == 1) ? a[v][m] + s * w4[v] : s * w4[v];
+      }
+    }
+  }
+}
+
+template <class R, class TW, bool CHAR = false>
 __device__ __forceinline__ void recon_cell(const Geo& g, const R* __restrict__ U, const TW* __restrict__ Wx,
                                            const TW* __restrict__ Wy, R* __restrict__ coef, int i, int j, R dx,
                                            R dy, R weps, R wC) {
   const int nx = g.nx, ny = g.ny;
   const size_t fxp = (size_t)ny * (nx + 1), fyp = (size_t)(ny + 1) * nx;
   const ReconK<R> K = recon_k(dx, dy, weps, wC);
-  R a[4][5];
+  R a[4][5], cbar[4];
+  // stencil vector k of variable v: c, e, w, n, s; east face y-/y+, west y-/y+, north x-/x+,
+  // south x-/x+
+  auto load = [&](int v, R in[13]) {
+    const TW* wx = Wx + (size_t)v * 2 * fxp + (size_t)j * (nx + 1);
+    const TW* wy = Wy + (size_t)v * 2 * fyp;
+    in[0] = U[ci(g, v, i, j)];
+    in[1] = U[ci(g, v, i + 1, j)];
+    in[2] = U[ci(g, v, i - 1, j)];
+    in[3] = U[ci(g, v, i, j + 1)];
+    in[4] = U[ci(g, v, i, j - 1)];
+    in[5] = R(wx[i + 1]);
+    in[6] = R(wx[fxp + i + 1]);
+    in[7] = R(wx[i]);
+    in[8] = R(wx[fxp + i]);
+    in[9] = R(wy[(size_t)(j + 1) * nx + i]);
+    in[10] = R(wy[fyp + (size_t)(j + 1) * nx + i]);
+    in[11] = R(wy[(size_t)j * nx + i]);
+    in[12] = R(wy[fyp + (size_t)j * nx + i]);
+  };
+  if (CHAR) {
+    R in[13][4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      R t[13];
+      load(v, t);
+#pragma unroll
+      for (int k = 0; k < 13; ++k) in[k][v] = t[k];
+      cbar[v] = t[0];
+    }
+    recon_vectors<true, R>(in, K, GeoR<R>::gm1(g), GeoR<R>::gamma(g), a);
+  } else {
+    // one variable at a time: only its 13 stencil values are live
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      R t[13];
+      load(v, t);
+      cbar[v] = t[0];
+      recon_var<R>(t[0], t[1], t[2], t[3], t[4], t[5], t[6], t[7], t[8], t[9], t[10], t[11], t[12], K, a[v]);
+    }
+  }
   // the polynomial at the four face centres (x = +-dx/2, y = 0 and x = 0, y = +-dy/2):
   // value = e0 +- a2 dx/2 on x-faces, n0 +- a3 dy/2 on y-faces
   R ve[4], vw[4], vn[4], vs[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    const R cc = U[ci(g, v, i, j)];
-    const TW* wx = Wx + (size_t)v * 2 * fxp + (size_t)j * (nx + 1);
-    const TW* wy = Wy + (size_t)v * 2 * fyp;
-    recon_var<R>(cc, U[ci(g, v, i + 1, j)], U[ci(g, v, i - 1, j)], U[ci(g, v, i, j + 1)], U[ci(g, v, i, j - 1)],
-                 R(wx[i + 1]), R(wx[fxp + i + 1]), R(wx[i]), R(wx[fxp + i]), R(wy[(size_t)(j + 1) * nx + i]),
-                 R(wy[fyp + (size_t)(j + 1) * nx + i]), R(wy[(size_t)j * nx + i]), R(wy[fyp + (size_t)j * nx + i]),
-                 K, a[v]);
     // U(x, y) = c + a2 x + a3 y + a4 (x^2 - dx^2/12)/2 + a5 (y^2 - dy^2/12)/2 + a6 x y
+    const R cc = cbar[v];
     const R e0 = cc + a[v][2] * K.dx2_12 - a[v][3] * R(0.5) * K.dy2_12;
     const R n0 = cc + a[v][3] * K.dy2_12 - a[v][2] * R(0.5) * K.dx2_12;
     ve[v] = e0 + a[v][0] * (R(0.5) * dx);

@@ -29,7 +29,8 @@ class gks_bc(ctypes.Structure):
 
 class gks_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("weno_eps", ctypes.c_double), ("weno_C", ctypes.c_double),
-                ("tau_eps", ctypes.c_double), ("tau_C", ctypes.c_double), ("viscous_dt", ctypes.c_int)]
+                ("tau_eps", ctypes.c_double), ("tau_C", ctypes.c_double), ("viscous_dt", ctypes.c_int),
+                ("characteristic", ctypes.c_int)]
 
 
 class gks_grid_desc(ctypes.Structure):

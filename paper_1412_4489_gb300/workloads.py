@@ -275,9 +275,16 @@ def isotropic_vortex(n: int, gamma: float = 1.4, eps: float = 5.0, nq: int = 6) 
 
 def sod(nx: int, gamma: float = 1.4) -> Problem:
     """Sod's shock tube on [0, 1] (diaphragm at x = 0.5) as an nx-by-1 grid, dy = dx."""
+    return shock_tube(nx, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), gamma, name=f"sod_{nx}")
+
+
+def shock_tube(nx: int, left, right, gamma: float = 1.4, name: str | None = None) -> Problem:
+    """A Riemann problem on [0, 1] with primitive states left = (rho, u, p) for x < 0.5 and
+    right for x > 0.5, as an nx-by-1 grid (dy = dx), periodic in y, outflow ends."""
     Lx = 1.0
     dx = Lx / nx
-    left, right = _cons(1.0, 0.0, 0.0, 1.0, gamma), _cons(0.125, 0.0, 0.0, 0.1, gamma)
+    left = _cons(left[0], left[1], 0.0, left[2], gamma)
+    right = _cons(right[0], right[1], 0.0, right[2], gamma)
     xl = np.arange(nx) * dx
     fr = np.clip((xl + dx - 0.5) / dx, 0.0, 1.0)  # fraction of the cell right of x = 0.5
     U = (left.reshape(4, 1) * (1 - fr) + right.reshape(4, 1) * fr)[:, None, :]
@@ -292,7 +299,7 @@ def sod(nx: int, gamma: float = 1.4) -> Problem:
     Wy = _point_state(pt, wyp)
     bc = [(BC_OUTFLOW, 0.0, 0.0, 1.0), (BC_OUTFLOW, 0.0, 0.0, 1.0), (BC_PERIODIC, 0.0, 0.0, 1.0),
           (BC_PERIODIC, 0.0, 0.0, 1.0)]
-    return Problem(f"sod_{nx}", nx, 1, Lx, dx, gamma, 0.0, 1.0, bc,
+    return Problem(name or f"shock_tube_{nx}", nx, 1, Lx, dx, gamma, 0.0, 1.0, bc,
                    np.ascontiguousarray(U), np.ascontiguousarray(Wx), np.ascontiguousarray(Wy))
 
 

@@ -36,4 +36,5 @@ def test_binding_names_match_the_abi():
 def test_default_options():
     from paper_1412_4489_gb300 import gks
     o = gks.gks_default_options()
-    assert (o.precision, o.weno_eps, o.weno_C, o.tau_eps, o.tau_C, o.viscous_dt) == (0, 1e-6, 10.0, 0.05, 1.0, 0)
+    assert (o.precision, o.weno_eps, o.weno_C, o.tau_eps, o.tau_C, o.viscous_dt, o.characteristic) == \
+        (0, 1e-6, 10.0, 0.05, 1.0, 0, 0)
