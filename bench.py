@@ -255,6 +255,7 @@ def run_ours(args):
     b.close()
     errors = error_legs(stream) if not args.no_batch else None
     validation = vortex_leg(stream) if not args.no_batch else None
+    characteristic = characteristic_leg(stream) if not args.no_batch else None
 
     # ---- end to end through the C ABI with host buffers ----
     KE = max(3, min(args.steps, 20))
@@ -346,6 +347,7 @@ def run_ours(args):
                               "kernel_ms": round(prof64[dom], 5)},
             "batched": batched,
             "validation": validation,
+            "characteristic": characteristic,
             "fp32_4096": big,
             "kernels_ms_fp32": {k: round(v, 5) for k, v in prof.items()},
             "kernels_ms_fp64": {k: round(v, 5) for k, v in prof64.items()},
@@ -436,6 +438,34 @@ def vortex_leg(stream):
         d = U[0] - p.U[0]
         out[name] = {"L1": float(np.mean(np.abs(d))), "L2": float(math.sqrt(np.mean(d * d))), "steps": int(k),
                      "value": round(121 * 121 * k / (ms * 1e-3) / 1e6, 3), "unit": UNIT}
+    return out
+
+
+def characteristic_leg(stream):
+    """The Navier-Stokes four-quadrant data at 1024^2 with the reconstruction in conservative
+    and in characteristic variables: step throughput (CUDA events over 20 graph-replayed steps
+    after 3 warm-up steps) and the reconstruction kernel's time."""
+    import torch
+    from paper_1412_4489_gb300 import gks, workloads as wl
+    p = wl.riemann_2d(1024, seed=3, mu=1e-4, Pr=0.72)
+    out = {"workload": "NS four-quadrant data 1024^2, seed 3, mu 1e-4, Pr 0.72, CFL 0.5", "unit": UNIT}
+    for prec, pname in ((gks.GKS_FP32_BULK, "fp32_bulk"), (gks.GKS_FP64, "fp64")):
+        for ch in (0, 1):
+            with torch.cuda.stream(stream):
+                s = gks.Solver(p, prec, stream=stream.cuda_stream, characteristic=ch)
+                s.advance(3, CFL)
+                s.sync()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.advance(20, CFL)
+                e1.record(stream)
+                e1.synchronize()
+                recon = gks.gks_profile_step(s.h, CFL)["recon"]
+                s.close()
+            ms = e0.elapsed_time(e1) / 20
+            out[f"{pname}_{'characteristic' if ch else 'conservative'}"] = {
+                "value": round(p.nx * p.ny / (ms * 1e-3) / 1e6, 3), "ms_per_step": round(ms, 4),
+                "recon_ms": round(recon, 4)}
     return out
 
 

@@ -117,8 +117,14 @@ __global__ void __launch_bounds__(128, FluxBlocks<R>::value) k_flux(Geo g, FaceC
 // keeps its own running minimum of the CFL bound.  Blocks walk the grid's
 // 32 x 8 tiles with a stride of the launch grid: pass 1 is launched with one block
 // per tile, passes 2 and 3 (usually no work) with a few blocks per SM.
+// Resident blocks per SM the update is compiled for: the rarely taken fallback path
+// must not raise the register count of the common one (FP32: 64 registers).
+template <class R> struct UpdateBlocks;
+template <> struct UpdateBlocks<double> { static constexpr int value = 2; };
+template <> struct UpdateBlocks<float> { static constexpr int value = 4; };
+
 template <class R, class TW>
-__global__ void __launch_bounds__(256) k_update(Geo g, Cells<R> U0, Cells<R> U1, const R* __restrict__ Fx,
+__global__ void __launch_bounds__(256, UpdateBlocks<R>::value) k_update(Geo g, Cells<R> U0, Cells<R> U1, const R* __restrict__ Fx,
                                                 const R* __restrict__ Fy, TW* Wx0, TW* Wx1, TW* Wy0, TW* Wy1,
                                                 unsigned char* __restrict__ bad, Ctrl* c, int pass) {
   pdl_enter();

@@ -354,44 +354,44 @@ __device__ __forceinline__ bool char_basis(const R w[4], R gm1, R gam, R Lv[4][4
 // the cross derivative a6 the mean of both.
 template <bool CHAR, class R>
 __device__ __forceinline__ void recon_vectors(const R in[13][4], const ReconK<R>& K, R gm1, R gam, R a[4][5]) {
-  if (!CHAR) {
+  if constexpr (!CHAR) {
 #pragma unroll
     for (int v = 0; v < 4; ++v)
       recon_var<R>(in[0][v], in[1][v], in[2][v], in[3][v], in[4][v], in[5][v], in[6][v], in[7][v], in[8][v],
                    in[9][v], in[10][v], in[11][v], in[12][v], K, a[v]);
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int axis = 0; axis < 2; ++axis) {
-    // momenta swapped for the y direction (the x-frame formulas with u <-> v)
-    const int m1 = axis == 0 ? 1 : 2, m2 = axis == 0 ? 2 : 1;
-    R ref[4] = {in[0][0], in[0][m1], in[0][m2], in[0][3]};
-    R Lv[4][4], Rv[4][4];
-    if (!char_basis(ref, gm1, gam, Lv, Rv)) {
-      recon_vectors<false, R>(in, K, gm1, gam, a);
-      return;
-    }
-    R cc[4][5];
+    for (int axis = 0; axis < 2; ++axis) {
+      // momenta swapped for the y direction (the x-frame formulas with u <-> v)
+      const int m1 = axis == 0 ? 1 : 2, m2 = axis == 0 ? 2 : 1;
+      R ref[4] = {in[0][0], in[0][m1], in[0][m2], in[0][3]};
+      R Lv[4][4], Rv[4][4];
+      if (!char_basis(ref, gm1, gam, Lv, Rv)) {
+        recon_vectors<false, R>(in, K, gm1, gam, a);
+        return;
+      }
+      R cc[4][5];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      R pr[13];
+      for (int r = 0; r < 4; ++r) {
+        R pr[13];
 #pragma unroll
-      for (int k = 0; k < 13; ++k)
-        pr[k] = Lv[r][0] * in[k][0] + Lv[r][1] * in[k][m1] + Lv[r][2] * in[k][m2] + Lv[r][3] * in[k][3];
-      recon_var<R>(pr[0], pr[1], pr[2], pr[3], pr[4], pr[5], pr[6], pr[7], pr[8], pr[9], pr[10], pr[11], pr[12],
-                   K, cc[r]);
-    }
+        for (int k = 0; k < 13; ++k)
+          pr[k] = Lv[r][0] * in[k][0] + Lv[r][1] * in[k][m1] + Lv[r][2] * in[k][m2] + Lv[r][3] * in[k][3];
+        recon_var<R>(pr[0], pr[1], pr[2], pr[3], pr[4], pr[5], pr[6], pr[7], pr[8], pr[9], pr[10], pr[11], pr[12],
+                     K, cc[r]);
+      }
 #pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      // a2, a4 (m = 0, 2) from the x pass; a3, a5 (m = 1, 3) from the y pass; a6 from both
-      if (m == 4 || (axis == 0) == (m == 0 || m == 2)) {
-        R o[4];
+      for (int m = 0; m < 5; ++m) {
+        // a2, a4 (m = 0, 2) from the x pass; a3, a5 (m = 1, 3) from the y pass; a6 from both
+        if (m == 4 || (axis == 0) == (m == 0 || m == 2)) {
+          R o[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) o[r] = Rv[r][0] * cc[0][m] + Rv[r][1] * cc[1][m] + Rv[r][2] * cc[2][m] + Rv[r][3] * cc[3][m];
-        const R s = m == 4 ? R(0.5) : R(1);
-        const R w4[4] = {o[0], axis == 0 ? o[1] : o[2], axis == 0 ? o[2] : o[1], o[3]};
+          for (int r = 0; r < 4; ++r) o[r] = Rv[r][0] * cc[0][m] + Rv[r][1] * cc[1][m] + Rv[r][2] * cc[2][m] + Rv[r][3] * cc[3][m];
+          const R s = m == 4 ? R(0.5) : R(1);
+          const R w4[4] = {o[0], axis == 0 ? o[1] : o[2], axis == 0 ? o[2] : o[1], o[3]};
 #pragma unroll
-        for (int v = 0; v < 4; ++v) a[v][m] = (m == 4 && axis == 1) ? a[v][m] + s * w4[v] : s * w4[v];
+          for (int v = 0; v < 4; ++v) a[v][m] = (m == 4 && axis == 1) ? a[v][m] + s * w4[v] : s * w4[v];
+        }
       }
     }
   }
@@ -424,7 +424,7 @@ __device__ __forceinline__ void recon_cell(const Geo& g, const R* __restrict__ U
     in[11] = R(wy[(size_t)j * nx + i]);
     in[12] = R(wy[fyp + (size_t)j * nx + i]);
   };
-  if (CHAR) {
+  if constexpr (CHAR) {
     R in[13][4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
