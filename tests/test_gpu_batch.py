@@ -98,3 +98,50 @@ def test_barrier_wait_times_out_instead_of_hanging():
     c.step(2, 0.5)
     assert c.sync() == (2, 2)
     c.close()
+
+
+def _bench_subset(n):
+    """The first n grids of the benchmark's 512-grid batch (sizes 32..384, both kinds, both
+    gammas, mu ~ logU[1e-5, 1e-3])."""
+    return [wl.batch_problem(sp) for sp in wl.batch_specs(512, seed=5)[:n]]
+
+
+def test_benchmark_batch_subset_fp64_against_the_oracle():
+    """16 grids of the benchmark batch in one persistent launch, FP64, against the oracle run
+    grid by grid (the oracle on the host cores): rel-Linf 1e-10 on the smooth waves, L1 1e-8 on
+    the four-quadrant data."""
+    ps = _bench_subset(16)
+    b = gks.Batch(ps, gks.GKS_FP64)
+    n = 3
+    b.step(n, 0.5)
+    b.sync()
+    for g, p in enumerate(ps):
+        P = oracle.params(gamma=p.gamma, mu=p.mu, Pr=p.Pr)
+        st = oracle.State2D(p.nx, p.ny, p.Lx, p.Ly, p.U, p.Wx, p.Wy)
+        bc = oracle.bcs([q[0] for q in p.bc], [q[1:] for q in p.bc])
+        for _ in range(n):
+            assert oracle.step2d(P, st, bc, 0.5)[0] == 0
+        U, _, _, t, _ = b.state(g)
+        assert t == pytest.approx(st.t, rel=1e-12)
+        if p.bc[0][0] == wl.BC_PERIODIC:
+            assert np.max(np.abs(U - st.U)) <= 1e-10 * np.max(np.abs(st.U)), g
+        else:
+            assert np.sum(np.abs(U[0] - st.U[0])) <= 1e-8 * np.sum(np.abs(st.U[0])), g
+    b.close()
+
+
+def test_benchmark_batch_fp32_bulk_l1_per_grid():
+    """The FP32-bulk batch against the FP64 batch, grid by grid: relative L1 of density within
+    1e-5 after the steps the benchmark times."""
+    ps = _bench_subset(64)
+    a, c = gks.Batch(ps, gks.GKS_FP64), gks.Batch(ps, gks.GKS_FP32_BULK)
+    for b in (a, c):
+        b.step(6, 0.5)
+        b.sync()
+    worst = 0.0
+    for g in range(len(ps)):
+        U64, U32 = a.state(g)[0], c.state(g)[0]
+        worst = max(worst, np.sum(np.abs(U32[0] - U64[0])) / np.sum(np.abs(U64[0])))
+    a.close()
+    c.close()
+    assert worst <= 1e-5, worst
