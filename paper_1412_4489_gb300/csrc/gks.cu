@@ -502,7 +502,9 @@ void make_geo(Geo& g, int nx, int ny, double Lx, double Ly, double gamma, double
 
 gks_status check_args(int nx, int ny, double Lx, double Ly, double gamma, double Pr, double mu, const gks_bc* bc,
                       const gks_options* o, std::string& why) {
-  if (nx < 1 || ny < 1 || (long long)nx * ny > (1LL << 31)) { why = "nx, ny must be >= 1"; return GKS_EINVAL; }
+  if (nx < 1 || ny < 1 || (long long)nx * ny > (1LL << 31)) { why = "nx, ny >= 1 and nx * ny <= 2^31 required"; return GKS_EINVAL; }
+  // launch grids: the face kernels cover ny + 1 rows with 4-row blocks (grid y <= 65535)
+  if (ny > 4 * 65535 - 1) { why = "ny must be < 262140"; return GKS_EINVAL; }
   if (!(Lx > 0) || !(Ly > 0)) { why = "Lx, Ly must be > 0"; return GKS_EINVAL; }
   if (!(gamma > 1.0) || !(gamma < 3.0)) { why = "gamma must lie in (1, 3)"; return GKS_EINVAL; }
   if (!(Pr > 0)) { why = "Pr must be > 0"; return GKS_EINVAL; }

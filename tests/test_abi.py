@@ -38,3 +38,14 @@ def test_default_options():
     o = gks.gks_default_options()
     assert (o.precision, o.weno_eps, o.weno_C, o.tau_eps, o.tau_C, o.viscous_dt, o.characteristic) == \
         (0, 1e-6, 10.0, 0.05, 1.0, 0, 0)
+
+
+def test_invalid_sizes_are_rejected_before_touching_the_device():
+    """Argument checks run before any CUDA call, so they hold on a host without a GPU: empty
+    grids, more than 2^31 cells, and grids taller than the launch grids can cover."""
+    import pytest
+    from paper_1412_4489_gb300 import gks
+    for nx, ny in ((0, 4), (4, 0), (-1, 3), (1 << 16, (1 << 15) + 1), (2, 262140)):
+        with pytest.raises(gks.GKSError) as e:
+            gks.gks_create(nx, ny, 1.0, 1.0, 1.4, 1.0, 0.0)
+        assert e.value.status == gks.GKS_EINVAL

@@ -155,3 +155,31 @@ def test_fp32_bulk_riemann_1024_within_the_schemes_own_sensitivity():
         assert e32 <= 1e-5 + 10 * ectl, (m, e32, ectl)
     for s in (f64, f32, ctl):
         s.close()
+
+
+@pytest.mark.parametrize("prec", [gks.GKS_FP32_BULK, gks.GKS_FP64])
+def test_free_stream_on_a_grid_with_over_2_31_coefficients(prec):
+    """The largest grids: 10400 x 10400 cells, so the coefficient array holds 2.16e9 > 2^31
+    entries (64-bit indexing in every kernel).  A uniform moving state on a periodic grid must
+    stay exactly uniform; its state is set and read through device arrays (17 GB FP64)."""
+    torch = pytest.importorskip("torch")
+    n = 10400
+    rho, u, v, pr, gamma = 1.2, 0.3, -0.2, 0.9, 1.4
+    w = torch.tensor([rho, rho * u, rho * v, pr / (gamma - 1) + 0.5 * rho * (u * u + v * v)],
+                     dtype=torch.float64, device="cuda")
+    s = gks.gks_create(n, n, 1.0, 1.0, gamma, 1.0, 0.0, options=gks.gks_default_options(prec))
+    try:
+        U = w.view(4, 1, 1).expand(4, n, n).contiguous()
+        Wx = w.view(4, 1, 1, 1).expand(4, 2, n, n + 1).contiguous()
+        Wy = w.view(4, 1, 1, 1).expand(4, 2, n + 1, n).contiguous()
+        gks.gks_set_state_device(s, U, Wx, Wy, 0.0)
+        for _ in range(2):
+            gks.gks_step(s, 0.5)
+        gks.gks_get_state_device(s, U, Wx, Wy)
+        for a in (U, Wx, Wy):
+            dev = (a - w.view(4, *([1] * (a.dim() - 1)))).abs().amax().item()
+            assert dev <= (1e-14 if prec == gks.GKS_FP64 else 1e-6), dev
+    finally:
+        gks.gks_destroy(s)
+        del U, Wx, Wy
+        torch.cuda.empty_cache()
