@@ -140,7 +140,10 @@ gks_status gks_create(int nx, int ny, double Lx, double Ly, double gamma, double
 gks_status gks_set_state(gks_handle* h, const double* U, const double* Wx, const double* Wy,
                          double t);
 
-/* Same, from device memory of the handle's device (FP64 arrays). */
+/* Same, from device memory of the handle's device (FP64 arrays).  The reads are
+ * ordered on the handle's stream only: the caller must have finished writing the
+ * arrays with respect to that stream (create the handle on the caller's stream,
+ * or synchronise first).  Synchronous on return. */
 gks_status gks_set_state_device(gks_handle* h, const double* dU, const double* dWx,
                                 const double* dWy, double t);
 
@@ -164,7 +167,9 @@ gks_status gks_sync(gks_handle* h, double* t, long long* steps);
  * Synchronous; returns the pending status (the state is the last good one). */
 gks_status gks_get_state(gks_handle* h, double* U, double* Wx, double* Wy, double* t);
 
-/* Same, into device memory (FP64 arrays). */
+/* Same, into device memory (FP64 arrays).  The writes are ordered on the handle's
+ * stream and complete on return; the arrays must not be in use by other streams
+ * meanwhile. */
 gks_status gks_get_state_device(gks_handle* h, double* dU, double* dWx, double* dWy, double* t);
 
 /* Frees the handle and its device memory.  NULL is ignored. */

@@ -265,6 +265,8 @@ struct gks_handle {
   int prec;
   cudaStream_t stream;
   bool own_stream;
+  cudaStream_t side;              // the y-face evolution runs here, beside the x-faces
+  cudaEvent_t fork, join;         // recon -> y-faces, y-faces -> update
   int device;
   int sms;  // multiprocessors of the device
   double* U[2];      // cell averages (Cells<R>: FP64, or FP32 hi / lo planes), 4 * plane doubles each
@@ -371,15 +373,34 @@ gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double 
   keep(launch_recon<R, TW>(h, force, with_begin_end ? 1 : 0, cfl, dt_max, t_end, pdl));
   mark(1);
   const dim3 b2(32, 8), bf(32, 4);
+  // the x- and y-face evolutions are independent: without per-kernel timing the y-faces run
+  // on a side stream (fork after the reconstruction, join before the update), so that each
+  // fills the other's tail wave
+  const bool fork = ev == nullptr;
+  if (fork) {
+    keep(cudaEventRecord(h->fork, s));
+    keep(cudaStreamWaitEvent(h->side, h->fork, 0));
+    keep(launch(false, k_flux<1, R, TW>, grid2(g.nx, g.ny + 1, bf), bf, h->side, g, fconst<R>(g, 1),
+                cells<R>(h, 0), cells<R>(h, 1), (const R*)h->coef, (TW*)h->Wy[0], (TW*)h->Wy[1], (R*)h->Fy,
+                (const Ctrl*)h->ctrl, force));
+    keep(cudaEventRecord(h->join, h->side));
+  }
   keep(launch(pdl, k_flux<0, R, TW>, grid2(g.nx + 1, g.ny, bf), bf, s, g, fconst<R>(g, 0), cells<R>(h, 0),
          cells<R>(h, 1), (const R*)h->coef, (TW*)h->Wx[0], (TW*)h->Wx[1], (R*)h->Fx, (const Ctrl*)h->ctrl, force));
   mark(2);
-  keep(launch(pdl, k_flux<1, R, TW>, grid2(g.nx, g.ny + 1, bf), bf, s, g, fconst<R>(g, 1), cells<R>(h, 0),
-         cells<R>(h, 1), (const R*)h->coef, (TW*)h->Wy[0], (TW*)h->Wy[1], (R*)h->Fy, (const Ctrl*)h->ctrl, force));
+  if (fork) {
+    keep(cudaStreamWaitEvent(s, h->join, 0));
+  } else {
+    keep(launch(pdl, k_flux<1, R, TW>, grid2(g.nx, g.ny + 1, bf), bf, s, g, fconst<R>(g, 1), cells<R>(h, 0),
+                cells<R>(h, 1), (const R*)h->coef, (TW*)h->Wy[0], (TW*)h->Wy[1], (R*)h->Fy, (const Ctrl*)h->ctrl,
+                force));
+  }
   mark(3);
   for (int pass = 1; pass <= 3; ++pass) {
     if (do_update)
-      keep(launch(pdl, k_update<R, TW>, update_grid(g, pass, h->sms), b2, s, g, cellbuf<R>(h, 0), cellbuf<R>(h, 1),
+      // pass 1 follows the join (two predecessors): an ordinary launch
+      keep(launch(pdl && !(fork && pass == 1), k_update<R, TW>, update_grid(g, pass, h->sms), b2, s, g,
+                  cellbuf<R>(h, 0), cellbuf<R>(h, 1),
                   (const R*)h->Fx, (const R*)h->Fy, (TW*)h->Wx[0], (TW*)h->Wx[1], (TW*)h->Wy[0], (TW*)h->Wy[1],
                   h->bad, h->ctrl, pass));
     mark(3 + pass);
@@ -565,6 +586,9 @@ gks_status gks_create(int nx, int ny, double Lx, double Ly, double gamma, double
     if (cuda_stream) { h->stream = (cudaStream_t)cuda_stream; h->own_stream = false; }
     else { e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking); h->own_stream = true; }
   }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
   auto alloc = [&](void** p, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(p, bytes);
   };
@@ -730,6 +754,10 @@ void gks_destroy(gks_handle* h) {
   cudaFree(h->ctrl);
   cudaFree(h->staging);
   if (h->hctrl) cudaFreeHost(h->hctrl);
+  if (h->side) cudaStreamSynchronize(h->side);
+  if (h->fork) cudaEventDestroy(h->fork);
+  if (h->join) cudaEventDestroy(h->join);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }

@@ -178,7 +178,7 @@ def test_advance_stops_at_t_end():
 def test_device_state_round_trip():
     torch = pytest.importorskip("torch")
     p = _perturbed(21, 17, seed=9)
-    s = gks.Solver(p)
+    s = gks.Solver(p, stream=torch.cuda.current_stream().cuda_stream)  # ordered with torch's work
     U = torch.zeros((4, p.ny, p.nx), dtype=torch.float64, device="cuda")
     Wx = torch.zeros((4, 2, p.ny, p.nx + 1), dtype=torch.float64, device="cuda")
     Wy = torch.zeros((4, 2, p.ny + 1, p.nx), dtype=torch.float64, device="cuda")
