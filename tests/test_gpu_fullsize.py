@@ -167,13 +167,12 @@ def test_free_stream_on_a_grid_with_over_2_31_coefficients(prec):
     rho, u, v, pr, gamma = 1.2, 0.3, -0.2, 0.9, 1.4
     w = torch.tensor([rho, rho * u, rho * v, pr / (gamma - 1) + 0.5 * rho * (u * u + v * v)],
                      dtype=torch.float64, device="cuda")
-    # the handle on torch's stream: the arrays torch fills are read in stream order
-    s = gks.gks_create(n, n, 1.0, 1.0, gamma, 1.0, 0.0, options=gks.gks_default_options(prec),
-                       stream=torch.cuda.current_stream().cuda_stream)
+    s = gks.gks_create(n, n, 1.0, 1.0, gamma, 1.0, 0.0, options=gks.gks_default_options(prec))
     try:
         U = w.view(4, 1, 1).expand(4, n, n).contiguous()
         Wx = w.view(4, 1, 1, 1).expand(4, 2, n, n + 1).contiguous()
         Wy = w.view(4, 1, 1, 1).expand(4, 2, n + 1, n).contiguous()
+        torch.cuda.synchronize()  # the library reads on its own stream
         gks.gks_set_state_device(s, U, Wx, Wy, 0.0)
         for _ in range(2):
             gks.gks_step(s, 0.5)

@@ -178,14 +178,17 @@ def test_advance_stops_at_t_end():
 def test_device_state_round_trip():
     torch = pytest.importorskip("torch")
     p = _perturbed(21, 17, seed=9)
-    s = gks.Solver(p, stream=torch.cuda.current_stream().cuda_stream)  # ordered with torch's work
+    s = gks.Solver(p)
     U = torch.zeros((4, p.ny, p.nx), dtype=torch.float64, device="cuda")
     Wx = torch.zeros((4, 2, p.ny, p.nx + 1), dtype=torch.float64, device="cuda")
     Wy = torch.zeros((4, 2, p.ny + 1, p.nx), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()  # the library works on its own stream
     gks.gks_get_state_device(s.h, U, Wx, Wy)
     assert np.array_equal(U.cpu().numpy(), p.U)
     assert np.array_equal(Wx.cpu().numpy(), p.Wx) and np.array_equal(Wy.cpu().numpy(), p.Wy)
-    gks.gks_set_state_device(s.h, U * 1.0, Wx, Wy, 0.0)
+    U2 = U * 1.0
+    torch.cuda.synchronize()
+    gks.gks_set_state_device(s.h, U2, Wx, Wy, 0.0)
     s.close()
 
 
