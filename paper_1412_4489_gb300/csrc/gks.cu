@@ -93,7 +93,8 @@ template <class R> struct FluxBlocks;
 template <> struct FluxBlocks<double> { static constexpr int value = 1; };
 template <> struct FluxBlocks<float> { static constexpr int value = GKS_FLUX_MINB_F32; };
 
-template <int AX, class R, class TW>
+// NS: Navier-Stokes (1) or Euler (0) face routine, chosen per grid by flux_kernel
+template <int AX, class R, class TW, int NS>
 __global__ void __launch_bounds__(128, FluxBlocks<R>::value) k_flux(Geo g, FaceConst<R> C, const R* U0, const R* U1,
                                                                     const R* __restrict__ coef, TW* Wn0, TW* Wn1,
                                                                     R* __restrict__ F, const Ctrl* c, int force) {
@@ -105,7 +106,12 @@ __global__ void __launch_bounds__(128, FluxBlocks<R>::value) k_flux(Geo g, FaceC
   if (i >= fx || j >= fy) return;
   const int par = (int)(c->steps & 1);
   // new face values go to the other buffer
-  flux_face<AX, R, TW>(g, C, par ? U1 : U0, coef, par ? Wn0 : Wn1, F, i, j, step_dt<R>(c));
+  flux_face<AX, R, TW, NS>(g, C, par ? U1 : U0, coef, par ? Wn0 : Wn1, F, i, j, step_dt<R>(c));
+}
+
+template <int AX, class R, class TW>
+auto flux_kernel(const Geo& g) -> decltype(&k_flux<AX, R, TW, 1>) {
+  return g.mu > 0.0 ? &k_flux<AX, R, TW, 1> : &k_flux<AX, R, TW, 0>;
 }
 
 // ---------------------------------------------------------------------------
@@ -380,18 +386,18 @@ gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double 
   if (fork) {
     keep(cudaEventRecord(h->fork, s));
     keep(cudaStreamWaitEvent(h->side, h->fork, 0));
-    keep(launch(false, k_flux<1, R, TW>, grid2(g.nx, g.ny + 1, bf), bf, h->side, g, fconst<R>(g, 1),
+    keep(launch(false, flux_kernel<1, R, TW>(g), grid2(g.nx, g.ny + 1, bf), bf, h->side, g, fconst<R>(g, 1),
                 cells<R>(h, 0), cells<R>(h, 1), (const R*)h->coef, (TW*)h->Wy[0], (TW*)h->Wy[1], (R*)h->Fy,
                 (const Ctrl*)h->ctrl, force));
     keep(cudaEventRecord(h->join, h->side));
   }
-  keep(launch(pdl, k_flux<0, R, TW>, grid2(g.nx + 1, g.ny, bf), bf, s, g, fconst<R>(g, 0), cells<R>(h, 0),
+  keep(launch(pdl, flux_kernel<0, R, TW>(g), grid2(g.nx + 1, g.ny, bf), bf, s, g, fconst<R>(g, 0), cells<R>(h, 0),
          cells<R>(h, 1), (const R*)h->coef, (TW*)h->Wx[0], (TW*)h->Wx[1], (R*)h->Fx, (const Ctrl*)h->ctrl, force));
   mark(2);
   if (fork) {
     keep(cudaStreamWaitEvent(s, h->join, 0));
   } else {
-    keep(launch(pdl, k_flux<1, R, TW>, grid2(g.nx, g.ny + 1, bf), bf, s, g, fconst<R>(g, 1), cells<R>(h, 0),
+    keep(launch(pdl, flux_kernel<1, R, TW>(g), grid2(g.nx, g.ny + 1, bf), bf, s, g, fconst<R>(g, 1), cells<R>(h, 0),
                 cells<R>(h, 1), (const R*)h->coef, (TW*)h->Wy[0], (TW*)h->Wy[1], (R*)h->Fy, (const Ctrl*)h->ctrl,
                 force));
   }
@@ -938,9 +944,9 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
       g, U0, U1, dWx, dWx_out, dWy, dWy_out, coef, g.dx, g.dy,
                                                             g.weno_eps, g.weno_C, ctrl, 0, 1, CFL,
                                                             dt_max, INFINITY);
-  k_flux<0, double, double><<<grid2(nx + 1, ny, bf), bf, 0, s>>>(g, fconst<double>(g, 0), U0, U1, coef,
+  flux_kernel<0, double, double>(g)<<<grid2(nx + 1, ny, bf), bf, 0, s>>>(g, fconst<double>(g, 0), U0, U1, coef,
                                                                   const_cast<double*>(dWx), dWx_out, Fx, ctrl, 0);
-  k_flux<1, double, double><<<grid2(nx, ny + 1, bf), bf, 0, s>>>(g, fconst<double>(g, 1), U0, U1, coef,
+  flux_kernel<1, double, double>(g)<<<grid2(nx, ny + 1, bf), bf, 0, s>>>(g, fconst<double>(g, 1), U0, U1, coef,
                                                                   const_cast<double*>(dWy), dWy_out, Fy, ctrl, 0);
   for (int pass = 1; pass <= 3; ++pass)
     k_update<double, double><<<update_grid(g, pass, 0), b2, 0, s>>>(g, C0, C1, Fx, Fy, const_cast<double*>(dWx), dWx_out,

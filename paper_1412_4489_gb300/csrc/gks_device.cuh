@@ -89,6 +89,23 @@ GKS_FN void moments(R U, R V, R lam, R K, int kind, Moments<R, NU, NV>& m) {
   m.xi4 = K * (K + R(2)) * var * var;
 }
 
+// The same half-space moments from their first two entries h = <u^0>, g = <u^1>
+// (already formed once for the same Maxwellian: no second erfc and exp).
+template <class R, int NU, int NV>
+GKS_FN void moments_from(R U, R V, R lam, R K, R h, R g, Moments<R, NU, NV>& m) {
+  const R var = d_div(R(0.5), lam);
+  m.u[0] = h;
+  m.u[1] = g;
+#pragma unroll
+  for (int n = 2; n < NU; ++n) m.u[n] = U * m.u[n - 1] + R(n - 1) * var * m.u[n - 2];
+  m.v[0] = R(1);
+  m.v[1] = V;
+#pragma unroll
+  for (int n = 2; n < NV; ++n) m.v[n] = V * m.v[n - 1] + R(n - 1) * var * m.v[n - 2];
+  m.xi2 = K * var;
+  m.xi4 = K * (K + R(2)) * var * var;
+}
+
 // <u^A v^B psi> and <xi^2 u^A v^B psi>, psi = (1, u, v, (u^2+v^2+xi^2)/2)
 template <int A, int B, class R, int NU, int NV>
 GKS_FN void psi_mom(const Moments<R, NU, NV>& m, R o[4]) {
@@ -425,19 +442,35 @@ GKS_FN void hydro_groups(const Coefs<R>& c, const R* W, R y2, Groups<R>& g) {
   g.X1[0] += W[1];
 }
 
-// Eq. dis2 grouped for one side; tn = tau for the Navier-Stokes f_G, 0 for Euler
-template <class R>
+// Eq. dis2 grouped for one side.  NS: f_G = g_k - tau (a u + A) g_k with the time
+// coefficients c.A, c.Atx, c.Aty and tn = tau; Euler: f_G = g_k, and the terms
+// with tn are absent (not formed).
+template <bool NS, class R>
 GKS_FN void kinetic_groups(const Coefs<R>& c, const R* W, R y2, R tn, Groups<R>& g) {
-  const R w78 = W[8] - tn * W[7];
-  const R wq = R(0.5) * W[10] - tn * W[8];
+  const R h7 = R(0.5) * y2 * W[7];
+  if (NS) {
+    const R w78 = W[8] - tn * W[7], t7 = tn * W[7], t8 = tn * W[8];
+    const R wq = R(0.5) * W[10] - t8;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    g.X1[k] = -tn * W[7] * c.A[k] + R(0.5) * y2 * W[7] * c.Ayy[k];
-    g.Xu[k] = w78 * c.a1[k] - tn * W[8] * c.Atx[k];
-    g.Xv[k] = w78 * c.a2[k] - tn * W[8] * c.Aty[k];
-    g.Xuu[k] = wq * c.Axx[k];
-    g.Xuv[k] = R(2) * wq * c.Axy[k];
-    g.Xvv[k] = wq * c.Ayy[k];
+    for (int k = 0; k < 4; ++k) {
+      g.X1[k] = h7 * c.Ayy[k] - t7 * c.A[k];
+      g.Xu[k] = w78 * c.a1[k] - t8 * c.Atx[k];
+      g.Xv[k] = w78 * c.a2[k] - t8 * c.Aty[k];
+      g.Xuu[k] = wq * c.Axx[k];
+      g.Xuv[k] = R(2) * wq * c.Axy[k];
+      g.Xvv[k] = wq * c.Ayy[k];
+    }
+  } else {
+    const R wq = R(0.5) * W[10];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      g.X1[k] = h7 * c.Ayy[k];
+      g.Xu[k] = W[8] * c.a1[k];
+      g.Xv[k] = W[8] * c.a2[k];
+      g.Xuu[k] = wq * c.Axx[k];
+      g.Xuv[k] = W[10] * c.Axy[k];
+      g.Xvv[k] = wq * c.Ayy[k];
+    }
   }
   g.X1[0] += W[7];
 }
@@ -597,10 +630,13 @@ GKS_FN void wall_image(int kind, R gamma, R uwt, R Tw, const FaceState<R>& in, F
 // which are called where they are needed so that they need not stay live in
 // registers.  Outputs the time-integrated face-mean flux and the point values
 // at the two Gauss points (tangential -/+ sqrt(3)/6 dtan) at t = dt.
+// NSM: 1 Navier-Stokes, 0 Euler (mu = 0: the terms of the time derivatives of
+// g_k vanish and are not formed), -1 decided at run time by C.ns.
 // ---------------------------------------------------------------------------
-template <class R, class Src>
+template <class R, int NSM = -1, class Src>
 GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], R Wm[4], R Wp[4]) {
-  R rs[2], us[2], vs[2], ls[2], ps[2];
+  const bool ns = NSM < 0 ? C.ns : NSM == 1;
+  R rs[2], us[2], vs[2], ls[2], ps[2], h0[2], h1[2];
   R U0[4] = {R(0), R(0), R(0), R(0)};
   // Eq. compatibility2: U0 = rho_l <psi>_{u>0} + rho_r <psi>_{u<0}
 #pragma unroll
@@ -611,6 +647,8 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
     ls[k] = d_div(R(0.5) * rs[k], ps[k]);
     Moments<R, 4, 3> m;
     moments(us[k], vs[k], ls[k], C.K, k == 0 ? +1 : -1, m);
+    h0[k] = m.u[0];
+    h1[k] = m.u[1];
     R a[4];
     psi_mom<0, 0>(m, a);
 #pragma unroll
@@ -622,8 +660,8 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
 
   // Section 4: collision time
   const R jump = fabs(d_div(ps[0] - ps[1], ps[0] + ps[1])) * dt;
-  const R tau = C.ns ? d_div(C.mu, p0) + jump : C.tau_eps * dt + C.tau_C * jump;
-  const R tn = C.ns ? tau : R(0);
+  const R tau = ns ? d_div(C.mu, p0) + jump : C.tau_eps * dt + C.tau_C * jump;
+  const R tn = ns ? tau : R(0);
 
   TimeW<R> tw;
   time_weights(dt, tau, tw);
@@ -686,28 +724,38 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
           for (int k = 0; k < 4; ++k) d[q][k] = S.w[q + 1][k];
       }
       Moments<R, 6, 6> mf;  // full-space moments fix the time coefficients of g_k (NS only)
-      if (C.ns) moments(U, V, lam, C.K, 0, mf);
-      coef_systems(mf, rho, solve_k(U, V, lam, C.N, C.iN), d, C.ns, false, c);
-    }
-    if (!C.ns) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) c.A[k] = c.Atx[k] = c.Aty[k] = R(0);
+      if (ns) moments(U, V, lam, C.K, 0, mf);
+      coef_systems(mf, rho, solve_k(U, V, lam, C.N, C.iN), d, ns, false, c);
     }
     Moments<R, 8, 7> mh;
-    moments(U, V, lam, C.K, side == 0 ? +1 : -1, mh);
+    moments_from(U, V, lam, C.K, side ? h0[1] : h0[0], side ? h1[1] : h1[0], mh);
     Groups<R> g;
-    kinetic_groups(c, tw.I, C.y2, tn, g);
-    add_flux(g, mh, rho, Fl);
-    if (C.prandtl) add_point(g, mh, rho, Mn);
-    kinetic_groups(c, tw.E, C.y2, tn, g);
-    add_point(g, mh, rho, P0);
     R Y1[4], Yu[4], Yv[4];
-    const R wy = -tn * tw.E[7] - tw.E[9];
+    if (ns) {
+      kinetic_groups<true>(c, tw.I, C.y2, tn, g);
+      add_flux(g, mh, rho, Fl);
+      if (C.prandtl) add_point(g, mh, rho, Mn);
+      kinetic_groups<true>(c, tw.E, C.y2, tn, g);
+      add_point(g, mh, rho, P0);
+      const R wy = -tn * tw.E[7] - tw.E[9];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      Y1[k] = tw.E[7] * (c.a2[k] - tn * c.Aty[k]);
-      Yu[k] = wy * c.Axy[k];
-      Yv[k] = wy * c.Ayy[k];
+      for (int k = 0; k < 4; ++k) {
+        Y1[k] = tw.E[7] * (c.a2[k] - tn * c.Aty[k]);
+        Yu[k] = wy * c.Axy[k];
+        Yv[k] = wy * c.Ayy[k];
+      }
+    } else {
+      kinetic_groups<false>(c, tw.I, C.y2, tn, g);
+      add_flux(g, mh, rho, Fl);
+      if (C.prandtl) add_point(g, mh, rho, Mn);
+      kinetic_groups<false>(c, tw.E, C.y2, tn, g);
+      add_point(g, mh, rho, P0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        Y1[k] = tw.E[7] * c.a2[k];
+        Yu[k] = -tw.E[9] * c.Axy[k];
+        Yv[k] = -tw.E[9] * c.Ayy[k];
+      }
     }
     add_point_linear(Y1, Yu, Yv, mh, rho, P1);
   }

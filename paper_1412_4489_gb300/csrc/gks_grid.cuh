@@ -609,7 +609,8 @@ __host__ __device__ inline FaceConst<R> grid_face_const(const Geo& g, int axis) 
 }
 
 // the evolution at face (i, j) of axis AX: flux F and new point values Wn
-template <int AX, class R, class TW>
+// (NSM: Navier-Stokes 1, Euler 0, decided per grid at run time -1)
+template <int AX, class R, class TW, int NSM = -1>
 __device__ __forceinline__ void flux_face(const Geo& g, const FaceConst<R>& C, const R* U, const R* __restrict__ coef,
                                           TW* __restrict__ Wn, R* __restrict__ F, int i, int j, R dt) {
   const int nx = g.nx, ny = g.ny;
@@ -646,7 +647,7 @@ __device__ __forceinline__ void flux_face(const Geo& g, const FaceConst<R>& C, c
   src.first_order = false;
 
   R Fl[4], Wm[4], Wp[4];
-  face_evolution<R>(C, src, dt, Fl, Wm, Wp);
+  face_evolution<R, NSM>(C, src, dt, Fl, Wm, Wp);
   if (src.img_lo) wall_face_flux<R>(src.img_lo, src.uwt_lo, Fl);
   else if (src.img_hi) wall_face_flux<R>(src.img_hi, src.uwt_hi, Fl);
 

@@ -92,7 +92,9 @@ void count_face(const double* L, const double* R, const double* avg, double dn, 
   src.a = av;
   const gks::FaceConst<N> C = gks::face_const<N>(FP);
   opc::C = opc::Counts{};  // per-launch constants are not per-face work
-  gks::face_evolution<N>(C, src, N(dt), F, Wm, Wp);
+  // the routine the face kernels run: Navier-Stokes for mu > 0, Euler otherwise
+  if (mu > 0.0) gks::face_evolution<N, 1>(C, src, N(dt), F, Wm, Wp);
+  else gks::face_evolution<N, 0>(C, src, N(dt), F, Wm, Wp);
 }
 
 template <class R>
