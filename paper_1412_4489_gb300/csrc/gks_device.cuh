@@ -80,11 +80,12 @@ GKS_FN void moments(R U, R V, R lam, R K, int kind, Moments<R, NU, NV>& m) {
     m.u[1] = U * h + R(kind) * b;
   }
 #pragma unroll
-  for (int n = 2; n < NU; ++n) m.u[n] = U * m.u[n - 1] + R(n - 1) * var * m.u[n - 2];
+  for (int n = 2; n < NU; ++n) m.u[n] = U * m.u[n - 1] + (n == 2 ? var : R(n - 1) * var) * m.u[n - 2];
   m.v[0] = R(1);
   m.v[1] = V;
+  m.v[2] = V * V + var;
 #pragma unroll
-  for (int n = 2; n < NV; ++n) m.v[n] = V * m.v[n - 1] + R(n - 1) * var * m.v[n - 2];
+  for (int n = 3; n < NV; ++n) m.v[n] = V * m.v[n - 1] + R(n - 1) * var * m.v[n - 2];
   m.xi2 = K * var;
   m.xi4 = K * (K + R(2)) * var * var;
 }
@@ -97,11 +98,12 @@ GKS_FN void moments_from(R U, R V, R lam, R K, R h, R g, Moments<R, NU, NV>& m) 
   m.u[0] = h;
   m.u[1] = g;
 #pragma unroll
-  for (int n = 2; n < NU; ++n) m.u[n] = U * m.u[n - 1] + R(n - 1) * var * m.u[n - 2];
+  for (int n = 2; n < NU; ++n) m.u[n] = U * m.u[n - 1] + (n == 2 ? var : R(n - 1) * var) * m.u[n - 2];
   m.v[0] = R(1);
   m.v[1] = V;
+  m.v[2] = V * V + var;
 #pragma unroll
-  for (int n = 2; n < NV; ++n) m.v[n] = V * m.v[n - 1] + R(n - 1) * var * m.v[n - 2];
+  for (int n = 3; n < NV; ++n) m.v[n] = V * m.v[n - 1] + R(n - 1) * var * m.v[n - 2];
   m.xi2 = K * var;
   m.xi4 = K * (K + R(2)) * var * var;
 }
@@ -117,24 +119,52 @@ GKS_FN void psi_mom(const Moments<R, NU, NV>& m, R o[4]) {
   o[3] = R(0.5) * (m.u[A + 2] * m.v[B] + m.u[A] * m.v[B + 2] + ab * m.xi2);
 }
 
-// <X u^A v^B psi> for X = X0 + X1 u + X2 v + X3 (u^2+v^2+xi^2)/2
+// <X u psi> and <X v psi> for X = X0 + X1 u + X2 v + X3 (u^2+v^2+xi^2)/2 are
+// X0 T_A + X1 T_(A+u) + X2 T_(A+v) + X3 S_A with the psi-moment vectors T and
+// S_A = (<u^2 A psi> + <v^2 A psi> + <xi^2 A psi>)/2, A = u or v: a table formed
+// once per Maxwellian.
+template <class R>
+struct MomTab {
+  R Tu[4], Tuu[4], Tuv[4], Tv[4], Tvv[4], Su[4], Sv[4];
+};
+
+// <xi^2 u^A v^B psi>
 template <int A, int B, class R, int NU, int NV>
-GKS_FN void coef_mom(const R X[4], const Moments<R, NU, NV>& m, R o[4]) {
-  R p0[4], p1[4], p2[4], pa[4], pb[4];
-  psi_mom<A, B>(m, p0);
-  psi_mom<A + 1, B>(m, p1);
-  psi_mom<A, B + 1>(m, p2);
-  psi_mom<A + 2, B>(m, pa);
-  psi_mom<A, B + 2>(m, pb);
+GKS_FN void xi2_psi_mom(const Moments<R, NU, NV>& m, R o[4]) {
   const R ab = m.u[A] * m.v[B];
-  R pc[4];
-  pc[0] = m.xi2 * ab;
-  pc[1] = m.xi2 * m.u[A + 1] * m.v[B];
-  pc[2] = m.xi2 * m.u[A] * m.v[B + 1];
-  pc[3] = R(0.5) * (m.xi2 * (m.u[A + 2] * m.v[B] + m.u[A] * m.v[B + 2]) + m.xi4 * ab);
-  const R h = R(0.5) * X[3];
+  o[0] = m.xi2 * ab;
+  o[1] = m.xi2 * (m.u[A + 1] * m.v[B]);
+  o[2] = m.xi2 * (m.u[A] * m.v[B + 1]);
+  o[3] = R(0.5) * (m.xi2 * (m.u[A + 2] * m.v[B] + m.u[A] * m.v[B + 2]) + m.xi4 * ab);
+}
+
+template <class R, int NU, int NV>
+GKS_FN void mom_tab(const Moments<R, NU, NV>& m, MomTab<R>& t) {
+  psi_mom<1, 0>(m, t.Tu);
+  psi_mom<2, 0>(m, t.Tuu);
+  psi_mom<1, 1>(m, t.Tuv);
+  psi_mom<0, 1>(m, t.Tv);
+  psi_mom<0, 2>(m, t.Tvv);
+  R a[4], b[4], c[4];
+  psi_mom<3, 0>(m, a);
+  psi_mom<1, 2>(m, b);
+  xi2_psi_mom<1, 0>(m, c);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) o[k] = X[0] * p0[k] + X[1] * p1[k] + X[2] * p2[k] + h * (pa[k] + pb[k] + pc[k]);
+  for (int k = 0; k < 4; ++k) t.Su[k] = R(0.5) * (a[k] + b[k] + c[k]);
+  psi_mom<2, 1>(m, a);
+  psi_mom<0, 3>(m, b);
+  xi2_psi_mom<0, 1>(m, c);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) t.Sv[k] = R(0.5) * (a[k] + b[k] + c[k]);
+}
+
+// r = -(<X u psi> + <Y v psi>)
+template <class R>
+GKS_FN void neg_coef_mom(const MomTab<R>& t, const R X[4], const R Y[4], R r[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    r[k] = -(X[0] * t.Tu[k] + X[1] * t.Tuu[k] + X[2] * t.Tuv[k] + X[3] * t.Su[k] +
+             Y[0] * t.Tv[k] + Y[1] * t.Tuv[k] + Y[2] * t.Tvv[k] + Y[3] * t.Sv[k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -276,27 +306,16 @@ GKS_FN void coef_systems(const Moments<R, NU, NV>& m, R rho, const SolveK<R>& sk
   for (int k = 0; k < 4; ++k) r[k] = d[4][k] * ir;
   solve(sk, r, c.Ayy);
   if (!time_terms) return;
-  R p[4], q[4];
-  coef_mom<1, 0>(c.a1, m, p);  // <A + a1 u + a2 v> = 0
-  coef_mom<0, 1>(c.a2, m, q);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) r[k] = -(p[k] + q[k]);
+  MomTab<R> t;
+  mom_tab(m, t);
+  neg_coef_mom(t, c.a1, c.a2, r);  // <A + a1 u + a2 v> = 0
   solve(sk, r, c.A);
-  coef_mom<1, 0>(c.Axx, m, p);  // <Axx u + Axy v + Atx> = 0
-  coef_mom<0, 1>(c.Axy, m, q);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) r[k] = -(p[k] + q[k]);
+  neg_coef_mom(t, c.Axx, c.Axy, r);  // <Axx u + Axy v + Atx> = 0
   solve(sk, r, c.Atx);
-  coef_mom<1, 0>(c.Axy, m, p);  // <Axy u + Ayy v + Aty> = 0
-  coef_mom<0, 1>(c.Ayy, m, q);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) r[k] = -(p[k] + q[k]);
+  neg_coef_mom(t, c.Axy, c.Ayy, r);  // <Axy u + Ayy v + Aty> = 0
   solve(sk, r, c.Aty);
   if (!second_time) return;
-  coef_mom<1, 0>(c.Atx, m, p);  // <Atx u + Aty v + Att> = 0
-  coef_mom<0, 1>(c.Aty, m, q);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) r[k] = -(p[k] + q[k]);
+  neg_coef_mom(t, c.Atx, c.Aty, r);  // <Atx u + Aty v + Att> = 0
   solve(sk, r, c.Att);
 }
 
@@ -372,23 +391,27 @@ GKS_FN void poly_moments(const Poly<R>& P, const Moments<R, NU, NV>& m, R rho, R
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
     const int Dc = c == 0 ? D : D1;
-    const R xa = c == 0 ? R(1) : m.xi2;    // <xi^2c>
-    const R xb = c == 0 ? m.xi2 : m.xi4;  // <xi^2(c+1)>
 #pragma unroll
     for (int b = 0; b <= Dc; ++b) {
-      R s0 = R(0), s1 = R(0), s2 = R(0);  // sum_a p u^(a+SU), u^(a+SU+1), u^(a+SU+2) moments
+      // sum_a p u^(a+SU), u^(a+SU+1), u^(a+SU+2) moments (the first term starts each sum)
+      R s0 = R(0), s1 = R(0), s2 = R(0);
 #pragma unroll
       for (int a = 0; a <= Dc - b; ++a) {
         const R p = c == 0 ? P.c0[pidx0(a, b)] : P.c1[pidx1(a, b)];
-        s0 += p * m.u[a + SU];
-        s1 += p * m.u[a + SU + 1];
-        s2 += p * m.u[a + SU + 2];
+        s0 = a == 0 ? p * m.u[SU] : s0 + p * m.u[a + SU];
+        s1 = a == 0 ? p * m.u[SU + 1] : s1 + p * m.u[a + SU + 1];
+        s2 = a == 0 ? p * m.u[SU + 2] : s2 + p * m.u[a + SU + 2];
       }
-      const R vb = xa * m.v[b];
-      o0 += s0 * vb;
-      o1 += s1 * vb;
-      o2 += s0 * (xa * m.v[b + 1]);
-      o3 += s2 * vb + s0 * (xa * m.v[b + 2] + xb * m.v[b]);
+      // <xi^2c v^b>, <xi^2c v^(b+1)>, <xi^2c v^(b+2)> + <xi^2(c+1) v^b> (v^0 = 1)
+      const R vb = c == 0 ? (b == 0 ? R(1) : m.v[b]) : (b == 0 ? m.xi2 : m.xi2 * m.v[b]);
+      const R vb1 = c == 0 ? m.v[b + 1] : m.xi2 * m.v[b + 1];
+      const R vb2 = c == 0 ? m.v[b + 2] + (b == 0 ? m.xi2 : m.xi2 * m.v[b])
+                           : m.xi2 * m.v[b + 2] + (b == 0 ? m.xi4 : m.xi4 * m.v[b]);
+      const bool first = c == 0 && b == 0;
+      o0 = first ? s0 * vb : o0 + s0 * vb;
+      o1 = first ? s1 * vb : o1 + s1 * vb;
+      o2 = first ? s0 * vb1 : o2 + s0 * vb1;
+      o3 = first ? s2 * vb + s0 * vb2 : o3 + (s2 * vb + s0 * vb2);
     }
   }
   out[0] += rho * o0;
@@ -430,14 +453,15 @@ GKS_FN void add_point_linear(const R Y1[4], const R Yu[4], const R Yv[4], const 
 // the face mean of y^2 and y^2 at the Gauss points.
 template <class R>
 GKS_FN void hydro_groups(const Coefs<R>& c, const R* W, R y2, Groups<R>& g) {
+  const R h5 = R(0.5) * W[5], hy = R(0.5) * y2 * W[1], h4 = R(0.5) * W[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    g.X1[k] = W[3] * c.A[k] + R(0.5) * W[5] * c.Att[k] + R(0.5) * y2 * W[1] * c.Ayy[k];
+    g.X1[k] = W[3] * c.A[k] + h5 * c.Att[k] + hy * c.Ayy[k];
     g.Xu[k] = W[2] * c.a1[k] + W[6] * c.Atx[k];
     g.Xv[k] = W[2] * c.a2[k] + W[6] * c.Aty[k];
-    g.Xuu[k] = R(0.5) * W[4] * c.Axx[k];
+    g.Xuu[k] = h4 * c.Axx[k];
     g.Xuv[k] = W[4] * c.Axy[k];
-    g.Xvv[k] = R(0.5) * W[4] * c.Ayy[k];
+    g.Xvv[k] = h4 * c.Ayy[k];
   }
   g.X1[0] += W[1];
 }
@@ -449,15 +473,15 @@ template <bool NS, class R>
 GKS_FN void kinetic_groups(const Coefs<R>& c, const R* W, R y2, R tn, Groups<R>& g) {
   const R h7 = R(0.5) * y2 * W[7];
   if (NS) {
-    const R w78 = W[8] - tn * W[7], t7 = tn * W[7], t8 = tn * W[8];
-    const R wq = R(0.5) * W[10] - t8;
+    const R t7 = tn * W[7], t8 = tn * W[8];
+    const R w78 = W[8] - t7, wq = R(0.5) * W[10] - t8, wq2 = W[10] - R(2) * t8;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       g.X1[k] = h7 * c.Ayy[k] - t7 * c.A[k];
       g.Xu[k] = w78 * c.a1[k] - t8 * c.Atx[k];
       g.Xv[k] = w78 * c.a2[k] - t8 * c.Aty[k];
       g.Xuu[k] = wq * c.Axx[k];
-      g.Xuv[k] = R(2) * wq * c.Axy[k];
+      g.Xuv[k] = wq2 * c.Axy[k];
       g.Xvv[k] = wq * c.Ayy[k];
     }
   } else {

@@ -130,12 +130,15 @@ def test_fp32_bulk_against_fp64_oracle_l1(case):
 def test_fp32_bulk_riemann_1024_within_the_schemes_own_sensitivity():
     """The 1024^2 Navier-Stokes Riemann workload for its 200 steps, FP32-bulk against FP64 (the
     oracle-pinned path).  The seeded quadrants put vortex sheets against the outflow boundaries;
-    their grid-scale growth makes the FP64 scheme diverge from itself when its start is
-    perturbed by 1e-12 (L1 ~1e-2 by step 200).  So the 1e-5 bound holds up to step 100; after
-    that FP32's deviation must stay within 1e-5 + 10x that FP64 control's."""
+    their grid-scale growth amplifies any perturbation: an FP64 run whose start is perturbed by
+    1e-12 drifts to L1 ~4e-4 by step 200.  So the 1e-5 bound holds up to step 100; after that
+    FP32's deviation is compared with the FP64 scheme's response to the perturbation FP32-bulk
+    itself makes first, its start with the face point values rounded to FP32: it must stay
+    within 1e-5 + 10x that control's deviation."""
     p = wl.riemann_2d(1024, seed=3, mu=1e-4, Pr=0.72)
     q = wl.riemann_2d(1024, seed=3, mu=1e-4, Pr=0.72)
-    q.U = q.U * (1.0 + 1e-12 * np.random.default_rng(1).standard_normal(q.U.shape))
+    q.Wx = q.Wx.astype(np.float32).astype(np.float64)
+    q.Wy = q.Wy.astype(np.float32).astype(np.float64)
     f64 = gks.Solver(p, gks.GKS_FP64, tau_eps=0.05)
     f32 = gks.Solver(p, gks.GKS_FP32_BULK, tau_eps=0.05)
     ctl = gks.Solver(q, gks.GKS_FP64, tau_eps=0.05)
@@ -150,6 +153,7 @@ def test_fp32_bulk_riemann_1024_within_the_schemes_own_sensitivity():
             s.advance(m - done, 0.5)
         done = m
         e32, ectl = l1(f32, f64), l1(ctl, f64)
+        print(f"step {m}: FP32-bulk L1 {e32:.3e}, FP64 from FP32-rounded face values L1 {ectl:.3e}")
         if m <= 100:
             assert e32 <= 1e-5, (m, e32)
         assert e32 <= 1e-5 + 10 * ectl, (m, e32, ectl)
