@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(256, UpdateBlocks<R>::value) k_update(Geo g, C
   pdl_enter();
   if (c->skip || (pass == 2 && !c->bad_found[0]) || (pass == 3 && !c->bad_found[1])) return;
   const int par = (int)(c->steps & 1);
+  R inv_max = R(0);  // over the block's tiles: one block reduction per block
   for (int j0 = blockIdx.y * blockDim.y; j0 < g.ny; j0 += gridDim.y * blockDim.y) {
     for (int i0 = blockIdx.x * blockDim.x; i0 < g.nx; i0 += gridDim.x * blockDim.x) {
       const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
@@ -153,15 +154,24 @@ __global__ void __launch_bounds__(256, UpdateBlocks<R>::value) k_update(Geo g, C
           c->fail_step = c->steps;
         }
       }
-      block_bound_to<R>(inv, &c->dtb[pass - 1]);
+      inv_max = fmax(inv_max, inv);
     }
   }
+  block_bound_to<R>(inv_max, &c->dtb[pass - 1]);
 }
 
-// launch grid of an update pass: one block per 32 x 8 tile for pass 1; for the
-// fallback passes at most 8 x (SMs / 2) blocks (four per SM)
-dim3 update_grid(const Geo& g, int pass, int sms) {
+// launch grid of an update pass (32 x 8 tiles): pass 1 takes one wave of resident
+// blocks (blocks_per_sm per SM), each walking ceil(tiles / wave) tiles along y, so
+// that the per-block work (control reads, the CFL reduction) is shared by its tiles;
+// the fallback passes at most 8 x (SMs / 2) blocks (usually no work)
+dim3 update_grid(const Geo& g, int pass, int sms, int blocks_per_sm) {
   unsigned tx = (unsigned)((g.nx + 31) / 32), ty = (unsigned)((g.ny + 7) / 8);
+  if (pass == 1 && sms > 0) {
+    const unsigned wave = (unsigned)sms * (unsigned)blocks_per_sm;
+    const unsigned rows = wave / tx > 0 ? wave / tx : 1;  // block rows that fit in one wave
+    const unsigned k = (ty + rows - 1) / rows;            // tiles per block
+    ty = (ty + k - 1) / k;
+  }
   if (pass > 1) {
     const unsigned cy = (unsigned)(sms > 1 ? sms / 2 : 76);
     if (tx > 8) tx = 8;
@@ -405,7 +415,7 @@ gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double 
   for (int pass = 1; pass <= 3; ++pass) {
     if (do_update)
       // pass 1 follows the join (two predecessors): an ordinary launch
-      keep(launch(pdl && !(fork && pass == 1), k_update<R, TW>, update_grid(g, pass, h->sms), b2, s, g,
+      keep(launch(pdl && !(fork && pass == 1), k_update<R, TW>, update_grid(g, pass, h->sms, UpdateBlocks<R>::value), b2, s, g,
                   cellbuf<R>(h, 0), cellbuf<R>(h, 1),
                   (const R*)h->Fx, (const R*)h->Fy, (TW*)h->Wx[0], (TW*)h->Wx[1], (TW*)h->Wy[0], (TW*)h->Wy[1],
                   h->bad, h->ctrl, pass));
@@ -949,7 +959,7 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
   flux_kernel<1, double, double>(g)<<<grid2(nx, ny + 1, bf), bf, 0, s>>>(g, fconst<double>(g, 1), U0, U1, coef,
                                                                   const_cast<double*>(dWy), dWy_out, Fy, ctrl, 0);
   for (int pass = 1; pass <= 3; ++pass)
-    k_update<double, double><<<update_grid(g, pass, 0), b2, 0, s>>>(g, C0, C1, Fx, Fy, const_cast<double*>(dWx), dWx_out,
+    k_update<double, double><<<update_grid(g, pass, 0, UpdateBlocks<double>::value), b2, 0, s>>>(g, C0, C1, Fx, Fy, const_cast<double*>(dWx), dWx_out,
                                                               const_cast<double*>(dWy), dWy_out, bad, ctrl, pass);
   k_end<<<1, 1, 0, s>>>(ctrl);
   k_scatter_U<double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, dU_out, C0, C1, ctrl, 0);
