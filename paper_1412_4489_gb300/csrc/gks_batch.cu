@@ -111,7 +111,9 @@ template <class R> struct BatchBlocks;
 template <> struct BatchBlocks<double> { static constexpr int value = 1; };
 template <> struct BatchBlocks<float> { static constexpr int value = GKS_BATCH_MINB_F32; };
 
-template <class R, class TW>
+// NSM = 1: every grid has mu > 0 (the Navier-Stokes face routine only); -1: the face
+// routine decides per grid
+template <class R, class TW, int NSM>
 __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<R, TW> a, int nsteps) {
   const int tid = threadIdx.x;
   for (int s = 0; s < nsteps; ++s) {
@@ -157,10 +159,11 @@ __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<
       const R dt = step_dt<R>(c);
       if (w.w == 0) {
         if (i <= g.nx && j < g.ny)
-          flux_face<0, R, TW>(g, a.fc[2 * w.x], U, a.coef + o.coef, a.Wx[par ^ 1] + o.wx, a.Fx + o.fx, i, j, dt);
+          flux_face<0, R, TW, NSM>(g, a.fc[2 * w.x], U, a.coef + o.coef, a.Wx[par ^ 1] + o.wx, a.Fx + o.fx, i, j, dt);
       } else {
         if (i < g.nx && j <= g.ny)
-          flux_face<1, R, TW>(g, a.fc[2 * w.x + 1], U, a.coef + o.coef, a.Wy[par ^ 1] + o.wy, a.Fy + o.fy, i, j, dt);
+          flux_face<1, R, TW, NSM>(g, a.fc[2 * w.x + 1], U, a.coef + o.coef, a.Wy[par ^ 1] + o.wy, a.Fy + o.fy, i, j,
+                                   dt);
       }
     }
     if (!grid_barrier(a.bar)) return;
@@ -287,6 +290,7 @@ struct gks_batch {
   size_t staging_n;
   // launch configuration
   int face_tw, cell_tw, blocks_per_sm, max_blocks_per_sm;
+  bool all_ns;  // every grid has mu > 0: the kernel with the Navier-Stokes face routine only
   double timeout_s;
   int skip_block;
   cudaGraphExec_t graph;
@@ -376,7 +380,7 @@ gks_status launch(gks_batch* b, int nsteps, double cfl) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  BCK(cudaLaunchKernelEx(&cfg, k_batch<R, TW>, a, nsteps));
+  BCK(cudaLaunchKernelEx(&cfg, b->all_ns ? k_batch<R, TW, 1> : k_batch<R, TW, -1>, a, nsteps));
   return GKS_OK;
 }
 
@@ -403,9 +407,11 @@ void drop_graph(gks_batch* b) {
 int occupancy(gks_batch* b) {
   int n = 0;
   if (b->prec == GKS_FP64)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<double, double>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &n, b->all_ns ? k_batch<double, double, 1> : k_batch<double, double, -1>, kThreads, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<float, float>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, b->all_ns ? k_batch<float, float, 1> : k_batch<float, float, -1>,
+                                                  kThreads, 0);
   return n;
 }
 
@@ -428,6 +434,7 @@ gks_status gks_batch_create(int n, const gks_grid_desc* grids, const gks_options
   b->face_tw = 32;
   b->timeout_s = 2.0;
   b->skip_block = -1;
+  b->all_ns = true;
   size_t nu = 0, nwx = 0, nwy = 0, nc = 0, nfx = 0, nfy = 0, nbad = 0;
   b->cells = 0;
   for (int g = 0; g < n; ++g) {
@@ -441,6 +448,7 @@ gks_status gks_batch_create(int n, const gks_grid_desc* grids, const gks_options
     G.nx = d.nx; G.ny = d.ny;
     G.dx = d.Lx / d.nx; G.dy = d.Ly / d.ny;
     G.gamma = d.gamma; G.mu = d.mu; G.Pr = d.Pr;
+    if (!(d.mu > 0)) b->all_ns = false;
     G.weno_eps = o.weno_eps; G.weno_C = o.weno_C; G.tau_eps = o.tau_eps; G.tau_C = o.tau_C;
     G.viscous_dt = o.viscous_dt;
     G.characteristic = o.characteristic;
