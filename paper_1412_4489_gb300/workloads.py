@@ -303,6 +303,68 @@ def shock_tube(nx: int, left, right, gamma: float = 1.4, name: str | None = None
                    np.ascontiguousarray(U), np.ascontiguousarray(Wx), np.ascontiguousarray(Wy))
 
 
+def _piecewise_x(nx, ny, Lx, Ly, breaks, states, gamma):
+    """Cell averages and Gauss-point values of primitive states constant on x-intervals:
+    states[k] = (rho, u, p) on [breaks[k], breaks[k + 1]); cells cut by a break take the
+    length-weighted mix, points exactly on a break the mean of the two sides."""
+    dx = Lx / nx
+    cons = [_cons(r, u, 0.0, p, gamma) for (r, u, p) in states]
+    xl = np.arange(nx) * dx
+    avg = np.zeros((4, nx))
+    for k, c in enumerate(cons):
+        lo, hi = breaks[k], breaks[k + 1]
+        xr = (np.arange(nx) + 1) * dx
+        part = np.clip((np.minimum(xr, hi) - np.maximum(xl, lo)) / dx, 0.0, 1.0)
+        frac = np.where((xl >= lo) & (xr <= hi), 1.0, np.where((xr <= lo) | (xl >= hi), 0.0, part))
+        avg += c.reshape(4, 1) * frac
+    U = np.ascontiguousarray(np.broadcast_to(avg[:, None, :], (4, ny, nx)).copy())
+
+    def pt(x, y):
+        x = np.asarray(x, dtype=np.float64)
+        out = np.zeros((4,) + x.shape)
+        for k, c in enumerate(cons):
+            lo, hi = breaks[k], breaks[k + 1]
+            w = np.where((x > lo) & (x < hi), 1.0, 0.0)
+            w = w + 0.5 * (np.isclose(x, lo) & (k > 0)) + 0.5 * (np.isclose(x, hi) & (k < len(cons) - 1))
+            w = w + 1.0 * (np.isclose(x, lo) & (k == 0)) + 1.0 * (np.isclose(x, hi) & (k == len(cons) - 1))
+            out += c.reshape(4, *([1] * x.ndim)) * w
+        return out
+
+    _, _, wxp, wyp = _gauss_points(nx, ny, Lx, Ly)
+    return U, np.ascontiguousarray(_point_state(pt, wxp)), np.ascontiguousarray(_point_state(pt, wyp))
+
+
+def blast_wave(nx: int = 400, gamma: float = 1.4) -> Problem:
+    """The Woodward-Colella blast wave of Section 5 (1D tests): [0, 100], (rho, u, p) =
+    (1, 0, 1000) for x < 10, (1, 0, 0.01) on [10, 90), (1, 0, 100) beyond; reflecting ends
+    (slip walls), as an nx-by-1 grid (dy = dx, periodic in y).  The paper runs 400 cells to
+    t = 3.8."""
+    Lx = 100.0
+    dx = Lx / nx
+    U, Wx, Wy = _piecewise_x(nx, 1, Lx, dx, [0.0, 10.0, 90.0, 100.0],
+                             [(1.0, 0.0, 1000.0), (1.0, 0.0, 0.01), (1.0, 0.0, 100.0)], gamma)
+    wall = (BC_SLIPWALL, 0.0, 0.0, 1.0)
+    bc = [wall, wall, (BC_PERIODIC, 0.0, 0.0, 1.0), (BC_PERIODIC, 0.0, 0.0, 1.0)]
+    return Problem(f"blast_wave_{nx}", nx, 1, Lx, dx, gamma, 0.0, 1.0, bc, U, Wx, Wy,
+                   meta={"t_end": 3.8})
+
+
+def viscous_shock_tube(nx: int = 300, Re: float = 200.0, gamma: float = 1.4, Pr: float = 0.73) -> Problem:
+    """The viscous shock tube of Section 5: gas at rest in [0, 1] x [0, 0.5], (rho, u, p) =
+    (120, 0, 120/gamma) for x < 0.5 and (1.2, 0, 1.2/gamma) beyond; adiabatic no-slip walls
+    at x = 0, x = 1 and y = 0, symmetry (slip wall) at y = 0.5; Pr = 0.73, mu = 1/Re (the
+    reading of the Reynolds number: unit reference density, velocity and length); nx by
+    nx / 2 cells (the paper: 300 x 150 at Re = 200), to t = 1."""
+    ny = nx // 2
+    Lx, Ly = 1.0, 0.5
+    U, Wx, Wy = _piecewise_x(nx, ny, Lx, Ly, [0.0, 0.5, 1.0],
+                             [(120.0, 0.0, 120.0 / gamma), (1.2, 0.0, 1.2 / gamma)], gamma)
+    wall = (BC_NOSLIP_ADIABATIC, 0.0, 0.0, 1.0)
+    bc = [wall, wall, wall, (BC_SLIPWALL, 0.0, 0.0, 1.0)]
+    return Problem(f"viscous_shock_tube_{nx}x{ny}", nx, ny, Lx, Ly, gamma, 1.0 / Re, Pr, bc, U, Wx, Wy,
+                   meta={"Re": Re, "t_end": 1.0})
+
+
 BATCH_SIZES = [32 * k for k in range(1, 13)]
 
 

@@ -1,0 +1,117 @@
+"""The paper's strong-shock and viscous wall workloads (Section 5) on the GPU: the
+Woodward-Colella blast wave (reflecting ends, pressure ratio 1e5) and the viscous shock
+tube (adiabatic no-slip walls, symmetry plane, Re 200).
+
+Both amplify roundoff: the oracle started from cell averages perturbed by 1e-14, or from
+face point values rounded to FP32, ends the blast wave at L1 1e-2 / 5e-3 from itself
+(tests/golden/blast_wave_400_t3.8.txt records both).  So the parity checks are exact-path
+(L1 1e-10) before the amplification sets in, and past it the GPU results must lie within
+3x that spread of the oracle's own answers.  Closed boxes: mass and energy are conserved."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1412_4489_gb300 import gks, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "blast_wave_400_t3.8.txt")
+
+
+def _blast_golden():
+    sens = {}
+    for line in open(GOLDEN):
+        if line.startswith("# sensitivity_"):
+            f = line[2:].split()
+            sens[f[0]] = np.array([float(x) for x in f[1:]])
+        elif line.startswith("# nx"):
+            f = line[1:].split()
+            meta = {f[k]: f[k + 1] for k in range(0, len(f) - 1, 2)}
+    rows = np.loadtxt(GOLDEN)
+    early = rows[rows[:, 0] == 0][:, 2:].T
+    final = rows[rows[:, 0] == 1][:, 2:].T
+    return meta, sens, early, final
+
+
+def _l1(a, b):
+    return np.abs(a - b).sum(axis=1) / np.abs(b).sum(axis=1)
+
+
+@pytest.mark.parametrize("prec", [gks.GKS_FP64, gks.GKS_FP32_BULK])
+def test_blast_wave_against_the_oracle(prec):
+    meta, sens, early, final = _blast_golden()
+    p = wl.blast_wave(400)
+    s = gks.Solver(p, prec, tau_eps=0.05)
+    check = int(meta["check"])
+    for _ in range(check):
+        s.step(0.5, 3.8)
+    U1 = s.state()[0][:, 0, :]
+    s.advance(2 * int(meta["steps"]), 0.5, t_end=3.8)
+    U2, _, _, t = s.state()
+    nsteps = s.sync()[1]
+    s.close()
+    U2 = U2[:, 0, :]
+    # FP32-bulk takes its dt from its own state: a few steps more or fewer
+    assert t == 3.8 and (nsteps == int(meta["steps"]) if prec == gks.GKS_FP64 else abs(nsteps - int(meta["steps"])) < 40)
+    rows = [0, 1, 3]  # rhoV stays at roundoff level in this 1D problem
+    e1, e2 = _l1(U1, early)[rows], _l1(U2, final)[rows]
+    spread = np.maximum(sens["sensitivity_u1e-14"], sens["sensitivity_w_fp32"])[rows]
+    print(f"blast wave prec {prec}: L1 after {check} steps {e1}, at t = 3.8 {e2} (oracle spread {spread})")
+    # before the amplification FP64 follows the oracle's arithmetic.  FP32-bulk does not: at
+    # the 1e5 pressure jumps its FP32 face arithmetic resolves the low-pressure side to about
+    # 1e-2 (L1 1e-3 after 150 steps), so it is held to the late-time spread only.
+    if prec == gks.GKS_FP64:
+        assert np.all(e1 <= 1e-10), e1
+    assert np.all(e2 <= 3 * spread), (e2, spread)
+    # closed box: mass and energy conserved (FP64 to roundoff; FP32-bulk to its double-float sums)
+    m0, m = p.U[:, 0, :].sum(axis=1), U2.sum(axis=1)
+    tol = 1e-13 if prec == gks.GKS_FP64 else 1e-9
+    assert abs(m[0] - m0[0]) <= tol * m0[0] and abs(m[3] - m0[3]) <= tol * m0[3], (m - m0) / m0
+    assert U2[0].min() > 0 and U2[0].max() > 4.0  # the shell between the colliding blasts
+
+
+def test_viscous_shock_tube_fp64_equals_the_oracle():
+    """60 x 30 cells for 100 steps (past the reflection of the shock at x = 1): adiabatic
+    no-slip walls on three sides, the symmetry plane on top."""
+    p = wl.viscous_shock_tube(60)
+    P = oracle.params(gamma=p.gamma, mu=p.mu, Pr=p.Pr, tau_eps=0.05)
+    st = oracle.State2D(p.nx, p.ny, p.Lx, p.Ly, p.U, p.Wx, p.Wy)
+    bc = oracle.bcs([b[0] for b in p.bc], [b[1:] for b in p.bc])
+    s = gks.Solver(p, gks.GKS_FP64, tau_eps=0.05)
+    for _ in range(100):
+        s.step(0.5)
+        rc, _ = oracle.step2d(P, st, bc, 0.5)
+        assert rc == 0
+    U, _, _, t = s.state()
+    s.close()
+    # dt follows the state, which differs at 1e-11 in places on this discontinuous flow
+    assert t == pytest.approx(st.t, rel=1e-9)
+    err = _l1(U.reshape(4, -1), st.U.reshape(4, -1))
+    assert np.all(err <= 1e-8), err  # discontinuous data: the L1 bound
+
+
+def test_viscous_shock_tube_300x150_to_t1():
+    """The paper's 300 x 150 grid at Re 200 to t = 1 in FP64 and FP32-bulk: the closed box
+    conserves mass and energy, and FP32-bulk stays within 1e-5 + 10x the FP64 scheme's own
+    response to face point values rounded to FP32."""
+    p = wl.viscous_shock_tube(300)
+    q = wl.viscous_shock_tube(300)
+    q.Wx = q.Wx.astype(np.float32).astype(np.float64)
+    q.Wy = q.Wy.astype(np.float32).astype(np.float64)
+    out = {}
+    for name, prob, prec in (("f64", p, gks.GKS_FP64), ("ctl", q, gks.GKS_FP64), ("f32", p, gks.GKS_FP32_BULK)):
+        s = gks.Solver(prob, prec, tau_eps=0.05)
+        s.advance(100000, 0.5, t_end=1.0)
+        U, _, _, t = s.state()
+        s.close()
+        assert t == 1.0
+        out[name] = U
+        m0, m = p.U.reshape(4, -1).sum(axis=1), U.reshape(4, -1).sum(axis=1)
+        tol = 1e-13 if prec == gks.GKS_FP64 else 1e-8
+        assert abs(m[0] - m0[0]) <= tol * m0[0] and abs(m[3] - m0[3]) <= tol * m0[3], (name, (m - m0) / m0)
+    l1 = lambda a, b: np.abs(a[0] - b[0]).sum() / np.abs(b[0]).sum()
+    e32, ectl = l1(out["f32"], out["f64"]), l1(out["ctl"], out["f64"])
+    print(f"viscous shock tube 300x150, t = 1: FP32-bulk L1 {e32:.3e}, FP64 from FP32-rounded face values {ectl:.3e}")
+    assert e32 <= 1e-5 + 10 * ectl, (e32, ectl)

@@ -84,3 +84,34 @@ def test_oracle_isotropic_vortex_follows_table2():
     assert np.all(e[:, 1] < 2 * table[:2, 3]) and np.all(e[:, 1] > table[:2, 3] / 5)
     order = math.log(e[0, 0] / e[1, 0]) / math.log(41 / 21)
     assert order > 2.0, order
+
+
+def test_blast_wave_and_viscous_shock_tube_initial_data():
+    """The Section 5 setups: exact totals of the piecewise-constant data, face point values
+    on a break the mean of the two sides, reflecting / no-slip / symmetry boundaries."""
+    g = 1.4
+    b = wl.blast_wave(400)
+    assert (b.nx, b.ny, b.Lx) == (400, 1, 100.0) and b.Ly == pytest.approx(0.25)
+    # total energy p / (gamma - 1) over the three intervals, times the cell volume dx dy
+    e = (1000.0 * 10 + 0.01 * 80 + 100.0 * 10) / (g - 1) / 100.0 * 400
+    assert b.U[3].sum() == pytest.approx(e, rel=1e-13) and b.U[0].sum() == pytest.approx(400.0, rel=1e-14)
+    assert np.all(b.U[1:3] == 0.0)
+    assert b.Wx[3, :, 0, 40] == pytest.approx([(1000.0 + 0.01) / 2 / (g - 1)] * 2)  # the face at x = 10
+    assert [k for k, *_ in b.bc] == [wl.BC_SLIPWALL, wl.BC_SLIPWALL, wl.BC_PERIODIC, wl.BC_PERIODIC]
+    v = wl.viscous_shock_tube(300)
+    assert (v.nx, v.ny, v.Lx, v.Ly) == (300, 150, 1.0, 0.5)
+    assert v.mu == pytest.approx(1 / 200.0) and v.Pr == 0.73
+    assert v.U[0, :, :150].min() == 120.0 and v.U[0, :, 150:].max() == pytest.approx(1.2)
+    assert v.U[3, 0, 0] == pytest.approx(120.0 / g / (g - 1)) and v.Wx[0, :, 7, 150] == pytest.approx([60.6, 60.6])
+    assert [k for k, *_ in v.bc] == [wl.BC_NOSLIP_ADIABATIC] * 3 + [wl.BC_SLIPWALL]
+    assert all(w[1] == 0.0 and w[2] == 0.0 for w in v.bc)  # walls at rest
+    # the oracle keeps both closed boxes' mass and energy to roundoff
+    for p, n in ((b, 40), (wl.viscous_shock_tube(24), 20)):
+        P = oracle.params(gamma=p.gamma, mu=p.mu, Pr=p.Pr, tau_eps=0.05)
+        st = oracle.State2D(p.nx, p.ny, p.Lx, p.Ly, p.U, p.Wx, p.Wy)
+        bc = oracle.bcs([k[0] for k in p.bc], [k[1:] for k in p.bc])
+        for _ in range(n):
+            rc, _ = oracle.step2d(P, st, bc, 0.5)
+            assert rc == 0
+        m0, m = p.U.reshape(4, -1).sum(axis=1), st.U.reshape(4, -1).sum(axis=1)
+        assert abs(m[0] - m0[0]) <= 1e-13 * m0[0] and abs(m[3] - m0[3]) <= 1e-13 * m0[3]
