@@ -136,7 +136,12 @@ gks_status gks_create(int nx, int ny, double Lx, double Ly, double gamma, double
 /* Copies a state from host memory (layouts above; Wx/Wy may be NULL, which
  * sets every face point value to the mean of the two adjacent cell averages, a
  * second-order start).  t is the simulation time.  Computes the first CFL
- * bound.  Synchronous.  Clears a pending GKS_ENONPHYSICAL. */
+ * bound.  Synchronous.  Clears a pending GKS_ENONPHYSICAL.
+ * Page-locked arrays mapped into the device's address space (cudaHostAlloc,
+ * cudaHostRegister with the mapped flag, or any page-locked memory on a system
+ * with unified addressing) are read in place by the kernels over the host link;
+ * other host memory goes through a device staging buffer.  Either way each array
+ * must hold the full size given above. */
 gks_status gks_set_state(gks_handle* h, const double* U, const double* Wx, const double* Wy,
                          double t);
 
@@ -163,7 +168,8 @@ gks_status gks_advance(gks_handle* h, int nsteps, double CFL, double t_end);
  * be NULL) receive the simulation time and the number of steps taken. */
 gks_status gks_sync(gks_handle* h, double* t, long long* steps);
 
-/* Copies the state to host memory (any of U, Wx, Wy, t may be NULL).
+/* Copies the state to host memory (any of U, Wx, Wy, t may be NULL); mapped
+ * page-locked arrays are written in place by the kernels, as in gks_set_state.
  * Synchronous; returns the pending status (the state is the last good one). */
 gks_status gks_get_state(gks_handle* h, double* U, double* Wx, double* Wy, double* t);
 

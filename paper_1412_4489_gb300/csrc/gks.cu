@@ -475,8 +475,24 @@ gks_status reset_ctrl(gks_handle* h, double t) {
 // Loads a state from device FP64 arrays.  With stage_w set, dWx /
 // dWy are host arrays copied in turn through the staging buffer (which must
 // then not hold dU).
+// The device address of a page-locked host array mapped into the device's address
+// space (cudaHostAlloc, cudaHostRegister): kernels then read or write it in place over
+// the host link.  nullptr for any other pointer (pageable host memory goes through
+// the staging buffer).
+const double* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // an unknown pointer: clear the error it left
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost && a.devicePointer ? (const double*)a.devicePointer : nullptr;
+}
+
+// dU, dWx, dWy: device-accessible arrays, except that a face-value array flagged in
+// stage_x / stage_y is a host array copied through the staging buffer first
 template <class TW>
-gks_status load_state(gks_handle* h, const double* dU, const double* dWx, const double* dWy, bool stage_w = false) {
+gks_status load_state(gks_handle* h, const double* dU, const double* dWx, const double* dWy, bool stage_x = false,
+                      bool stage_y = false) {
   const Geo& g = h->g;
   cudaStream_t s = h->stream;
   const dim3 b2(32, 8);
@@ -489,7 +505,7 @@ gks_status load_state(gks_handle* h, const double* dU, const double* dWx, const 
     TW* W0 = (TW*)(axis == 0 ? h->Wx[0] : h->Wy[0]);
     TW* W1 = (TW*)(axis == 0 ? h->Wx[1] : h->Wy[1]);
     if (src) {
-      if (stage_w) {
+      if (axis == 0 ? stage_x : stage_y) {
         CK(cudaMemcpyAsync(h->staging, src, n * sizeof(double), cudaMemcpyHostToDevice, s));
         src = h->staging;
       }
@@ -662,14 +678,23 @@ gks_status gks_set_state(gks_handle* h, const double* U, const double* Wx, const
   if (!h || !U) return fail(h, GKS_EINVAL, "gks_set_state: U is required");
   CK(cudaSetDevice(h->device));
   const Geo& g = h->g;
-  // U goes through the staging buffer; face values through the same buffer in turn
   gks_status st = reset_ctrl(h, t);
   if (st != GKS_OK) return st;
-  // U goes in through the staging buffer first (the scatter reads it before the
-  // face values reuse the buffer: same stream)
-  CK(cudaMemcpyAsync(h->staging, U, n_u(g) * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-  st = h->prec == GKS_FP64 ? load_state<double>(h, h->staging, Wx, Wy, true)
-                           : load_state<float>(h, h->staging, Wx, Wy, true);
+  // page-locked host arrays are read in place by the kernels; the others go through
+  // the staging buffer in turn (U first: the scatter reads it before the face values
+  // reuse the buffer, same stream)
+  const double* dU = mapped_host(U);
+  const double* dWx = Wx ? mapped_host(Wx) : nullptr;
+  const double* dWy = Wy ? mapped_host(Wy) : nullptr;
+  if (!dU) {
+    CK(cudaMemcpyAsync(h->staging, U, n_u(g) * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    dU = h->staging;
+  }
+  const bool sx = Wx && !dWx, sy = Wy && !dWy;
+  if (sx) dWx = Wx;
+  if (sy) dWy = Wy;
+  st = h->prec == GKS_FP64 ? load_state<double>(h, dU, dWx, dWy, sx, sy)
+                           : load_state<float>(h, dU, dWx, dWy, sx, sy);
   if (st != GKS_OK) return st;
   st = read_ctrl(h);
   if (st != GKS_OK) return st;
@@ -738,13 +763,17 @@ gks_status gks_get_state(gks_handle* h, double* U, double* Wx, double* Wy, doubl
   struct { double* host; size_t n; int which; } parts[3] = {{U, n_u(g), 0}, {Wx, n_wx(g), 1}, {Wy, n_wy(g), 2}};
   for (auto& p : parts) {
     if (!p.host) continue;
+    // page-locked host arrays are written in place by the kernels; the others through
+    // the staging buffer in turn
+    double* direct = const_cast<double*>(mapped_host(p.host));
+    double* dst = direct ? direct : h->staging;
     gks_status st = h->prec == GKS_FP64
-                        ? store_state<double>(h, p.which == 0 ? h->staging : nullptr, p.which == 1 ? h->staging : nullptr,
-                                              p.which == 2 ? h->staging : nullptr)
-                        : store_state<float>(h, p.which == 0 ? h->staging : nullptr, p.which == 1 ? h->staging : nullptr,
-                                             p.which == 2 ? h->staging : nullptr);
+                        ? store_state<double>(h, p.which == 0 ? dst : nullptr, p.which == 1 ? dst : nullptr,
+                                              p.which == 2 ? dst : nullptr)
+                        : store_state<float>(h, p.which == 0 ? dst : nullptr, p.which == 1 ? dst : nullptr,
+                                             p.which == 2 ? dst : nullptr);
     if (st != GKS_OK) return st;
-    CK(cudaMemcpyAsync(p.host, h->staging, p.n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (!direct) CK(cudaMemcpyAsync(p.host, h->staging, p.n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   }
   gks_status st = read_ctrl(h);
   if (st != GKS_OK) return st;

@@ -285,3 +285,33 @@ def test_characteristic_fp32_bulk_within_budget():
     a.close()
     b.close()
     assert np.sum(np.abs(Ub[0] - Ua[0])) / np.sum(np.abs(Ua[0])) < 1e-5
+
+
+@pytest.mark.parametrize("prec", [gks.GKS_FP64, gks.GKS_FP32_BULK])
+def test_page_locked_host_arrays_round_trip_like_pageable_ones(prec):
+    """gks_set_state / gks_get_state read and write page-locked host arrays in place (over the
+    host link) and copy pageable ones through the staging buffer: the same state either way."""
+    import torch
+    p = wl.riemann_2d(70, 45, seed=3, mu=1e-4, Pr=0.72)
+
+    def pinned_like(a):
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = a
+        return t
+
+    pins = [pinned_like(a) for a in (p.U, p.Wx, p.Wy)]
+    out = []
+    for host in ((p.U, p.Wx, p.Wy), tuple(t.numpy() for t in pins)):
+        s = gks.Solver(p, prec)
+        gks.gks_set_state(s.h, *host, 0.25)
+        s.advance(3, 0.5)
+        if host[0] is p.U:
+            U, Wx, Wy, t = s.state()
+        else:
+            dst = [pinned_like(np.zeros_like(a)) for a in (p.U, p.Wx, p.Wy)]
+            t = gks.gks_get_state(s.h, *(d.numpy() for d in dst))
+            U, Wx, Wy = (d.numpy().copy() for d in dst)
+        s.close()
+        out.append((U, Wx, Wy, t))
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
