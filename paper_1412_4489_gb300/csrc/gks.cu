@@ -85,9 +85,12 @@ __global__ void __launch_bounds__(256) k_recon(Geo g, const R* U0, const R* U1, 
 // ---------------------------------------------------------------------------
 // face evolution
 // ---------------------------------------------------------------------------
-// resident 128-thread blocks per SM the face kernel is compiled for (register cap)
+// resident 128-thread blocks per SM the face kernel is compiled for (register cap).
+// FP32: 4 blocks = 16 warps per SM at 128 registers (registers are allocated per SM
+// quarter, so more than 12 warps means at most 128); the Euler routine fits without
+// spilling, and the extra warps hide more of its latency than 3 blocks at 168 registers.
 #ifndef GKS_FLUX_MINB_F32
-#define GKS_FLUX_MINB_F32 3
+#define GKS_FLUX_MINB_F32 4
 #endif
 template <class R> struct FluxBlocks;
 template <> struct FluxBlocks<double> { static constexpr int value = 1; };
