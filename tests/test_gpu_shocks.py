@@ -65,10 +65,13 @@ def test_blast_wave_against_the_oracle(prec):
     if prec == gks.GKS_FP64:
         assert np.all(e1 <= 1e-10), e1
     assert np.all(e2 <= 3 * spread), (e2, spread)
-    # closed box: mass and energy conserved (FP64 to roundoff; FP32-bulk to its double-float sums)
+    # closed box: mass conserved to the roundoff of the sums (the walls' mass flux is zero by
+    # their definition); energy to the roundoff of the slip walls' energy flux, zero only up
+    # to rounding of its terms (~p c ~ 4e4): FP64 1e-13, FP32 rounding ~4e4 x 6e-8 per unit
+    # time over t = 3.8 against a total of 1.1e5, i.e. ~1e-7
     m0, m = p.U[:, 0, :].sum(axis=1), U2.sum(axis=1)
-    tol = 1e-13 if prec == gks.GKS_FP64 else 1e-9
-    assert abs(m[0] - m0[0]) <= tol * m0[0] and abs(m[3] - m0[3]) <= tol * m0[3], (m - m0) / m0
+    etol = 1e-13 if prec == gks.GKS_FP64 else 1e-7
+    assert abs(m[0] - m0[0]) <= 1e-13 * m0[0] and abs(m[3] - m0[3]) <= etol * m0[3], (m - m0) / m0
     assert U2[0].min() > 0 and U2[0].max() > 4.0  # the shell between the colliding blasts
 
 
@@ -124,9 +127,11 @@ def test_viscous_shock_tube_300x150_to_t1():
         s.close()
         assert t == 1.0
         out[name] = U
+        # mass exact up to the sums' roundoff; energy up to the rounding of the symmetry
+        # plane's energy flux (FP32: ~1e-7, as for the blast wave's walls)
         m0, m = p.U.reshape(4, -1).sum(axis=1), U.reshape(4, -1).sum(axis=1)
-        tol = 1e-13 if prec == gks.GKS_FP64 else 1e-8
-        assert abs(m[0] - m0[0]) <= tol * m0[0] and abs(m[3] - m0[3]) <= tol * m0[3], (name, (m - m0) / m0)
+        etol = 1e-13 if prec == gks.GKS_FP64 else 1e-7
+        assert abs(m[0] - m0[0]) <= 1e-13 * m0[0] and abs(m[3] - m0[3]) <= etol * m0[3], (name, (m - m0) / m0)
     l1 = lambda a, b: np.abs(a[0] - b[0]).sum() / np.abs(b[0]).sum()
     e32, ectl = l1(out["f32"], out["f64"]), l1(out["ctl"], out["f64"])
     print(f"viscous shock tube 300x150, t = 1: FP32-bulk L1 {e32:.3e}, FP64 from FP32-rounded face values {ectl:.3e}")
