@@ -104,8 +104,10 @@ __device__ bool grid_barrier(Barrier* b) {
   return *(volatile int*)&b->error == 0;
 }
 
+// resident blocks per SM the FP32 batch kernel is compiled for: 4 (128 registers, 16 warps
+// per SM; the autotuner may run fewer)
 #ifndef GKS_BATCH_MINB_F32
-#define GKS_BATCH_MINB_F32 3
+#define GKS_BATCH_MINB_F32 4
 #endif
 template <class R> struct BatchBlocks;
 template <> struct BatchBlocks<double> { static constexpr int value = 1; };
