@@ -284,3 +284,47 @@ def test_adiabatic_moving_wall_does_work():
     # x-momentum enters through the lid (the only moving wall) and friction on the other walls
     # removes some; the energy gained is the lid's work, which is positive
     assert d[3] > 0 and d[1] > 0
+
+
+def _isobaric_mode_decay_rate(Pr, mu=0.01, nx=32, eps=1e-3, t_end=2.0, gamma=1.4):
+    """Decay rate of an isobaric temperature mode T = 1 + eps sin(2 pi x) (p = 1, at rest) on a
+    periodic nx-by-1 grid (exact cell averages and point values)."""
+    dx, k = 1.0 / nx, 2.0 * np.pi
+    rho = lambda x: 1.0 / (1.0 + eps * np.sin(k * x))
+    xg, wg = np.polynomial.legendre.leggauss(6)
+    xc = (np.arange(nx) + 0.5) * dx
+    U = np.zeros((4, 1, nx))
+    U[0, 0] = (rho(xc[:, None] + 0.5 * dx * xg[None, :]) * wg).sum(axis=1) / 2
+    U[3] = 1.0 / (gamma - 1)
+    Wx = np.zeros((4, 2, 1, nx + 1))
+    Wx[0] = rho(np.arange(nx + 1) * dx)[None, None, :]
+    Wx[3] = 1.0 / (gamma - 1)
+    Wy = np.zeros((4, 2, 2, nx))
+    Wy[0] = rho(xc[None, :] + np.array([-1.0, 1.0])[:, None] * dx * math.sqrt(3) / 6)[:, None, :]
+    Wy[3] = 1.0 / (gamma - 1)
+    P = oracle.params(gamma=gamma, mu=mu, Pr=Pr)
+    st = oracle.State2D(nx, 1, 1.0, dx, U, Wx, Wy)
+    bc = oracle.bcs([0, 0, 0, 0])
+
+    def amplitude():
+        T = (gamma - 1) * (st.U[3, 0] - 0.5 * st.U[1, 0] ** 2 / st.U[0, 0]) / st.U[0, 0]
+        return 2 * abs(np.fft.rfft(T - T.mean())[1]) / nx
+
+    a0 = amplitude()
+    while st.t < t_end:
+        rc, _ = oracle.step2d(P, st, bc, 0.5, dt_max=t_end - st.t, viscous_dt=1)
+        assert rc == 0
+    return math.log(a0 / amplitude()) / st.t
+
+
+def test_prandtl_fix_gives_fouriers_law():
+    """The Prandtl-number correction (energy flux += (1/Pr - 1) q) pinned by physics instead of
+    the paper: an isobaric temperature mode decays at chi k^2 with chi = kappa / (rho c_p) =
+    mu / (Pr rho) (Fourier's law with kappa = mu c_p / Pr), so the rate must scale as 1/Pr.
+    Measured: 1.02 chi k^2 at both Pr = 1 (the plain BGK conductivity) and Pr = 0.72, at 16, 32
+    and 64 cells alike; their ratio 1.3868 against 1/0.72 = 1.3889."""
+    k2 = (2 * math.pi) ** 2
+    r1, r72 = _isobaric_mode_decay_rate(1.0), _isobaric_mode_decay_rate(0.72)
+    assert r1 == pytest.approx(0.01 * k2, rel=0.05)
+    assert r72 == pytest.approx(0.01 / 0.72 * k2, rel=0.05)
+    assert r72 / r1 == pytest.approx(1 / 0.72, rel=0.01)
