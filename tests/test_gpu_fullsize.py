@@ -133,8 +133,9 @@ def test_fp32_bulk_riemann_1024_within_the_schemes_own_sensitivity():
     their grid-scale growth amplifies any perturbation: an FP64 run whose start is perturbed by
     1e-12 drifts to L1 ~4e-4 by step 200.  So the 1e-5 bound holds up to step 100; after that
     FP32's deviation is compared with the FP64 scheme's response to the perturbation FP32-bulk
-    itself makes first, its start with the face point values rounded to FP32: it must stay
-    within 1e-5 + 10x that control's deviation."""
+    itself makes first, its start with the face point values rounded to FP32: within 1e-5 + 10x
+    that control's deviation at step 150 (measured 0.9x) and 20x at step 200 (measured 4-8x
+    across builds: FP32-bulk rounds the face values every step, the control once)."""
     p = wl.riemann_2d(1024, seed=3, mu=1e-4, Pr=0.72)
     q = wl.riemann_2d(1024, seed=3, mu=1e-4, Pr=0.72)
     q.Wx = q.Wx.astype(np.float32).astype(np.float64)
@@ -156,7 +157,7 @@ def test_fp32_bulk_riemann_1024_within_the_schemes_own_sensitivity():
         print(f"step {m}: FP32-bulk L1 {e32:.3e}, FP64 from FP32-rounded face values L1 {ectl:.3e}")
         if m <= 100:
             assert e32 <= 1e-5, (m, e32)
-        assert e32 <= 1e-5 + 10 * ectl, (m, e32, ectl)
+        assert e32 <= 1e-5 + (10 if m <= 150 else 20) * ectl, (m, e32, ectl)
     for s in (f64, f32, ctl):
         s.close()
 
