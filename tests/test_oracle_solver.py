@@ -364,3 +364,35 @@ def test_viscous_collision_time_gives_the_shear_viscosity():
     r1, r72 = _shear_mode_decay_rate(1.0), _shear_mode_decay_rate(0.72)
     assert r1 == pytest.approx(0.01 * k2, rel=1e-3)
     assert r72 == pytest.approx(r1, rel=1e-3)
+
+
+def test_isothermal_walls_conduct_fouriers_heat_flux():
+    """The isothermal no-slip wall image pinned by physics: gas at rest between walls at
+    T = 1.2 and 0.8 (mu = 0.05, Pr = 1, 16 cells) relaxes to steady conduction in which every
+    face, the two wall faces included, carries the same energy flux, the bulk conductivity is
+    mu c_p (Fourier's law for the BGK gas), and the linear bulk profile meets the walls at their
+    temperatures (measured: conductivity within 1.3e-4, wall values within 1.5e-3)."""
+    g, nx, mu, T1, T2 = 1.4, 16, 0.05, 1.2, 0.8
+    dx = 1.0 / nx
+    U = np.zeros((4, 1, nx))
+    U[0] = 1.0
+    U[3] = 1.0 / (g - 1)
+    Wx = np.ascontiguousarray(np.broadcast_to(U[:, None, :, :1], (4, 2, 1, nx + 1)))
+    Wy = np.ascontiguousarray(np.broadcast_to(U[:, None, :1, :], (4, 2, 2, nx)))
+    P = oracle.params(gamma=g, mu=mu, Pr=1.0)
+    st = oracle.State2D(nx, 1, 1.0, dx, U, Wx, Wy)
+    bc = oracle.bcs([3, 3, 0, 0], [(0.0, 0.0, T1), (0.0, 0.0, T2), (0.0, 0.0, 1.0), (0.0, 0.0, 1.0)])
+    while st.t < 60.0:  # four conduction times L^2 rho c_v / kappa
+        rc, _ = oracle.step2d(P, st, bc, 0.5, viscous_dt=1)
+        assert rc == 0
+    dt = oracle.dt2d(P, st, 0.5, viscous_dt=1)
+    Fx, _, _, _ = oracle.flux2d(P, st, bc, dt)
+    q = Fx[3, 0] / dt
+    assert np.ptp(q) <= 1e-3 * abs(q.mean()), q
+    assert np.all(Fx[0, 0, [0, -1]] == 0.0)  # impermeable walls
+    T = (g - 1) * (st.U[3, 0] - 0.5 * st.U[1, 0] ** 2 / st.U[0, 0]) / st.U[0, 0]
+    x = (np.arange(nx) + 0.5) * dx
+    slope, icpt = np.polyfit(x[nx // 4:3 * nx // 4], T[nx // 4:3 * nx // 4], 1)
+    assert -q.mean() / slope == pytest.approx(mu * g / (g - 1), rel=1e-2)
+    assert icpt == pytest.approx(T1, abs=1e-2) and icpt + slope == pytest.approx(T2, abs=1e-2)
+    assert np.abs(st.U[1, 0] / st.U[0, 0]).max() < 1e-2
