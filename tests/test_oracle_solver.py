@@ -396,3 +396,36 @@ def test_isothermal_walls_conduct_fouriers_heat_flux():
     assert -q.mean() / slope == pytest.approx(mu * g / (g - 1), rel=1e-2)
     assert icpt == pytest.approx(T1, abs=1e-2) and icpt + slope == pytest.approx(T2, abs=1e-2)
     assert np.abs(st.U[1, 0] / st.U[0, 0]).max() < 1e-2
+
+
+def test_moving_isothermal_wall_gives_couette_flow():
+    """The moving no-slip (isothermal) wall pinned by plane Couette flow: walls at T = 1, the
+    one at x = 1 sliding at V_w = 0.1 (mu = 0.05, Pr = 1, 16 cells).  Steady state: the shear
+    stress is the same through every face, walls included, and equals mu dV/dx of a linear
+    profile that meets both wall velocities; the wall's work mu V_w^2 / L leaves as heat, half
+    through each wall, so the total energy flux is -mu V_w^2 / (2 L) through every face
+    (measured: stress uniform to 1e-14, mu dV/dx and the wall velocities to 1e-5)."""
+    g, nx, mu, Vw = 1.4, 16, 0.05, 0.1
+    dx = 1.0 / nx
+    U = np.zeros((4, 1, nx))
+    U[0] = 1.0
+    U[3] = 1.0 / (g - 1)
+    Wx = np.ascontiguousarray(np.broadcast_to(U[:, None, :, :1], (4, 2, 1, nx + 1)))
+    Wy = np.ascontiguousarray(np.broadcast_to(U[:, None, :1, :], (4, 2, 2, nx)))
+    P = oracle.params(gamma=g, mu=mu, Pr=1.0)
+    st = oracle.State2D(nx, 1, 1.0, dx, U, Wx, Wy)
+    bc = oracle.bcs([3, 3, 0, 0], [(0.0, 0.0, 1.0), (0.0, Vw, 1.0), (0.0, 0.0, 1.0), (0.0, 0.0, 1.0)])
+    while st.t < 80.0:  # four viscous times L^2 / nu
+        rc, _ = oracle.step2d(P, st, bc, 0.5, viscous_dt=1)
+        assert rc == 0
+    dt = oracle.dt2d(P, st, 0.5, viscous_dt=1)
+    Fx, _, _, _ = oracle.flux2d(P, st, bc, dt)
+    stress, energy = Fx[2, 0] / dt, Fx[3, 0] / dt
+    V = st.U[2, 0] / st.U[0, 0]
+    x = (np.arange(nx) + 0.5) * dx
+    slope, icpt = np.polyfit(x[nx // 4:3 * nx // 4], V[nx // 4:3 * nx // 4], 1)
+    assert np.ptp(stress) <= 1e-8 * abs(stress.mean())
+    assert -stress.mean() == pytest.approx(mu * slope, rel=1e-3)
+    assert icpt == pytest.approx(0.0, abs=1e-3 * Vw) and icpt + slope == pytest.approx(Vw, rel=1e-3)
+    assert np.all(Fx[0, 0, [0, -1]] == 0.0)
+    assert energy == pytest.approx(np.full(nx + 1, -mu * Vw * Vw / 2), rel=1e-2)
