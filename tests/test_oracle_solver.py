@@ -429,3 +429,34 @@ def test_moving_isothermal_wall_gives_couette_flow():
     assert icpt == pytest.approx(0.0, abs=1e-3 * Vw) and icpt + slope == pytest.approx(Vw, rel=1e-3)
     assert np.all(Fx[0, 0, [0, -1]] == 0.0)
     assert energy == pytest.approx(np.full(nx + 1, -mu * Vw * Vw / 2), rel=1e-2)
+
+
+def test_moving_adiabatic_wall_sends_its_work_to_the_isothermal_wall():
+    """The adiabatic no-slip wall pinned by Couette flow: the sliding wall at x = 1 adiabatic
+    (V_w = 0.1), the fixed one at x = 0 isothermal (T = 1).  No heat crosses the adiabatic wall,
+    so the whole work mu V_w^2 / L leaves through the isothermal one: the total energy flux is
+    -mu V_w^2 / L through every face, the stress mu dV/dx, and the temperature peaks at the
+    adiabatic wall with zero slope (measured: flux and stress to 1e-5)."""
+    g, nx, mu, Vw = 1.4, 16, 0.05, 0.1
+    dx = 1.0 / nx
+    U = np.zeros((4, 1, nx))
+    U[0] = 1.0
+    U[3] = 1.0 / (g - 1)
+    Wx = np.ascontiguousarray(np.broadcast_to(U[:, None, :, :1], (4, 2, 1, nx + 1)))
+    Wy = np.ascontiguousarray(np.broadcast_to(U[:, None, :1, :], (4, 2, 2, nx)))
+    P = oracle.params(gamma=g, mu=mu, Pr=1.0)
+    st = oracle.State2D(nx, 1, 1.0, dx, U, Wx, Wy)
+    bc = oracle.bcs([3, 4, 0, 0], [(0.0, 0.0, 1.0), (0.0, Vw, 1.0), (0.0, 0.0, 1.0), (0.0, 0.0, 1.0)])
+    while st.t < 120.0:  # the temperature relaxes over rho c_v L^2 / kappa, longer than L^2 / nu
+        rc, _ = oracle.step2d(P, st, bc, 0.5, viscous_dt=1)
+        assert rc == 0
+    dt = oracle.dt2d(P, st, 0.5, viscous_dt=1)
+    Fx, _, _, _ = oracle.flux2d(P, st, bc, dt)
+    stress, energy = Fx[2, 0] / dt, Fx[3, 0] / dt
+    V = st.U[2, 0] / st.U[0, 0]
+    T = (g - 1) * (st.U[3, 0] - 0.5 * (st.U[1, 0] ** 2 + st.U[2, 0] ** 2) / st.U[0, 0]) / st.U[0, 0]
+    x = (np.arange(nx) + 0.5) * dx
+    slope = np.polyfit(x[nx // 4:3 * nx // 4], V[nx // 4:3 * nx // 4], 1)[0]
+    assert -stress.mean() == pytest.approx(mu * slope, rel=1e-3) and np.ptp(stress) <= 1e-8 * abs(stress.mean())
+    assert energy == pytest.approx(np.full(nx + 1, -mu * Vw * Vw), rel=1e-2)
+    assert np.all(np.diff(T) > 0) and (T[-1] - T[-2]) < 0.1 * (T[1] - T[0])
