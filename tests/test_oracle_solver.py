@@ -460,3 +460,33 @@ def test_moving_adiabatic_wall_sends_its_work_to_the_isothermal_wall():
     assert -stress.mean() == pytest.approx(mu * slope, rel=1e-3) and np.ptp(stress) <= 1e-8 * abs(stress.mean())
     assert energy == pytest.approx(np.full(nx + 1, -mu * Vw * Vw), rel=1e-2)
     assert np.all(np.diff(T) > 0) and (T[-1] - T[-2]) < 0.1 * (T[1] - T[0])
+
+
+def _mirror_symmetric_wave(nx, L, gamma=1.4):
+    """rho = 1 + 0.2 cos(2 pi x), u = 0.3 sin(2 pi x), p = 1 + 0.1 cos(2 pi x), v = 0 on [0, L]
+    (nx-by-1, exact cell averages and point values): mirror symmetric about x = 0 and 0.5."""
+    dx = L / nx
+    cons = lambda x: np.stack([1.0 + 0.2 * np.cos(2 * np.pi * x), (1.0 + 0.2 * np.cos(2 * np.pi * x)) * 0.3 * np.sin(2 * np.pi * x),
+                               0.0 * x, (1.0 + 0.1 * np.cos(2 * np.pi * x)) / (gamma - 1)
+                               + 0.5 * (1.0 + 0.2 * np.cos(2 * np.pi * x)) * (0.3 * np.sin(2 * np.pi * x)) ** 2])
+    xg, wg = np.polynomial.legendre.leggauss(6)
+    xc = (np.arange(nx) + 0.5) * dx
+    U = (cons(xc[:, None] + 0.5 * dx * xg[None, :]) * wg).sum(axis=-1)[:, None, :] / 2
+    Wx = np.repeat(cons(np.arange(nx + 1) * dx)[:, None, None, :], 2, axis=1)
+    Wy = np.repeat(cons(xc[None, :] + np.array([-1.0, 1.0])[:, None] * dx * math.sqrt(3) / 6)[:, :, None, :], 2, axis=2)
+    return oracle.State2D(nx, 1, L, dx, np.ascontiguousarray(U), np.ascontiguousarray(Wx), np.ascontiguousarray(Wy))
+
+
+@pytest.mark.parametrize("mu", [0.0, 1e-3])
+def test_slip_walls_are_symmetry_planes(mu):
+    """The slip-wall image pinned by symmetry: data mirror symmetric about x = 0 and x = 0.5 on
+    the periodic [0, 1] evolve exactly like the half domain [0, 0.5] closed by slip walls (60
+    steps, Euler and Navier-Stokes; measured equal to 1e-15)."""
+    P = oracle.params(gamma=1.4, mu=mu, Pr=0.72 if mu else 1.0, tau_eps=0.05 if mu else 0.0)
+    full, half = _mirror_symmetric_wave(64, 1.0), _mirror_symmetric_wave(32, 0.5)
+    for _ in range(60):
+        assert oracle.step2d(P, full, oracle.bcs([0, 0, 0, 0]), 0.5)[0] == 0
+        assert oracle.step2d(P, half, oracle.bcs([2, 2, 0, 0]), 0.5)[0] == 0
+    assert half.t == pytest.approx(full.t, rel=1e-14)
+    # one scale for all variables: rho V stays at roundoff level (v = 0 by symmetry)
+    assert np.max(np.abs(full.U[:, :, :32] - half.U)) < 1e-13 * np.abs(full.U).max()
