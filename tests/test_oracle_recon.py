@@ -152,3 +152,187 @@ def test_slip_wall_face_is_impermeable(mu):
     scale = abs(F[1])
     assert abs(F[0]) < 1e-13 * scale and abs(F[2]) < 1e-13 * scale and abs(F[3]) < 1e-13 * scale
     assert np.all(np.abs(Wg[:, 1]) < 1e-13)
+
+
+# ---------------- the smallest-|a6| choice and the nonlinear weights ----------------
+#
+# Eq. over-sys solves each one-sided stencil in the least-squares sense.  Its cross
+# coefficient a6 enters only the four Gauss-point conditions of the stencil's two faces
+# (the neighbour averages do not see x y), so with Ubar, a2..a5 held, a6^k is the
+# least-squares solution of those four conditions.  The tests below compute it that way,
+# from the point coordinates alone, and never from the oracle's closed form.
+
+_STENCILS = ((1, 1), (-1, 1), (-1, -1), (1, -1))  # the order of Section 3.2's stencils 1..4
+
+
+def _gauss_points(sx, sy, dx, dy):
+    """(x, y, slot) of the four Gauss points of stencil (sx, sy): its x-face x = sx dx/2 at
+    y = -/+ sqrt(3)/6 dy (slots of fx), and its y-face y = sy dy/2 at x = -/+ sqrt(3)/6 dx
+    (slots of fy)."""
+    ex = 0 if sx > 0 else 2
+    ey = 0 if sy > 0 else 2
+    return ([(sx * dx / 2, -G * dy, ("x", ex)), (sx * dx / 2, G * dy, ("x", ex + 1))] +
+            [(-G * dx, sy * dy / 2, ("y", ey)), (G * dx, sy * dy / 2, ("y", ey + 1))])
+
+
+def _lstsq_cross(coef, fx, fy, dx, dy, sx, sy):
+    """a6 of one-sided stencil (sx, sy) for one variable: least squares over its four
+    Gauss-point conditions, coef = (Ubar, a2, a3, a4, a5) held."""
+    c0, a2, a3, a4, a5 = coef
+    rows, rhs = [], []
+    for x, y, (face, k) in _gauss_points(sx, sy, dx, dy):
+        val = fx[k] if face == "x" else fy[k]
+        rows.append([x * y])
+        rhs.append(val - (c0 + a2 * x + a3 * y + a4 * 0.5 * (x * x - dx * dx / 12)
+                          + a5 * 0.5 * (y * y - dy * dy / 12)))
+    return float(np.linalg.lstsq(np.array(rows), np.array(rhs), rcond=None)[0][0])
+
+
+def _cell_with_face_differences(seed, dx, dy, z):
+    """A quadratic cell (averages and Gauss-point values) whose face Gauss-point pairs are
+    then pulled apart: the y+ (x+) value of face f rises by z[f] and the y- (x-) value falls by
+    z[f], f = east, west, north, south, per variable.  The face means, hence the one-sided
+    a2..a5 (and the central a2..a5), stay those of the quadratic."""
+    a, nb, fx, fy = _quadratic_cell(seed, dx, dy)
+    fx, fy = fx.copy(), fy.copy()
+    ze, zw, zn, zs = (np.asarray(z[k], dtype=float) for k in range(4))
+    fx[0] -= ze; fx[1] += ze
+    fx[2] -= zw; fx[3] += zw
+    fy[0] -= zn; fy[1] += zn
+    fy[2] -= zs; fy[3] += zs
+    return a, nb, fx, fy
+
+
+# weights that keep only the one-sided polynomial: I(U1) = C dx dy ~ 1e-33 against
+# I(U2) ~ 1e-4, so omega_2 ~ 1e-58 and the output is the one-sided polynomial itself
+_ONE_SIDED = dict(weno_eps=0.0, weno_C=1e-30)
+
+
+def _expected_choice(a, fx, fy, dx, dy, v):
+    cands = [_lstsq_cross(a[v, :5], fx[:, v], fy[:, v], dx, dy, sx, sy) for sx, sy in _STENCILS]
+    return cands
+
+
+def test_cross_derivative_keeps_the_smallest_stencil():
+    """Section 3.2: of the four one-sided cross derivatives the one with the smallest absolute
+    value is kept.  Variable v of the cell is built so that stencil v is the smallest, with
+    a clear margin, so every position of the order is exercised and a reversed comparison,
+    a wrong sign in any stencil or the wrong face of a stencil changes the result."""
+    dx, dy = 0.04, 0.03
+    rng = np.random.default_rng(17)
+    z = np.zeros((4, 4))
+    a = None
+    for v in range(4):
+        for _ in range(1000):
+            z[:, v] = rng.normal(scale=2e-4, size=4)
+            a, nb, fx, fy = _cell_with_face_differences(11, dx, dy, z)
+            c = np.abs(_expected_choice(a, fx, fy, dx, dy, v))
+            order = np.argsort(c)
+            if order[0] == v and c[order[1]] > 1.3 * c[order[0]]:
+                break
+        else:
+            raise AssertionError("no draw makes stencil %d the smallest" % v)
+    a, nb, fx, fy = _cell_with_face_differences(11, dx, dy, z)
+    got = oracle.recon_cell(oracle.params(**_ONE_SIDED), nb, fx, fy, dx, dy)
+    # the face means are untouched: the limited one-sided a2..a5 are the quadratic's
+    np.testing.assert_allclose(got[:, :5], a[:, :5], rtol=1e-9, atol=1e-9)
+    for v in range(4):
+        cands = _expected_choice(a, fx, fy, dx, dy, v)
+        assert int(np.argmin(np.abs(cands))) == v
+        assert got[v, 5] == pytest.approx(cands[v], rel=1e-9, abs=1e-9), (v, cands)
+        # and it is not any of the other three
+        for k in range(4):
+            if k != v:
+                assert abs(got[v, 5] - cands[k]) > 1e-3 * abs(cands[k] - cands[v])
+
+
+# (z_east, z_west, z_north, z_south) in units of tau, and the stencil whose a6 is kept:
+# in each case two candidates tie at +-k tau (opposite signs) and the other two are
+# 9 k tau and 11 k tau, with k = 2 sqrt(3) / (dx dy); the earlier stencil of the tie wins
+_TIES = [
+    ((1, 1, 0, -10), 0),   # (+,+) = k tau, (-,+) = -k tau
+    ((10, 0, 1, 1), 1),    # (-,+) = k tau, (-,-) = -k tau
+    ((1, 1, 10, 0), 2),    # (-,-) = -k tau, (+,-) = k tau
+    ((0, -10, 1, 1), 0),   # (+,+) = k tau, (+,-) = -k tau
+]
+
+
+@pytest.mark.parametrize("zs,keep", _TIES)
+def test_cross_derivative_tie_keeps_the_earlier_stencil(zs, keep):
+    """The paper gives no tie rule; the reading keeps the first stencil of the order
+    (+,+), (-,+), (-,-), (+,-).  Exact ties of opposite sign are built from the face
+    differences alone (quadratic cross term zero), for each adjacent pair of the order."""
+    dx, dy = 0.05, 0.04
+    tau = 3e-5
+    z = np.array([[zz * tau] * 4 for zz in zs])
+    a, nb, fx, fy = _cell_with_face_differences(4, dx, dy, z)
+    a6 = a[:, 5].copy()
+    # remove the quadratic's own cross term so that the two tied candidates are exactly +-k tau
+    for k in range(2):
+        fx[k] -= a6 * (dx / 2) * (-G * dy if k == 0 else G * dy)
+        fx[2 + k] -= a6 * (-dx / 2) * (-G * dy if k == 0 else G * dy)
+        fy[k] -= a6 * (-G * dx if k == 0 else G * dx) * (dy / 2)
+        fy[2 + k] -= a6 * (-G * dx if k == 0 else G * dx) * (-dy / 2)
+    kk = 2 * math.sqrt(3.0) / (dx * dy)
+    got = oracle.recon_cell(oracle.params(**_ONE_SIDED), nb, fx, fy, dx, dy)
+    for v in range(4):
+        cands = _expected_choice(a, fx, fy, dx, dy, v)
+        mags = sorted(abs(c) for c in cands)
+        assert mags[0] == pytest.approx(kk * tau, rel=1e-9) and mags[1] == pytest.approx(kk * tau, rel=1e-9)
+        assert mags[2] > 8 * kk * tau
+        assert got[v, 5] == pytest.approx(cands[keep], rel=1e-7), (v, cands, keep)
+
+
+def _indicator_by_quadrature(q, dx, dy):
+    """I(U) = dx^2 <Ux^2> + dy^2 <Uy^2> + dx^4 Uxx^2 + dx^2 dy^2 Uxy^2 + dy^4 Uyy^2 for
+    U = q0 + q1 x + q2 y + q3 wx + q4 wy + q5 x y, with the cell means <.> taken by a 3 x 3
+    Gauss-Legendre rule (exact for these quadratics)."""
+    t, w = np.polynomial.legendre.leggauss(3)
+    X, Y = np.meshgrid(t * dx / 2, t * dy / 2, indexing="ij")
+    W = np.outer(w, w) / 4.0
+    ux = q[1] + q[3] * X + q[5] * Y
+    uy = q[2] + q[4] * Y + q[5] * X
+    return (dx * dx * np.sum(W * ux * ux) + dy * dy * np.sum(W * uy * uy) + dx ** 4 * q[3] ** 2
+            + dx * dx * dy * dy * q[5] ** 2 + dy ** 4 * q[4] ** 2)
+
+
+@pytest.mark.parametrize("eps_rel", [0.0, 1.0])
+def test_nonlinear_weights_follow_the_inverse_square(eps_rel):
+    """Eq. average: omega_i = alpha_i / sum alpha, alpha_i = 1 / (eps + I(U_i))^2, with
+    I(U_1) = C dx dy.  The cell is a quadratic Q whose face Gauss values are all shifted
+    by a constant per face: the central polynomial (averages and face differences) stays Q,
+    the one-sided one does not.  Every output coefficient is then
+    Q_k + omega_1(C) (one-sided_k - Q_k), with the one-sided part independent of C, so for
+    three values of C the ratio of output differences equals that of omega_1 alone -- which
+    fixes the exponent 2 and the place of eps, given I(Q) by quadrature."""
+    dx, dy = 0.05, 0.035
+    a, nb, fx, fy = _quadratic_cell(21, dx, dy)
+    shift = np.array([[2e-3, -1e-3, 5e-4, 1.5e-3], [-8e-4, 1.2e-3, -2e-3, 7e-4],
+                      [1e-3, 6e-4, -1.1e-3, -9e-4], [-1.4e-3, -5e-4, 9e-4, 1.6e-3]])  # [face][var]
+    fx = fx.copy(); fy = fy.copy()
+    fx[0] += shift[0]; fx[1] += shift[0]
+    fx[2] += shift[1]; fx[3] += shift[1]
+    fy[0] += shift[2]; fy[1] += shift[2]
+    fy[2] += shift[3]; fy[3] += shift[3]
+    A = dx * dy
+    checked = 0
+    for v in range(4):
+        I2 = _indicator_by_quadrature(a[v], dx, dy)
+        eps = eps_rel * I2
+        Cs = [0.3 * I2 / A, I2 / A, 3.0 * I2 / A]
+        outs = []
+        for C in Cs:
+            P = oracle.params(weno_eps=eps, weno_C=C)
+            outs.append(oracle.recon_cell(P, nb, fx, fy, dx, dy)[v])
+        w1 = [(eps + I2) ** 2 / ((eps + C * A) ** 2 + (eps + I2) ** 2) for C in Cs]
+        want = (w1[0] - w1[1]) / (w1[1] - w1[2])
+        for k in range(1, 6):
+            d01, d12 = outs[0][k] - outs[1][k], outs[1][k] - outs[2][k]
+            if abs(d12) < 1e-6 * max(1.0, abs(a[v, k])):
+                continue  # this coefficient's one-sided value equals the central one
+            assert d01 / d12 == pytest.approx(want, rel=1e-7), (v, k)
+            # and the output lies on the segment at omega_1 from the central value Q_k
+            one_sided = a[v, k] + (outs[1][k] - a[v, k]) / w1[1]
+            assert outs[0][k] == pytest.approx(a[v, k] + w1[0] * (one_sided - a[v, k]), rel=1e-8, abs=1e-10)
+            checked += 1
+    assert checked >= 8
