@@ -294,23 +294,26 @@ gks_status gks_measure_alu_peak(int precision, double* tflops);
  *
  * One FP64 time step (the same kernels as gks_step) from the caller's device
  * arrays dU, dWx, dWy (state layouts above, FP64, on the current device) into
- * the caller's device arrays dU_out, dWx_out, dWy_out (must not alias the
- * inputs), with dt = min(CFL * dt_cfl, dt_max) written to *dt_taken (may be
- * NULL).  The other arguments mean what they mean for gks_create (opt may be
- * NULL; its precision must be GKS_FP64).  Work is queued on cuda_stream (NULL =
- * the legacy default stream) and the call waits for it.
+ * the caller's device arrays dU_out, dWx_out, dWy_out, with dt = min(CFL *
+ * dt_cfl, dt_max) written to *dt_taken (may be NULL).  An output that overlaps
+ * an input or another output is rejected with GKS_EINVAL.  The other arguments
+ * mean what they mean for gks_create (opt may be NULL; its precision must be
+ * GKS_FP64).  The call is synchronous: its work is queued on cuda_stream (NULL =
+ * the legacy default stream) and it returns after that work has finished.
  *
  * It calls no cudaMalloc, cudaFree or allocating library routine: its scratch
  * (cell averages before and after, reconstruction coefficients, face fluxes and
- * a control block) is one static 32 MiB device array inside this library, which
- * every GPU that loads the library holds until the process exits.  Grids of more
- * than 65,536 cells are rejected with GKS_EINVAL and a message in
- * gks_last_error(NULL).  Every call shares that array and leaves its contents
+ * a control block) is one static 34 MiB device array inside this library, which
+ * every GPU that loads the library holds until the process exits.  Every grid
+ * of up to 65,536 cells fits; larger grids are rejected with GKS_EINVAL and a
+ * message in gks_last_error(NULL).  Every call shares that array and leaves its contents
  * behind; the control block is cleared at the start of each call.  Calls whose
  * work overlaps on the GPU (from several threads or streams) race on the array
  * and must be serialised by the caller.  The first call on a device looks up the
  * array's device address (once per device, with that device current); make that
- * first call before any stream capture.  Returns GKS_ENONPHYSICAL (outputs not
+ * first call before any stream capture.  The address is kept for the life of the
+ * process, so the device's primary context must not be reset (cudaDeviceReset)
+ * between calls.  Returns GKS_ENONPHYSICAL (outputs not
  * valid) if the new state is not physical, GKS_EINVAL if dt would be 0. */
 gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, double gamma, double Pr, double mu,
                             const gks_bc* bc, const gks_options* opt, const double* dU,

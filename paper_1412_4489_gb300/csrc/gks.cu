@@ -898,12 +898,15 @@ gks_status gks_debug_flux(gks_handle* h, double dt, double* Fx, double* Fy, doub
 // ===========================================================================
 namespace {
 
-constexpr size_t kNoallocBytes = (size_t)32 << 20;  // 32 MiB: any grid of up to 65,536 cells
+// 34 MiB: any grid of up to 65,536 cells.  The padded cell planes make the need largest
+// for a single column (nx = 1, rows padded to 4): 33,620,992 bytes at 1 x 65,536.
+constexpr size_t kNoallocBytes = (size_t)34 << 20;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
 
-// device address of g_noalloc_scratch per device, looked up once with the device current
+// device address of g_noalloc_scratch per device, looked up once with the device current;
+// the cache assumes that the device's primary context is never reset (cudaDeviceReset)
 void* noalloc_base(int device, std::string& why) {
   static std::atomic<void*> base[64];
   if (device < 0 || device >= 64) { why = "device index out of range"; return nullptr; }
@@ -946,6 +949,20 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
     g_create_err = "gks_step_noalloc: all six state pointers, CFL > 0 and dt_max > 0 are required";
     return GKS_EINVAL;
   }
+  {
+    // outputs must not overlap inputs or each other: the face kernels write new face values
+    // that other faces' reconstruction still reads, and the update reads the old averages
+    const size_t nu = (size_t)4 * nx * ny, nwx = (size_t)8 * ny * (nx + 1), nwy = (size_t)8 * (ny + 1) * nx;
+    const struct { const double* p; size_t n; } in[3] = {{dU, nu}, {dWx, nwx}, {dWy, nwy}},
+                                                 out[3] = {{dU_out, nu}, {dWx_out, nwx}, {dWy_out, nwy}};
+    auto overlap = [](const double* a, size_t na, const double* b, size_t nb) { return a < b + nb && b < a + na; };
+    for (int k = 0; k < 3; ++k)
+      for (int m = 0; m < 3; ++m)
+        if (overlap(out[k].p, out[k].n, in[m].p, in[m].n) || (m > k && overlap(out[k].p, out[k].n, out[m].p, out[m].n))) {
+          g_create_err = "gks_step_noalloc: the output arrays must not overlap the inputs or each other";
+          return GKS_EINVAL;
+        }
+  }
   Geo g;
   make_geo(g, nx, ny, Lx, Ly, gamma, Pr, mu, bc, o);
   // scratch layout: control block | padded U before | padded U after | coefficients | Fx | Fy
@@ -957,7 +974,7 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
   const size_t b_bad = align256((size_t)nx * ny);
   const size_t need = b_ctrl + 2 * b_u + b_coef + b_fx + b_fy + b_bad;
   if ((long long)nx * ny > 65536 || need > kNoallocBytes) {
-    g_create_err = "gks_step_noalloc: grid too large for the static scratch (at most 65,536 cells, " +
+    g_create_err = "gks_step_noalloc: grid too large for the static scratch (at most 65,536 cells; " +
                    std::to_string(kNoallocBytes >> 20) + " MiB); need " + std::to_string(need) + " bytes";
     return GKS_EINVAL;
   }
