@@ -303,7 +303,7 @@ gks_status gks_measure_alu_peak(int precision, double* tflops);
  *
  * It calls no cudaMalloc, cudaFree or allocating library routine: its scratch
  * (cell averages before and after, reconstruction coefficients, face fluxes and
- * a control block) is one static 34 MiB device array inside this library, which
+ * a control block) is one static 60 MiB device array inside this library, which
  * every GPU that loads the library holds until the process exits.  Every grid
  * of up to 65,536 cells fits; larger grids are rejected with GKS_EINVAL and a
  * message in gks_last_error(NULL).  Every call shares that array and leaves its contents

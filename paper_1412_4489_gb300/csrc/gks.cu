@@ -66,7 +66,7 @@ __global__ void k_ghost(Geo g, Cells<R> U0, Cells<R> U1, const Ctrl* c, int forc
 // CHAR: reconstruction in characteristic variables.
 template <class R, class TW, bool CHAR>
 __global__ void __launch_bounds__(256) k_recon(Geo g, const R* U0, const R* U1, const TW* Wx0, const TW* Wx1,
-                                               const TW* Wy0, const TW* Wy1, R* __restrict__ coef, R dx, R dy,
+                                               const TW* Wy0, const TW* Wy1, R* __restrict__ rec, R dx, R dy,
                                                R weps, R wC, Ctrl* c, int force, int begin, double cfl,
                                                double dt_max, double t_end) {
   pdl_enter();
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_recon(Geo g, const R* U0, const R* U1, 
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
   const int par = (int)(c->steps & 1);
-  recon_cell<R, TW, CHAR>(g, par ? U1 : U0, par ? Wx1 : Wx0, par ? Wy1 : Wy0, coef, i, j, dx, dy, weps, wC);
+  recon_cell<R, TW, CHAR>(g, par ? U1 : U0, par ? Wx1 : Wx0, par ? Wy1 : Wy0, rec, i, j, dx, dy, weps, wC);
 }
 
 // ---------------------------------------------------------------------------
@@ -98,9 +98,9 @@ template <> struct FluxBlocks<float> { static constexpr int value = GKS_FLUX_MIN
 
 // NS: Navier-Stokes (1) or Euler (0) face routine, chosen per grid by flux_kernel
 template <int AX, class R, class TW, int NS>
-__global__ void __launch_bounds__(128, FluxBlocks<R>::value) k_flux(Geo g, FaceConst<R> C, const R* U0, const R* U1,
-                                                                    const R* __restrict__ coef, TW* Wn0, TW* Wn1,
-                                                                    R* __restrict__ F, const Ctrl* c, int force) {
+__global__ void __launch_bounds__(128, FluxBlocks<R>::value) k_flux(Geo g, FaceConst<R> C, const R* __restrict__ rec,
+                                                                    TW* Wn0, TW* Wn1, R* __restrict__ F,
+                                                                    const Ctrl* c, int force) {
   pdl_enter();
   if (!force && c->skip) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(128, FluxBlocks<R>::value) k_flux(Geo g, FaceC
   if (i >= fx || j >= fy) return;
   const int par = (int)(c->steps & 1);
   // new face values go to the other buffer
-  flux_face<AX, R, TW, NS>(g, C, par ? U1 : U0, coef, par ? Wn0 : Wn1, F, i, j, step_dt<R>(c));
+  flux_face<AX, R, TW, NS>(g, C, rec, par ? Wn0 : Wn1, F, i, j, step_dt<R>(c));
 }
 
 template <int AX, class R, class TW>
@@ -250,15 +250,16 @@ __global__ void k_init_W(Geo g, Cells<TW> U0, Cells<TW> U1, TW* W0, TW* W1, cons
 }
 
 template <class R>
-__global__ void k_coef_out(Geo g, Cells<R> U0, Cells<R> U1, const R* coef, double* out, const Ctrl* c) {
+__global__ void k_coef_out(Geo g, Cells<R> U0, Cells<R> U1, const R* rec, double* out, const Ctrl* c) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
   const Cells<R> U = (c->steps & 1) ? U1 : U0;
   const size_t N = (size_t)g.nx * g.ny, o = (size_t)j * g.nx + i;
+  const R* r = rec + ri(g, i, j);
   for (int v = 0; v < 4; ++v) {
     out[(size_t)(v * 6) * N + o] = U.get(g, v, i, j);
-    for (int k = 0; k < 5; ++k) out[(size_t)(v * 6 + k + 1) * N + o] = (double)coef[(size_t)(k * 4 + v) * N + o];
+    for (int k = 0; k < 5; ++k) out[(size_t)(v * 6 + k + 1) * N + o] = (double)r[4 + 4 * k + v];
   }
 }
 
@@ -291,7 +292,7 @@ struct gks_handle {
   double* U[2];      // cell averages (Cells<R>: FP64, or FP32 hi / lo planes), 4 * plane doubles each
   void* Wx[2];
   void* Wy[2];
-  void* coef;
+  void* rec;  // reconstruction records (rec_count(g) values of the compute type)
   void* Fx;
   void* Fy;
   unsigned char* bad;  // cells whose first update failed (positivity fallback)
@@ -365,7 +366,7 @@ cudaError_t launch_recon(gks_handle* h, int force, int begin = 0, double cfl = 0
   const dim3 b2(32, 8);
   return launch(pdl, g.characteristic ? k_recon<R, TW, true> : k_recon<R, TW, false>, grid2(g.nx, g.ny, b2), b2,
                 h->stream, g, cells<R>(h, 0), cells<R>(h, 1),
-         (const TW*)h->Wx[0], (const TW*)h->Wx[1], (const TW*)h->Wy[0], (const TW*)h->Wy[1], (R*)h->coef, R(g.dx),
+         (const TW*)h->Wx[0], (const TW*)h->Wx[1], (const TW*)h->Wy[0], (const TW*)h->Wy[1], (R*)h->rec, R(g.dx),
          R(g.dy), R(g.weno_eps), R(g.weno_C), h->ctrl, force, begin, cfl, dt_max, t_end);
 }
 
@@ -400,19 +401,17 @@ gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double 
     keep(cudaEventRecord(h->fork, s));
     keep(cudaStreamWaitEvent(h->side, h->fork, 0));
     keep(launch(false, flux_kernel<1, R, TW>(g), grid2(g.nx, g.ny + 1, bf), bf, h->side, g, fconst<R>(g, 1),
-                cells<R>(h, 0), cells<R>(h, 1), (const R*)h->coef, (TW*)h->Wy[0], (TW*)h->Wy[1], (R*)h->Fy,
-                (const Ctrl*)h->ctrl, force));
+                (const R*)h->rec, (TW*)h->Wy[0], (TW*)h->Wy[1], (R*)h->Fy, (const Ctrl*)h->ctrl, force));
     keep(cudaEventRecord(h->join, h->side));
   }
-  keep(launch(pdl, flux_kernel<0, R, TW>(g), grid2(g.nx + 1, g.ny, bf), bf, s, g, fconst<R>(g, 0), cells<R>(h, 0),
-         cells<R>(h, 1), (const R*)h->coef, (TW*)h->Wx[0], (TW*)h->Wx[1], (R*)h->Fx, (const Ctrl*)h->ctrl, force));
+  keep(launch(pdl, flux_kernel<0, R, TW>(g), grid2(g.nx + 1, g.ny, bf), bf, s, g, fconst<R>(g, 0), (const R*)h->rec,
+              (TW*)h->Wx[0], (TW*)h->Wx[1], (R*)h->Fx, (const Ctrl*)h->ctrl, force));
   mark(2);
   if (fork) {
     keep(cudaStreamWaitEvent(s, h->join, 0));
   } else {
-    keep(launch(pdl, flux_kernel<1, R, TW>(g), grid2(g.nx, g.ny + 1, bf), bf, s, g, fconst<R>(g, 1), cells<R>(h, 0),
-                cells<R>(h, 1), (const R*)h->coef, (TW*)h->Wy[0], (TW*)h->Wy[1], (R*)h->Fy, (const Ctrl*)h->ctrl,
-                force));
+    keep(launch(pdl, flux_kernel<1, R, TW>(g), grid2(g.nx, g.ny + 1, bf), bf, s, g, fconst<R>(g, 1),
+                (const R*)h->rec, (TW*)h->Wy[0], (TW*)h->Wy[1], (R*)h->Fy, (const Ctrl*)h->ctrl, force));
   }
   mark(3);
   for (int pass = 1; pass <= 3; ++pass) {
@@ -632,7 +631,7 @@ gks_status gks_create(int nx, int ny, double Lx, double Ly, double gamma, double
     alloc(&h->Wx[b], n_wx(g) * wsz);
     alloc(&h->Wy[b], n_wy(g) * wsz);
   }
-  alloc(&h->coef, (size_t)20 * nx * ny * wsz);
+  alloc(&h->rec, rec_count(g) * wsz);
   alloc(&h->Fx, (size_t)4 * ny * (nx + 1) * wsz);
   alloc(&h->Fy, (size_t)4 * (ny + 1) * nx * wsz);
   alloc((void**)&h->bad, (size_t)nx * ny);
@@ -795,7 +794,7 @@ void gks_destroy(gks_handle* h) {
     cudaFree(h->Wx[b]);
     cudaFree(h->Wy[b]);
   }
-  cudaFree(h->coef);
+  cudaFree(h->rec);
   cudaFree(h->Fx);
   cudaFree(h->Fy);
   cudaFree(h->bad);
@@ -846,12 +845,12 @@ gks_status gks_debug_recon(gks_handle* h, double* coef) {
     launch_ghost<double>(h, 1);
     launch_recon<double, double>(h, 1);
     k_coef_out<double><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, cellbuf<double>(h, 0), cellbuf<double>(h, 1),
-                                                                     (const double*)h->coef, h->staging, h->ctrl);
+                                                                     (const double*)h->rec, h->staging, h->ctrl);
   } else {
     launch_ghost<float>(h, 1);
     launch_recon<float, float>(h, 1);
     k_coef_out<float><<<grid2(g.nx, g.ny, b2), b2, 0, h->stream>>>(g, cellbuf<float>(h, 0), cellbuf<float>(h, 1),
-                                                                    (const float*)h->coef, h->staging, h->ctrl);
+                                                                    (const float*)h->rec, h->staging, h->ctrl);
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(coef, h->staging, (size_t)24 * g.nx * g.ny * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -898,9 +897,10 @@ gks_status gks_debug_flux(gks_handle* h, double dt, double* Fx, double* Fy, doub
 // ===========================================================================
 namespace {
 
-// 34 MiB: any grid of up to 65,536 cells.  The padded cell planes make the need largest
-// for a single column (nx = 1, rows padded to 4): 33,620,992 bytes at 1 x 65,536.
-constexpr size_t kNoallocBytes = (size_t)34 << 20;
+// 60 MiB: any grid of up to 65,536 cells.  The padded cell planes and the ghost ring of
+// the reconstruction records make the need largest for a single column (nx = 1, rows
+// padded to 4 and 3 records wide): 60,885,248 bytes at 1 x 65,536.
+constexpr size_t kNoallocBytes = (size_t)60 << 20;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
@@ -965,14 +965,14 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
   }
   Geo g;
   make_geo(g, nx, ny, Lx, Ly, gamma, Pr, mu, bc, o);
-  // scratch layout: control block | padded U before | padded U after | coefficients | Fx | Fy
+  // scratch layout: control block | padded U before | padded U after | reconstruction records | Fx | Fy
   const size_t b_ctrl = align256(sizeof(Ctrl));
   const size_t b_u = align256(4 * g.plane * sizeof(double));
-  const size_t b_coef = align256((size_t)20 * nx * ny * sizeof(double));
+  const size_t b_rec = align256(rec_count(g) * sizeof(double));
   const size_t b_fx = align256((size_t)4 * ny * (nx + 1) * sizeof(double));
   const size_t b_fy = align256((size_t)4 * (ny + 1) * nx * sizeof(double));
   const size_t b_bad = align256((size_t)nx * ny);
-  const size_t need = b_ctrl + 2 * b_u + b_coef + b_fx + b_fy + b_bad;
+  const size_t need = b_ctrl + 2 * b_u + b_rec + b_fx + b_fy + b_bad;
   if ((long long)nx * ny > 65536 || need > kNoallocBytes) {
     g_create_err = "gks_step_noalloc: grid too large for the static scratch (at most 65,536 cells; " +
                    std::to_string(kNoallocBytes >> 20) + " MiB); need " + std::to_string(need) + " bytes";
@@ -986,10 +986,10 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
   Ctrl* ctrl = (Ctrl*)base;
   double* U0 = (double*)(base + b_ctrl);
   double* U1 = (double*)(base + b_ctrl + b_u);
-  double* coef = (double*)(base + b_ctrl + 2 * b_u);
-  double* Fx = (double*)(base + b_ctrl + 2 * b_u + b_coef);
-  double* Fy = (double*)(base + b_ctrl + 2 * b_u + b_coef + b_fx);
-  unsigned char* bad = base + b_ctrl + 2 * b_u + b_coef + b_fx + b_fy;
+  double* rec = (double*)(base + b_ctrl + 2 * b_u);
+  double* Fx = (double*)(base + b_ctrl + 2 * b_u + b_rec);
+  double* Fy = (double*)(base + b_ctrl + 2 * b_u + b_rec + b_fx);
+  unsigned char* bad = base + b_ctrl + 2 * b_u + b_rec + b_fx + b_fy;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const dim3 b2(32, 8), bf(32, 4);
   const int per = perimeter(g);
@@ -1000,12 +1000,12 @@ extern "C" gks_status gks_step_noalloc(int nx, int ny, double Lx, double Ly, dou
   k_ghost<double><<<(per + 127) / 128, 128, 0, s>>>(g, C0, C1, ctrl, 1);
   k_dtbound<double><<<grid2(nx, ny, b2), b2, 0, s>>>(g, C0, C1, ctrl);
   (g.characteristic ? k_recon<double, double, true> : k_recon<double, double, false>)<<<grid2(nx, ny, b2), b2, 0, s>>>(
-      g, U0, U1, dWx, dWx_out, dWy, dWy_out, coef, g.dx, g.dy,
+      g, U0, U1, dWx, dWx_out, dWy, dWy_out, rec, g.dx, g.dy,
                                                             g.weno_eps, g.weno_C, ctrl, 0, 1, CFL,
                                                             dt_max, INFINITY);
-  flux_kernel<0, double, double>(g)<<<grid2(nx + 1, ny, bf), bf, 0, s>>>(g, fconst<double>(g, 0), U0, U1, coef,
+  flux_kernel<0, double, double>(g)<<<grid2(nx + 1, ny, bf), bf, 0, s>>>(g, fconst<double>(g, 0), rec,
                                                                   const_cast<double*>(dWx), dWx_out, Fx, ctrl, 0);
-  flux_kernel<1, double, double>(g)<<<grid2(nx, ny + 1, bf), bf, 0, s>>>(g, fconst<double>(g, 1), U0, U1, coef,
+  flux_kernel<1, double, double>(g)<<<grid2(nx, ny + 1, bf), bf, 0, s>>>(g, fconst<double>(g, 1), rec,
                                                                   const_cast<double*>(dWy), dWy_out, Fy, ctrl, 0);
   for (int pass = 1; pass <= 3; ++pass)
     k_update<double, double><<<update_grid(g, pass, 0, UpdateBlocks<double>::value), b2, 0, s>>>(g, C0, C1, Fx, Fy, const_cast<double*>(dWx), dWx_out,

@@ -33,7 +33,7 @@ constexpr int kThreads = 128;  // one work tile = one block = 128 cells or faces
 struct GridOff {
   size_t u;     // padded cell arrays (4 * plane doubles: Cells<R>)
   size_t wx, wy;
-  size_t coef;  // 20 * nx * ny
+  size_t rec;   // rec_count: reconstruction records with the ghost ring
   size_t fx, fy;
   size_t bad;   // nx * ny flags of the positivity fallback
 };
@@ -57,7 +57,7 @@ struct Args {
   double* U[2];
   TW* Wx[2];
   TW* Wy[2];
-  R* coef;
+  R* rec;
   R* Fx;
   R* Fy;
   unsigned char* bad;
@@ -140,10 +140,10 @@ __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<
       const GridOff& o = a.off[w.x];
       const R* U = (const R*)(a.U[par] + o.u);
       if (g.characteristic)
-        recon_cell<R, TW, true>(g, U, a.Wx[par] + o.wx, a.Wy[par] + o.wy, a.coef + o.coef, i, j, GeoR<R>::dx(g),
+        recon_cell<R, TW, true>(g, U, a.Wx[par] + o.wx, a.Wy[par] + o.wy, a.rec + o.rec, i, j, GeoR<R>::dx(g),
                                 GeoR<R>::dy(g), GeoR<R>::weps(g), GeoR<R>::wC(g));
       else
-        recon_cell<R, TW, false>(g, U, a.Wx[par] + o.wx, a.Wy[par] + o.wy, a.coef + o.coef, i, j,
+        recon_cell<R, TW, false>(g, U, a.Wx[par] + o.wx, a.Wy[par] + o.wy, a.rec + o.rec, i, j,
                                  GeoR<R>::dx(g), GeoR<R>::dy(g), GeoR<R>::weps(g), GeoR<R>::wC(g));
     }
     if (!grid_barrier(a.bar)) return;
@@ -161,10 +161,10 @@ __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<
       const R dt = step_dt<R>(c);
       if (w.w == 0) {
         if (i <= g.nx && j < g.ny)
-          flux_face<0, R, TW, NSM>(g, a.fc[2 * w.x], U, a.coef + o.coef, a.Wx[par ^ 1] + o.wx, a.Fx + o.fx, i, j, dt);
+          flux_face<0, R, TW, NSM>(g, a.fc[2 * w.x], a.rec + o.rec, a.Wx[par ^ 1] + o.wx, a.Fx + o.fx, i, j, dt);
       } else {
         if (i < g.nx && j <= g.ny)
-          flux_face<1, R, TW, NSM>(g, a.fc[2 * w.x + 1], U, a.coef + o.coef, a.Wy[par ^ 1] + o.wy, a.Fy + o.fy, i, j,
+          flux_face<1, R, TW, NSM>(g, a.fc[2 * w.x + 1], a.rec + o.rec, a.Wy[par ^ 1] + o.wy, a.Fy + o.fy, i, j,
                                    dt);
       }
     }
@@ -278,7 +278,7 @@ struct gks_batch {
   double* U[2];  // per grid 4 * plane doubles at off.u (Cells<R>)
   void* Wx[2];
   void* Wy[2];
-  void* coef;
+  void* rec;
   void* Fx;
   void* Fy;
   unsigned char* bad;
@@ -355,7 +355,7 @@ Args<R, TW> make_args(gks_batch* b, double cfl) {
     a.Wx[k] = (TW*)b->Wx[k];
     a.Wy[k] = (TW*)b->Wy[k];
   }
-  a.coef = (R*)b->coef;
+  a.rec = (R*)b->rec;
   a.Fx = (R*)b->Fx;
   a.Fy = (R*)b->Fy;
   a.bad = b->bad;
@@ -472,7 +472,7 @@ gks_status gks_batch_create(int n, const gks_grid_desc* grids, const gks_options
     nu = (nu + 31) & ~(size_t)31;
     of.wx = nwx; nwx += (size_t)8 * d.ny * (d.nx + 1);
     of.wy = nwy; nwy += (size_t)8 * (d.ny + 1) * d.nx;
-    of.coef = nc; nc += (size_t)20 * d.nx * d.ny;
+    of.rec = nc; nc += rec_count(G);
     of.fx = nfx; nfx += (size_t)4 * d.ny * (d.nx + 1);
     of.fy = nfy; nfy += (size_t)4 * (d.ny + 1) * d.nx;
     of.bad = nbad; nbad += (size_t)d.nx * d.ny;
@@ -500,7 +500,7 @@ gks_status gks_batch_create(int n, const gks_grid_desc* grids, const gks_options
     alloc(&b->Wx[k], nwx * ws);
     alloc(&b->Wy[k], nwy * ws);
   }
-  alloc(&b->coef, nc * ws);
+  alloc(&b->rec, nc * ws);
   alloc(&b->Fx, nfx * ws);
   alloc(&b->Fy, nfy * ws);
   alloc((void**)&b->bad, nbad);
@@ -805,7 +805,7 @@ void gks_batch_destroy(gks_batch* b) {
     cudaFree(b->Wx[k]);
     cudaFree(b->Wy[k]);
   }
-  cudaFree(b->coef);
+  cudaFree(b->rec);
   cudaFree(b->Fx);
   cudaFree(b->Fy);
   cudaFree(b->bad);

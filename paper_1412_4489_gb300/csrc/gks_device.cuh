@@ -64,18 +64,19 @@ struct Moments {
   R xi2, xi4;
 };
 
-// kind: 0 full space, +1 over u > 0, -1 over u < 0
+// kind: 0 full space, +1 over u > 0, -1 over u < 0; var = 1/(2 lam) = p/rho, formed
+// once per Maxwellian by the caller
 template <class R, int NU, int NV>
-GKS_FN void moments(R U, R V, R lam, R K, int kind, Moments<R, NU, NV>& m) {
-  const R var = d_div(R(0.5), lam);
+GKS_FN void moments(R U, R V, R lam, R var, R K, int kind, Moments<R, NU, NV>& m) {
   if (kind == 0) {
     m.u[0] = R(1);
     m.u[1] = U;
   } else {
-    const R s = d_sqrt(lam);
+    const R rs = d_rsqrt(lam);
+    const R s = lam * rs;  // sqrt(lam)
     const R h = R(0.5) * d_erfc(-R(kind) * s * U);
     // boundary term of the integration by parts at u = 0
-    const R b = d_exp(-lam * U * U) * R(0.28209479177387814) * d_rsqrt(lam);  // 1/(2 sqrt(pi lam))
+    const R b = d_exp(-lam * U * U) * R(0.28209479177387814) * rs;  // 1/(2 sqrt(pi lam))
     m.u[0] = h;
     m.u[1] = U * h + R(kind) * b;
   }
@@ -93,8 +94,7 @@ GKS_FN void moments(R U, R V, R lam, R K, int kind, Moments<R, NU, NV>& m) {
 // The same half-space moments from their first two entries h = <u^0>, g = <u^1>
 // (already formed once for the same Maxwellian: no second erfc and exp).
 template <class R, int NU, int NV>
-GKS_FN void moments_from(R U, R V, R lam, R K, R h, R g, Moments<R, NU, NV>& m) {
-  const R var = d_div(R(0.5), lam);
+GKS_FN void moments_from(R U, R V, R var, R K, R h, R g, Moments<R, NU, NV>& m) {
   m.u[0] = h;
   m.u[1] = g;
 #pragma unroll
@@ -182,16 +182,16 @@ struct SolveK {
 };
 
 template <class R>
-GKS_FN SolveK<R> solve_k(R U, R V, R lam, R N, R iN) {
+GKS_FN SolveK<R> solve_k(R U, R V, R lam, R var, R N, R iN) {
   SolveK<R> k;
   const R q2 = U * U + V * V;
-  const R nl = d_div(N, lam);
+  const R nv = N * var;  // N / (2 lam)
   k.U = U;
   k.V = V;
   k.l2 = R(2) * lam;
   k.c4 = R(4) * lam * lam * iN;
-  k.s0 = q2 - R(0.5) * nl;
-  k.s1 = R(0.5) * q2 + R(0.25) * nl;
+  k.s0 = q2 - nv;
+  k.s1 = R(0.5) * (q2 + nv);
   return k;
 }
 
@@ -201,6 +201,19 @@ GKS_FN void solve(const SolveK<R>& k, const R r[4], R x[4]) {
   const R x3 = k.l2 * (r[2] - k.V * r[0]) - k.V * x4;
   const R x2 = k.l2 * (r[1] - k.U * r[0]) - k.U * x4;
   x[0] = r[0] - k.U * x2 - k.V * x3 - x4 * k.s1;
+  x[1] = x2;
+  x[2] = x3;
+  x[3] = x4;
+}
+
+// the same for <a> = rho r with r = ir d, ir = 1/rho folded into the factors:
+// c4i = c4 ir, l2i = l2 ir
+template <class R>
+GKS_FN void solve_scaled(const SolveK<R>& k, R c4i, R l2i, R ir, const R d[4], R x[4]) {
+  const R x4 = c4i * (R(2) * (d[3] - k.U * d[1] - k.V * d[2]) + k.s0 * d[0]);
+  const R x3 = l2i * (d[2] - k.V * d[0]) - k.V * x4;
+  const R x2 = l2i * (d[1] - k.U * d[0]) - k.U * x4;
+  x[0] = ir * d[0] - k.U * x2 - k.V * x3 - x4 * k.s1;
   x[1] = x2;
   x[2] = x3;
   x[3] = x4;
@@ -285,27 +298,18 @@ struct Coefs {
   R a1[4], a2[4], Axx[4], Axy[4], Ayy[4], A[4], Atx[4], Aty[4], Att[4];
 };
 
+// ir = 1/rho of the Maxwellian
 template <class R, int NU, int NV>
-GKS_FN void coef_systems(const Moments<R, NU, NV>& m, R rho, const SolveK<R>& sk, const R d[5][4],
+GKS_FN void coef_systems(const Moments<R, NU, NV>& m, R ir, const SolveK<R>& sk, const R d[5][4],
                          bool time_terms, bool second_time, Coefs<R>& c) {
-  const R ir = d_div(R(1), rho);
-  R r[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) r[k] = d[0][k] * ir;
-  solve(sk, r, c.a1);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) r[k] = d[1][k] * ir;
-  solve(sk, r, c.a2);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) r[k] = d[2][k] * ir;
-  solve(sk, r, c.Axx);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) r[k] = d[3][k] * ir;
-  solve(sk, r, c.Axy);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) r[k] = d[4][k] * ir;
-  solve(sk, r, c.Ayy);
+  const R c4i = sk.c4 * ir, l2i = sk.l2 * ir;
+  solve_scaled(sk, c4i, l2i, ir, d[0], c.a1);
+  solve_scaled(sk, c4i, l2i, ir, d[1], c.a2);
+  solve_scaled(sk, c4i, l2i, ir, d[2], c.Axx);
+  solve_scaled(sk, c4i, l2i, ir, d[3], c.Axy);
+  solve_scaled(sk, c4i, l2i, ir, d[4], c.Ayy);
   if (!time_terms) return;
+  R r[4];
   MomTab<R> t;
   mom_tab(m, t);
   neg_coef_mom(t, c.a1, c.a2, r);  // <A + a1 u + a2 v> = 0
@@ -411,7 +415,7 @@ GKS_FN void poly_moments(const Poly<R>& P, const Moments<R, NU, NV>& m, R rho, R
       o0 = first ? s0 * vb : o0 + s0 * vb;
       o1 = first ? s1 * vb : o1 + s1 * vb;
       o2 = first ? s0 * vb1 : o2 + s0 * vb1;
-      o3 = first ? s2 * vb + s0 * vb2 : o3 + (s2 * vb + s0 * vb2);
+      o3 = first ? s2 * vb + s0 * vb2 : o3 + s2 * vb + s0 * vb2;
     }
   }
   out[0] += rho * o0;
@@ -508,12 +512,12 @@ struct FaceState {
 };
 
 template <class R>
-GKS_FN void prim(const R w[4], R gm1, R& rho, R& U, R& V, R& p) {
+GKS_FN void prim(const R w[4], R gm1, R& rho, R& ir, R& U, R& V, R& p) {
   rho = w[0];
-  const R ir = d_div(R(1), rho);
+  ir = d_div(R(1), rho);
   U = w[1] * ir;
   V = w[2] * ir;
-  p = gm1 * (w[3] - R(0.5) * rho * (U * U + V * V));
+  p = gm1 * (w[3] - R(0.5) * (w[1] * U + w[2] * V));
 }
 
 struct FaceParams {
@@ -660,17 +664,20 @@ GKS_FN void wall_image(int kind, R gamma, R uwt, R Tw, const FaceState<R>& in, F
 template <class R, int NSM = -1, class Src>
 GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], R Wm[4], R Wp[4]) {
   const bool ns = NSM < 0 ? C.ns : NSM == 1;
-  R rs[2], us[2], vs[2], ls[2], ps[2], h0[2], h1[2];
+  // per side: rho, 1/rho, U, V, lam = rho / (2 p), 1 / (2 lam) = p / rho, p, and the
+  // half-space <u^0>, <u^1>
+  R rs[2], irs[2], us[2], vs[2], ls[2], vrs[2], ps[2], h0[2], h1[2];
   R U0[4] = {R(0), R(0), R(0), R(0)};
   // Eq. compatibility2: U0 = rho_l <psi>_{u>0} + rho_r <psi>_{u<0}
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     FaceState<R> S;
     src.side(k, S);
-    prim(S.w[0], C.gm1, rs[k], us[k], vs[k], ps[k]);
+    prim(S.w[0], C.gm1, rs[k], irs[k], us[k], vs[k], ps[k]);
     ls[k] = d_div(R(0.5) * rs[k], ps[k]);
+    vrs[k] = ps[k] * irs[k];
     Moments<R, 4, 3> m;
-    moments(us[k], vs[k], ls[k], C.K, k == 0 ? +1 : -1, m);
+    moments(us[k], vs[k], ls[k], vrs[k], C.K, k == 0 ? +1 : -1, m);
     h0[k] = m.u[0];
     h1[k] = m.u[1];
     R a[4];
@@ -678,9 +685,9 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
 #pragma unroll
     for (int v = 0; v < 4; ++v) U0[v] += rs[k] * a[v];
   }
-  R r0, u0, v0, p0;
-  prim(U0, C.gm1, r0, u0, v0, p0);
-  const R lam0 = d_div(R(0.5) * r0, p0);
+  R r0, ir0, u0, v0, p0;
+  prim(U0, C.gm1, r0, ir0, u0, v0, p0);
+  const R lam0 = d_div(R(0.5) * r0, p0), var0 = p0 * ir0;
 
   // Section 4: collision time
   const R jump = fabs(d_div(ps[0] - ps[1], ps[0] + ps[1])) * dt;
@@ -711,9 +718,9 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
       }
     }
     Moments<R, 8, 7> m;
-    moments(u0, v0, lam0, C.K, 0, m);
+    moments(u0, v0, lam0, var0, C.K, 0, m);
     Coefs<R> c;
-    coef_systems(m, r0, solve_k(u0, v0, lam0, C.N, C.iN), d, true, true, c);
+    coef_systems(m, ir0, solve_k(u0, v0, lam0, var0, C.N, C.iN), d, true, true, c);
     Groups<R> g;
     hydro_groups(c, tw.I, C.y2, g);
     add_flux(g, m, r0, Fl);
@@ -736,6 +743,7 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
     // selects, not indexing: a dynamic index would put these arrays in local memory
     const R rho = side ? rs[1] : rs[0], U = side ? us[1] : us[0];
     const R V = side ? vs[1] : vs[0], lam = side ? ls[1] : ls[0];
+    const R ir = side ? irs[1] : irs[0], var = side ? vrs[1] : vrs[0];
     Coefs<R> c;
     {
       R d[5][4];
@@ -748,11 +756,11 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
           for (int k = 0; k < 4; ++k) d[q][k] = S.w[q + 1][k];
       }
       Moments<R, 6, 6> mf;  // full-space moments fix the time coefficients of g_k (NS only)
-      if (ns) moments(U, V, lam, C.K, 0, mf);
-      coef_systems(mf, rho, solve_k(U, V, lam, C.N, C.iN), d, ns, false, c);
+      if (ns) moments(U, V, lam, var, C.K, 0, mf);
+      coef_systems(mf, ir, solve_k(U, V, lam, var, C.N, C.iN), d, ns, false, c);
     }
     Moments<R, 8, 7> mh;
-    moments_from(U, V, lam, C.K, side ? h0[1] : h0[0], side ? h1[1] : h1[0], mh);
+    moments_from(U, V, var, C.K, side ? h0[1] : h0[0], side ? h1[1] : h1[0], mh);
     Groups<R> g;
     R Y1[4], Yu[4], Yv[4];
     if (ns) {

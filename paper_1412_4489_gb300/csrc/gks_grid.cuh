@@ -52,6 +52,71 @@ __host__ __device__ __forceinline__ size_t ci(const Geo& g, int v, int i, int j)
   return (size_t)v * g.plane + (size_t)(j + 1) * g.pitch + (i + 1);
 }
 
+// ---------------------------------------------------------------------------
+// Reconstruction records.  Per cell, ghost ring included, the compute-type cell
+// average and the coefficient vectors a2..a6 of Section 3.2, four variables each:
+// 24 contiguous values (96 bytes in FP32, 192 in FP64), so that a face reads each
+// of its two cells with 16-byte loads from one address instead of gathering 24
+// values from separate planes.  Ghost records hold only the average (the images
+// of the ghost ring), which the equilibrium polynomial of Section 3.3 reads.
+//   [0..3] average, [4 + 4 (k - 2) + v] = a_k of variable v, k = 2..6
+// ---------------------------------------------------------------------------
+constexpr int kRec = 24;
+
+__host__ __device__ __forceinline__ size_t rec_count(const Geo& g) { return (size_t)(g.nx + 2) * (g.ny + 2) * kRec; }
+__host__ __device__ __forceinline__ size_t ri(const Geo& g, int i, int j) {
+  return ((size_t)(j + 1) * (g.nx + 2) + (i + 1)) * kRec;
+}
+
+template <class R> struct RecIO;
+template <> struct RecIO<float> {
+  static __device__ __forceinline__ void load(const float* __restrict__ p, float r[kRec]) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int k = 0; k < kRec / 4; ++k) {
+      const float4 t = q[k];
+      r[4 * k] = t.x; r[4 * k + 1] = t.y; r[4 * k + 2] = t.z; r[4 * k + 3] = t.w;
+    }
+  }
+  static __device__ __forceinline__ void load_avg(const float* __restrict__ p, float r[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    r[0] = t.x; r[1] = t.y; r[2] = t.z; r[3] = t.w;
+  }
+  static __device__ __forceinline__ void store(float* p, const float r[kRec]) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int k = 0; k < kRec / 4; ++k) q[k] = make_float4(r[4 * k], r[4 * k + 1], r[4 * k + 2], r[4 * k + 3]);
+  }
+  static __device__ __forceinline__ void store_avg(float* p, const float r[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+  }
+};
+template <> struct RecIO<double> {
+  static __device__ __forceinline__ void load(const double* __restrict__ p, double r[kRec]) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int k = 0; k < kRec / 2; ++k) {
+      const double2 t = q[k];
+      r[2 * k] = t.x; r[2 * k + 1] = t.y;
+    }
+  }
+  static __device__ __forceinline__ void load_avg(const double* __restrict__ p, double r[4]) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 a = q[0], b = q[1];
+    r[0] = a.x; r[1] = a.y; r[2] = b.x; r[3] = b.y;
+  }
+  static __device__ __forceinline__ void store(double* p, const double r[kRec]) {
+    double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+    for (int k = 0; k < kRec / 2; ++k) q[k] = make_double2(r[2 * k], r[2 * k + 1]);
+  }
+  static __device__ __forceinline__ void store_avg(double* p, const double r[4]) {
+    double2* q = reinterpret_cast<double2*>(p);
+    q[0] = make_double2(r[0], r[1]);
+    q[1] = make_double2(r[2], r[3]);
+  }
+};
+
 // derived fields: sizes of the padded arrays, reciprocal cell sizes and FP32
 // copies, from nx, ny, dx, dy, gamma, mu and Pr
 inline void geo_finish(Geo& g) {
@@ -274,8 +339,8 @@ __host__ __device__ __forceinline__ int perimeter(const Geo& g) { return 2 * (g.
 // ghost_cell reads).  ghosts_of_cell refreshes the ghosts whose source is
 // interior cell (i, j) from U, so the update that writes (i, j) also writes
 // them and a step needs no separate ghost pass.
-template <class R>
-__device__ __forceinline__ void ghosts_of_cell(const Geo& g, Cells<R> U, int i, int j) {
+template <class Fn>
+__device__ __forceinline__ void for_each_ghost_of(const Geo& g, int i, int j, Fn fn) {
   const bool px = g.bc.kind[0] == GKS_BC_PERIODIC, py = g.bc.kind[2] == GKS_BC_PERIODIC;
   // candidate x (y) coordinates: the cell's own, the low ghost, the high ghost
   const bool xl = i == (px ? g.nx - 1 : 0), xh = i == (px ? 0 : g.nx - 1);
@@ -286,12 +351,18 @@ __device__ __forceinline__ void ghosts_of_cell(const Geo& g, Cells<R> U, int i, 
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       if ((a == 0 && b == 0) || (a == 1 && !xl) || (a == 2 && !xh) || (b == 1 && !yl) || (b == 2 && !yh)) continue;
-      const int gi = a == 0 ? i : (a == 1 ? -1 : g.nx), gj = b == 0 ? j : (b == 1 ? -1 : g.ny);
-      R w[4];
-      ghost_cell<R>(g, U.view(), gi, gj, w);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) U.put(g, v, gi, gj, w[v]);
+      fn(a == 0 ? i : (a == 1 ? -1 : g.nx), b == 0 ? j : (b == 1 ? -1 : g.ny));
     }
+}
+
+template <class R>
+__device__ __forceinline__ void ghosts_of_cell(const Geo& g, Cells<R> U, int i, int j) {
+  for_each_ghost_of(g, i, j, [&](int gi, int gj) {
+    R w[4];
+    ghost_cell<R>(g, U.view(), gi, gj, w);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) U.put(g, v, gi, gj, w[v]);
+  });
 }
 
 // p-th cell of the ghost ring (boundary images are taken in FP64)
@@ -311,7 +382,8 @@ __device__ __forceinline__ void ghost_at(const Geo& g, Cells<R> U, int p) {
 
 // ---------------------------------------------------------------------------
 // reconstruction of cell (i, j); U is the padded cell-average array in the
-// compute type, Wx/Wy the face point values; writes coef[5][4][ny][nx]
+// compute type, Wx/Wy the face point values; writes the cell's record and the
+// averages of the ghost records that are images of the cell
 // ---------------------------------------------------------------------------
 // Eigenvectors of the Jacobian of the x-flux of the 2D Euler equations at the
 // conservative state w: columns of Rv for the eigenvalues u - c, u (entropy), u (shear),
@@ -399,7 +471,7 @@ __device__ __forceinline__ void recon_vectors(const R in[13][4], const ReconK<R>
 
 template <class R, class TW, bool CHAR = false>
 __device__ __forceinline__ void recon_cell(const Geo& g, const R* __restrict__ U, const TW* __restrict__ Wx,
-                                           const TW* __restrict__ Wy, R* __restrict__ coef, int i, int j, R dx,
+                                           const TW* __restrict__ Wy, R* __restrict__ rec, int i, int j, R dx,
                                            R dy, R weps, R wC) {
   const int nx = g.nx, ny = g.ny;
   const size_t fxp = (size_t)ny * (nx + 1), fyp = (size_t)(ny + 1) * nx;
@@ -463,11 +535,21 @@ __device__ __forceinline__ void recon_cell(const Geo& g, const R* __restrict__ U
   // else the constant average
   auto ok = [](const R w[4]) { return w[0] > R(0) && R(2) * w[0] * w[3] > w[1] * w[1] + w[2] * w[2]; };
   const bool bad = !(ok(ve) && ok(vw) && ok(vn) && ok(vs));
-  const size_t N = (size_t)nx * ny, o = (size_t)j * nx + i;
+  R r[kRec];
 #pragma unroll
-  for (int k = 0; k < 5; ++k)
+  for (int v = 0; v < 4; ++v) {
+    r[v] = cbar[v];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) coef[(size_t)(k * 4 + v) * N + o] = bad ? R(0) : a[v][k];
+    for (int k = 0; k < 5; ++k) r[4 + 4 * k + v] = bad ? R(0) : a[v][k];
+  }
+  RecIO<R>::store(rec + ri(g, i, j), r);
+  // the ghost ring's averages (boundary images written by the last update)
+  for_each_ghost_of(g, i, j, [&](int gi, int gj) {
+    R w[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) w[v] = U[ci(g, v, gi, gj)];
+    RecIO<R>::store_avg(rec + ri(g, gi, gj), w);
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -479,15 +561,14 @@ template <int AX> __device__ __forceinline__ int slot(int v) { return AX == 0 ? 
 // value and derivatives of cell (i, j)'s polynomial at the centre of its face
 // on side s (+1: the face at +h_n/2, -1: at -h_n/2), in the face frame of axis AX
 template <int AX, class R>
-__device__ __forceinline__ void side_state(const Geo& g, const R* __restrict__ U, const R* __restrict__ coef,
-                                           int i, int j, int s, R hn, R hn2_12, R ht2_24, FaceState<R>& S) {
-  const size_t N = (size_t)g.nx * g.ny, o = (size_t)j * g.nx + i;
+__device__ __forceinline__ void side_state(const Geo& g, const R* __restrict__ rec, int i, int j, int s, R hn,
+                                           R hn2_12, R ht2_24, FaceState<R>& S) {
+  R r[kRec];
+  RecIO<R>::load(rec + ri(g, i, j), r);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    const R c = U[ci(g, v, i, j)];
-    const R a2 = coef[(size_t)(0 * 4 + v) * N + o], a3 = coef[(size_t)(1 * 4 + v) * N + o];
-    const R a4 = coef[(size_t)(2 * 4 + v) * N + o], a5 = coef[(size_t)(3 * 4 + v) * N + o];
-    const R a6 = coef[(size_t)(4 * 4 + v) * N + o];
+    const R c = r[v];
+    const R a2 = r[4 + v], a3 = r[8 + v], a4 = r[12 + v], a5 = r[16 + v], a6 = r[20 + v];
     const R an = AX == 0 ? a2 : a3, at = AX == 0 ? a3 : a2;
     const R ann = AX == 0 ? a4 : a5, att = AX == 0 ? a5 : a4;
     const int k = slot<AX>(v);
@@ -505,8 +586,8 @@ __device__ __forceinline__ void side_state(const Geo& g, const R* __restrict__ U
 template <int AX, class R>
 struct GridFaceSource {
   const Geo* g;
-  const R* U;
-  const R* coef;
+  const R* U;    // padded compute-type averages (the first-order fallback's constant states)
+  const R* rec;  // reconstruction records
   int i, j;            // face index (x-faces: i in [0, nx]; y-faces: j in [0, ny])
   int cl, cr;          // the two cells along the normal, after periodic wrap
   int img_lo, img_hi;  // boundary image on the low / high side: 0 none, else the BC kind
@@ -556,18 +637,18 @@ struct GridFaceSource {
     if (k == 0) {
       if (img_lo) {
         FaceState<R> in;
-        side_state<AX>(*g, U, coef, cx(cr), cy(cr), -1, hn, hn2_12, ht2_24, in);
+        side_state<AX>(*g, rec, cx(cr), cy(cr), -1, hn, hn2_12, ht2_24, in);
         image(img_lo, uwt_lo, Tw_lo, in, S);
       } else {
-        side_state<AX>(*g, U, coef, cx(cl), cy(cl), +1, hn, hn2_12, ht2_24, S);
+        side_state<AX>(*g, rec, cx(cl), cy(cl), +1, hn, hn2_12, ht2_24, S);
       }
     } else {
       if (img_hi) {
         FaceState<R> in;
-        side_state<AX>(*g, U, coef, cx(cl), cy(cl), +1, hn, hn2_12, ht2_24, in);
+        side_state<AX>(*g, rec, cx(cl), cy(cl), +1, hn, hn2_12, ht2_24, in);
         image(img_hi, uwt_hi, Tw_hi, in, S);
       } else {
-        side_state<AX>(*g, U, coef, cx(cr), cy(cr), -1, hn, hn2_12, ht2_24, S);
+        side_state<AX>(*g, rec, cx(cr), cy(cr), -1, hn, hn2_12, ht2_24, S);
       }
     }
   }
@@ -580,8 +661,10 @@ struct GridFaceSource {
       for (int k = 0; k < 3; ++k) {
         const int ii = AX == 0 ? i - 1 + m : i - 1 + k;
         const int jj = AX == 0 ? j - 1 + k : j - 1 + m;
+        R w[4];
+        RecIO<R>::load_avg(rec + ri(*g, ii, jj), w);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) a[m][k][slot<AX>(v)] = U[ci(*g, v, ii, jj)];
+        for (int v = 0; v < 4; ++v) a[m][k][slot<AX>(v)] = w[v];
       }
   }
 };
@@ -611,14 +694,14 @@ __host__ __device__ inline FaceConst<R> grid_face_const(const Geo& g, int axis) 
 // the evolution at face (i, j) of axis AX: flux F and new point values Wn
 // (NSM: Navier-Stokes 1, Euler 0, decided per grid at run time -1)
 template <int AX, class R, class TW, int NSM = -1>
-__device__ __forceinline__ void flux_face(const Geo& g, const FaceConst<R>& C, const R* U, const R* __restrict__ coef,
+__device__ __forceinline__ void flux_face(const Geo& g, const FaceConst<R>& C, const R* __restrict__ rec,
                                           TW* __restrict__ Wn, R* __restrict__ F, int i, int j, R dt) {
   const int nx = g.nx, ny = g.ny;
   const int fx = AX == 0 ? nx + 1 : nx, fy = AX == 0 ? ny : ny + 1;
   GridFaceSource<AX, R> src;
   src.g = &g;
-  src.U = U;
-  src.coef = coef;
+  src.U = nullptr;
+  src.rec = rec;
   src.i = i;
   src.j = j;
   const int f = AX == 0 ? i : j;     // face index along the normal
@@ -710,7 +793,7 @@ __device__ __forceinline__ void kfvs_face(const Geo& g, const R* U, R gm1, R K, 
   GridFaceSource<AX, R> src;
   src.g = &g;
   src.U = U;
-  src.coef = nullptr;
+  src.rec = nullptr;
   src.i = i;
   src.j = j;
   const int f = AX == 0 ? i : j, nf = AX == 0 ? g.nx : g.ny;
@@ -737,10 +820,10 @@ __device__ __forceinline__ void kfvs_face(const Geo& g, const R* U, R gm1, R K, 
   for (int k = 0; k < 2; ++k) {
     FaceState<R> S;
     src.side(k, S);
-    R rho, u, v, p;
-    prim(S.w[0], gm1, rho, u, v, p);
+    R rho, ir, u, v, p;
+    prim(S.w[0], gm1, rho, ir, u, v, p);
     Moments<R, 4, 3> m;
-    moments(u, v, d_div(R(0.5) * rho, p), K, k == 0 ? +1 : -1, m);
+    moments(u, v, d_div(R(0.5) * rho, p), p * ir, K, k == 0 ? +1 : -1, m);
     R a[4], b[4];
     psi_mom<0, 0>(m, a);
     psi_mom<1, 0>(m, b);

@@ -77,7 +77,11 @@ def test_blast_wave_against_the_oracle(prec):
 
 def test_blast_wave_fp32_bulk_follows_fp64_before_the_amplification():
     """FP32-bulk against the (oracle-pinned) FP64 path over the first 50 steps of the blast
-    wave: FP32 rounding differences only (measured L1 4e-8 density, 2e-7 energy)."""
+    wave: FP32 rounding differences only.  Measured over three FP32 builds that differ only in
+    rounding order (relative L1 at step 50): density 5e-8..1e-7, energy 1.4e-7..2.2e-7,
+    momentum 9.6e-7..1.7e-6 (momentum is zero at t = 0 and lives only at the shocks, so its
+    relative figure is the loosest); by step 60 the amplification has raised every build's
+    momentum difference to ~1.4e-5."""
     p = wl.blast_wave(400)
     a = gks.Solver(p, gks.GKS_FP64, tau_eps=0.05)
     b = gks.Solver(p, gks.GKS_FP32_BULK, tau_eps=0.05)
@@ -88,7 +92,7 @@ def test_blast_wave_fp32_bulk_follows_fp64_before_the_amplification():
     a.close()
     b.close()
     err = _l1(Ub, Ua)[[0, 1, 3]]
-    assert np.all(err <= 1e-6), err
+    assert err[0] <= 3e-7 and err[2] <= 6e-7 and err[1] <= 4e-6, err
 
 
 def test_viscous_shock_tube_fp64_equals_the_oracle():
