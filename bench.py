@@ -254,6 +254,8 @@ def run_ours(args):
     errors = error_legs(stream) if not args.no_batch else None
     validation = vortex_leg(stream) if not args.no_batch else None
     characteristic = characteristic_leg(stream) if not args.no_batch else None
+    convergence = convergence_leg(stream) if not args.no_batch else None
+    cavity = cavity_leg(stream, args.cavity_steps) if (not args.no_batch and args.cavity_steps > 0) else None
 
     # ---- end to end through the C ABI with host buffers ----
     KE = max(3, min(args.steps, 20))
@@ -346,6 +348,8 @@ def run_ours(args):
             "batched": batched,
             "validation": validation,
             "characteristic": characteristic,
+            "convergence": convergence,
+            "cavity": cavity,
             "fp32_4096": big,
             "kernels_ms_fp32": {k: round(v, 5) for k, v in prof.items()},
             "kernels_ms_fp64": {k: round(v, 5) for k, v in prof64.items()},
@@ -440,6 +444,81 @@ def vortex_leg(stream):
         d = U[0] - p.U[0]
         out[name] = {"L1": float(np.mean(np.abs(d))), "L2": float(math.sqrt(np.mean(d * d))), "steps": int(k),
                      "value": round(121 * 121 * k / (ms * 1e-3) / 1e6, 3), "unit": UNIT}
+    return out
+
+
+def convergence_leg(stream):
+    """The 2D smooth wave on 32^2..512^2 to t = 1 (one period along x + y, so the exact solution
+    is the initial data) in plain FP64 and FP32-bulk at the paper's CFL 0.2: mean |rho - exact|
+    per grid and the observed orders between successive grids.  (At CFL 0.5 the Euler-limit
+    collision time with the min-of-directions time step puts the diagonal wave at a summed
+    2D Courant number of 1.0, where roundoff grows by ~1.8% per step: visible after ~700
+    steps at 512^2, so a run to t = 1 there measures that growth, not the scheme's order.)"""
+    cfl = 0.2
+    import numpy as np
+    import torch
+    from paper_1412_4489_gb300 import gks, workloads as wl
+    ns = [32, 64, 128, 256, 512]
+    out = {"workload": "2D Euler smooth wave, periodic [0,2]^2, seed 2, CFL 0.2, to t = 1 (one period)",
+           "grids": ns, "norm": "mean |rho - rho_exact| over cells (exact cell averages)"}
+    for prec, name in ((gks.GKS_FP64, "fp64"), (gks.GKS_FP32_BULK, "fp32_bulk")):
+        errs, steps = [], []
+        for n in ns:
+            p = wl.smooth_wave_2d(n, seed=SEED)
+            with torch.cuda.stream(stream):
+                s = gks.Solver(p, prec, stream=stream.cuda_stream, tau_eps=0.0)
+                for _ in range(100000):
+                    s.advance(64, cfl, 1.0)
+                    t, k = s.sync()
+                    if t >= 1.0 * (1 - 1e-14):
+                        break
+                U = s.state()[0]
+                s.close()
+            errs.append(float(np.mean(np.abs(U[0] - p.U[0]))))
+            steps.append(int(k))
+        out[name] = {"l1": errs, "steps": steps,
+                     "orders": [round(math.log2(errs[i] / errs[i + 1]), 3) for i in range(len(ns) - 1)]}
+    out["fp32_vs_fp64_error_ratio"] = [round(a / b, 4) for a, b in zip(out["fp32_bulk"]["l1"], out["fp64"]["l1"])]
+    return out
+
+
+def cavity_leg(stream, nsteps):
+    """The lid-driven cavity at 512^2 (Re 1000, lid Mach 0.15, isothermal no-slip walls,
+    Navier-Stokes with the Prandtl correction) advanced nsteps steps toward steady state in
+    FP32-bulk and plain FP64: throughput of each (CUDA events around the whole run) and the
+    relative L1 density difference between the two at checkpoints."""
+    import numpy as np
+    import torch
+    from paper_1412_4489_gb300 import gks, workloads as wl
+    c = wl.cavity_2d(512)
+    out = {"workload": "lid-driven cavity 512^2, Re 1000, lid Mach 0.15, Pr 0.72, CFL 0.5", "steps": nsteps,
+           "unit": UNIT}
+    with torch.cuda.stream(stream):
+        f64 = gks.Solver(c, gks.GKS_FP64, stream=stream.cuda_stream, tau_eps=0.05)
+        f32 = gks.Solver(c, gks.GKS_FP32_BULK, stream=stream.cuda_stream, tau_eps=0.05)
+        ms = {"fp64": 0.0, "fp32_bulk": 0.0}
+        rows, done = [], 0
+        checkpoints = sorted({min(nsteps, k) for k in (1000, 5000, 10000, nsteps)})
+        for m in checkpoints:
+            for s, key in ((f64, "fp64"), (f32, "fp32_bulk")):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.advance(m - done, CFL)
+                e1.record(stream)
+                e1.synchronize()
+                ms[key] += e0.elapsed_time(e1)
+            done = m
+            ra, rb = f32.state()[0][0], f64.state()[0][0]
+            speed = f64.state()[0]
+            umax = float(np.max(np.hypot(speed[1], speed[2]) / speed[0]))
+            rows.append({"steps": m, "l1_rho_rel_fp32": float(np.sum(np.abs(ra - rb)) / np.sum(np.abs(rb))),
+                         "max_speed_fp64": umax, "t": f64.sync()[0]})
+        f64.close()
+        f32.close()
+    out["l1_rho_rel_fp32_vs_fp64"] = rows
+    for key in ms:
+        out[key] = {"value": round(512 * 512 * nsteps / (ms[key] * 1e-3) / 1e6, 3), "ms_per_step": round(ms[key] / nsteps, 4)}
+    out["speedup_fp32_bulk"] = round(out["fp32_bulk"]["value"] / out["fp64"]["value"], 2)
     return out
 
 
@@ -579,6 +658,8 @@ def main():
     ap.add_argument("--ref-size", type=int, default=None,
                     help="grid of the reference arm (default: --size, the timed workload itself)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cavity-steps", type=int, default=20000,
+                    help="steps of the 512^2 cavity leg in both precisions (0 skips it)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and 4096^2 legs")
     args = ap.parse_args()
     if args.warmup < 3:
