@@ -568,9 +568,9 @@ def run_batched(args, stream):
            "parallelism": f"grids sharded over {world} rank(s), no data-path collective",
            "workload": "512 seeded grids 32..384 per side: smooth waves (periodic) and four-quadrant Riemann "
                        "data (outflow), gamma 1.4 or 5/3, mu logU[1e-5, 1e-3], Pr 0.72, CFL 0.5"}
-    for prec, key, K in ((gks.GKS_FP32_BULK, "fp32_bulk", 5), (gks.GKS_FP64, "fp64", 2)):
+    for prec, key, K in ((gks.GKS_FP32_BULK, "fp32_bulk", 20), (gks.GKS_FP64, "fp64", 10)):
         b = gks.Batch(probs, prec, stream=stream.cuda_stream)
-        w, bps, _ = gks.gks_batch_autotune(b.b, CFL, 1)
+        (wx, wy), bps, _ = gks.gks_batch_autotune(b.b, CFL, 1)
         with torch.cuda.stream(stream):
             b.step(1, CFL)
             b.sync()
@@ -580,12 +580,33 @@ def run_batched(args, stream):
             e1.record(stream)
             e1.synchronize()
             lo, hi = b.sync()
+            # the split of a step over the kernel's phases (device clock at each barrier)
+            phases = gks.gks_batch_profile(b.b, 3, CFL)
         ms = parallel.max_over_ranks(e0.elapsed_time(e1), device="cuda")
         out[key] = {"value": round(cells * K / (ms * 1e-3) / 1e6, 3), "ms_per_step": round(ms / K, 3),
-                    "steps": K, "face_tile_width": w, "blocks_per_sm": bps, "steps_per_grid": [lo, hi]}
+                    "steps": K, "face_tile_width": {"x": wx, "y": wy}, "blocks_per_sm": bps,
+                    "steps_per_grid": [lo, hi], "phases_ms_per_step": {k: round(v, 4) for k, v in phases.items()}}
         b.close()
     out["value"] = out["fp32_bulk"]["value"]
     out["speedup_fp32_bulk"] = round(out["fp32_bulk"]["value"] / out["fp64"]["value"], 2)
+    # the same work on one grid: every batch grid is Navier-Stokes with the Prandtl correction,
+    # so the comparison is the single-grid FP32-bulk Navier-Stokes rate at a size above L2
+    p = wl.riemann_2d(2048, seed=3, mu=1e-4, Pr=0.72)
+    with torch.cuda.stream(stream):
+        s = gks.Solver(p, gks.GKS_FP32_BULK, stream=stream.cuda_stream)
+        s.advance(3, CFL)
+        s.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.advance(20, CFL)
+        e1.record(stream)
+        e1.synchronize()
+        s.close()
+    ms1 = e0.elapsed_time(e1) / 20
+    single = p.nx * p.ny / (ms1 * 1e-3) / 1e6
+    out["single_grid_ns_fp32_bulk"] = {"workload": "NS four-quadrant data 2048^2, mu 1e-4, Pr 0.72", "unit": UNIT,
+                                       "value": round(single, 3), "ms_per_step": round(ms1, 4)}
+    out["batched_vs_single_grid_ns"] = round(out["fp32_bulk"]["value"] / single, 3)
     return out
 
 

@@ -242,21 +242,36 @@ gks_status gks_batch_sync(gks_batch* b, long long* steps_min, long long* steps_m
 /* Time, step count and status of grid g (synchronous). */
 gks_status gks_batch_grid_info(gks_batch* b, int g, double* t, long long* steps, int* status);
 
-/* Sets the face-phase tile width (16, 32, 64 or 128 faces per row of a
- * 128-face tile) and the resident blocks per SM of the persistent kernel. */
+/* Sets the face-phase tile widths of x-faces and y-faces (4, 8, 16, 32, 64 or 128
+ * faces per row of a 128-face tile: a grid has nx + 1 x-faces per row and ny + 1 rows
+ * of y-faces, so narrow tiles waste least on x-faces and wide ones on y-faces) and the
+ * resident blocks per SM of the persistent kernel.  gks_batch_configure sets one width
+ * for both. */
+gks_status gks_batch_configure_tiles(gks_batch* b, int face_tile_width_x, int face_tile_width_y,
+                                     int blocks_per_sm);
 gks_status gks_batch_configure(gks_batch* b, int face_tile_width, int blocks_per_sm);
 
-/* Autotuner: times trial_steps steps for every tile width and every feasible
- * blocks-per-SM on the batch itself (the state is saved and restored), keeps
- * the fastest and reports it (any output may be NULL; best_ms per step). */
-gks_status gks_batch_autotune(gks_batch* b, double CFL, int trial_steps, int* face_tile_width,
-                              int* blocks_per_sm, float* best_ms);
+/* Autotuner: on the batch itself (the state is saved and restored) times trial_steps
+ * steps per trial, searching the x-face tile width, then the y-face tile width, then
+ * the resident blocks per SM, keeping the fastest of each; reports the result (any
+ * output may be NULL; best_ms per step). */
+gks_status gks_batch_autotune(gks_batch* b, double CFL, int trial_steps, int* face_tile_width_x,
+                              int* face_tile_width_y, int* blocks_per_sm, float* best_ms);
 
 /* Limit of every device barrier wait, in seconds (default 2).
  * test_skip_block >= 0 makes that block of the persistent kernel skip its
  * barrier arrivals -- a test hook that makes every other wait run out, so that
  * the timeout path can be exercised; -1 disables it. */
 gks_status gks_batch_set_wait_limit(gks_batch* b, double seconds, int test_skip_block);
+
+/* Measurement: advances the batch nsteps steps in one (uncaptured) persistent launch
+ * in which one block stamps the device clock at each device-wide barrier, and writes
+ * the mean time per step of each phase to ms[6], in milliseconds: opening the step
+ * (dt per grid), reconstruction, face evolution, update passes 1, 2 and 3 (the last two
+ * are 0 unless some grid needed the positivity fallback).  The grids advance as with
+ * gks_batch_step.  Synchronous; allocates nsteps * 48 bytes of device memory for the
+ * stamps. */
+gks_status gks_batch_profile(gks_batch* b, int nsteps, double CFL, double* ms);
 
 /* Total cells of all grids; kernel launches per gks_batch_step call. */
 long long gks_batch_cells(const gks_batch* b);

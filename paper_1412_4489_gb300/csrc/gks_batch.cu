@@ -28,7 +28,8 @@ using namespace gks;
 
 namespace {
 
-constexpr int kThreads = 128;  // one work tile = one block = 128 cells or faces
+constexpr int kThreads = 128;  // one work tile = one block: 128 faces, or 2 x 128 cells
+constexpr int kCellsPerThread = 2;  // cells per thread in a cell tile (both in flight at once)
 
 struct GridOff {
   size_t u;     // padded cell arrays (4 * plane doubles: Cells<R>)
@@ -64,10 +65,16 @@ struct Args {
   const int4* cell_items;   // (grid, x0, y0, -)
   const int4* face_items;   // (grid, x0, y0, axis)
   int n_cell, n_face;
-  int cell_tw, face_tw;     // tile widths (heights = 128 / width)
+  int cell_tw;              // cell tile width (height = 2 x 128 / width)
+  int face_tw[2];           // face tile widths of x- and y-faces (heights = 128 / width)
   Barrier* bar;
   double cfl;
+  unsigned long long* stamps;  // optional: %globaltimer at the end of each phase, kPhases per step (block 0)
 };
+
+// phases of one step, each ended by a device-wide barrier: open the step (dt per grid),
+// reconstruction, face evolution, update passes 1, 2, 3 (2 and 3 only when needed)
+constexpr int kPhases = 6;
 
 __device__ __forceinline__ unsigned long long now_ns() {
   unsigned long long t;
@@ -104,20 +111,27 @@ __device__ bool grid_barrier(Barrier* b) {
   return *(volatile int*)&b->error == 0;
 }
 
-// resident blocks per SM the FP32 batch kernel is compiled for: 4 (128 registers, 16 warps
-// per SM; the autotuner may run fewer)
+// resident blocks per SM the FP32 batch kernel is compiled for: 3 (168 registers, 12 warps
+// per SM; at 4 blocks and 128 registers the Navier-Stokes face routine inside the persistent
+// loop spills ~360 bytes; the autotuner may run fewer)
 #ifndef GKS_BATCH_MINB_F32
-#define GKS_BATCH_MINB_F32 4
+#define GKS_BATCH_MINB_F32 3
 #endif
 template <class R> struct BatchBlocks;
 template <> struct BatchBlocks<double> { static constexpr int value = 1; };
 template <> struct BatchBlocks<float> { static constexpr int value = GKS_BATCH_MINB_F32; };
 
 // NSM = 1: every grid has mu > 0 (the Navier-Stokes face routine only); -1: the face
-// routine decides per grid
-template <class R, class TW, int NSM>
+// routine decides per grid.  CHAR: the reconstruction in characteristic variables (an
+// option of the whole batch); the kernel without it carries only the conservative one,
+// whose registers are far fewer.
+template <class R, class TW, int NSM, bool CHAR>
 __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<R, TW> a, int nsteps) {
   const int tid = threadIdx.x;
+  auto stamp = [&](int s, int phase) {
+    if (a.stamps && blockIdx.x == 0 && tid == 0) a.stamps[(size_t)s * kPhases + phase] = now_ns();
+  };
+  if (a.stamps && blockIdx.x == 0 && tid == 0) a.stamps[(size_t)nsteps * kPhases] = now_ns();  // start
   for (int s = 0; s < nsteps; ++s) {
     // dt of this step per grid (after ending the previous one)
     for (int g = blockIdx.x * kThreads + tid; g < a.G; g += gridDim.x * kThreads) {
@@ -125,28 +139,29 @@ __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<
       ctrl_begin(&a.ctrl[g], a.cfl, INFINITY, INFINITY);
     }
     if (!grid_barrier(a.bar)) return;
+    stamp(s, 0);
     // every block read the previous step's flags before the barrier above
     if (blockIdx.x == 0 && tid == 0) a.bar->any_bad[0] = a.bar->any_bad[1] = 0;
 
-    // reconstruction
+    // reconstruction (two cells per thread, kThreads / cell_tw rows apart)
     for (int it = blockIdx.x; it < a.n_cell; it += gridDim.x) {
       const int4 w = a.cell_items[it];
       const Ctrl* c = &a.ctrl[w.x];
       if (c->skip) continue;
       const Geo& g = a.geo[w.x];
-      const int i = w.y + tid % a.cell_tw, j = w.z + tid / a.cell_tw;
-      if (i >= g.nx || j >= g.ny) continue;
       const int par = (int)(c->steps & 1);
       const GridOff& o = a.off[w.x];
       const R* U = (const R*)(a.U[par] + o.u);
-      if (g.characteristic)
-        recon_cell<R, TW, true>(g, U, a.Wx[par] + o.wx, a.Wy[par] + o.wy, a.rec + o.rec, i, j, GeoR<R>::dx(g),
-                                GeoR<R>::dy(g), GeoR<R>::weps(g), GeoR<R>::wC(g));
-      else
-        recon_cell<R, TW, false>(g, U, a.Wx[par] + o.wx, a.Wy[par] + o.wy, a.rec + o.rec, i, j,
-                                 GeoR<R>::dx(g), GeoR<R>::dy(g), GeoR<R>::weps(g), GeoR<R>::wC(g));
+#pragma unroll
+      for (int r = 0; r < kCellsPerThread; ++r) {
+        const int i = w.y + tid % a.cell_tw, j = w.z + tid / a.cell_tw + r * (kThreads / a.cell_tw);
+        if (i < g.nx && j < g.ny)
+          recon_cell<R, TW, CHAR>(g, U, a.Wx[par] + o.wx, a.Wy[par] + o.wy, a.rec + o.rec, i, j, GeoR<R>::dx(g),
+                                  GeoR<R>::dy(g), GeoR<R>::weps(g), GeoR<R>::wC(g));
+      }
     }
     if (!grid_barrier(a.bar)) return;
+    stamp(s, 1);
 
     // face evolution
     for (int it = blockIdx.x; it < a.n_face; it += gridDim.x) {
@@ -154,7 +169,8 @@ __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<
       const Ctrl* c = &a.ctrl[w.x];
       if (c->skip) continue;
       const Geo& g = a.geo[w.x];
-      const int i = w.y + tid % a.face_tw, j = w.z + tid / a.face_tw;
+      const int tw = a.face_tw[w.w];
+      const int i = w.y + tid % tw, j = w.z + tid / tw;
       const int par = (int)(c->steps & 1);
       const GridOff& o = a.off[w.x];
       const R* U = (const R*)(a.U[par] + o.u);
@@ -169,45 +185,54 @@ __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<
       }
     }
     if (!grid_barrier(a.bar)) return;
+    stamp(s, 2);
 
     // update and the CFL minimum of the new state (update_cell): pass 1; pass 2
     // for grids where pass 1 left a cell non-physical; pass 3 for grids where
     // pass 2 still did.  The global flags let every block skip an unneeded pass
     // together.
     for (int pass = 1; pass <= 3; ++pass) {
-      if (pass > 1 && *(volatile int*)&a.bar->any_bad[pass - 2] == 0) break;
+      if (pass > 1 && *(volatile int*)&a.bar->any_bad[pass - 2] == 0) {
+        for (int q = pass; q <= 3; ++q) stamp(s, 2 + q);  // the skipped passes take no time
+        break;
+      }
       for (int it = blockIdx.x; it < a.n_cell; it += gridDim.x) {
         const int4 w = a.cell_items[it];
         Ctrl* c = &a.ctrl[w.x];
         if (c->skip || (pass == 2 && !c->bad_found[0]) || (pass == 3 && !c->bad_found[1])) continue;  // per block
         const Geo& g = a.geo[w.x];
-        const int i = w.y + tid % a.cell_tw, j = w.z + tid / a.cell_tw;
         const int par = (int)(c->steps & 1);
         const GridOff& o = a.off[w.x];
         R inv = R(0);
-        if (i < g.nx && j < g.ny) {
-          bool bad;
-          inv = update_cell<R, TW>(g, Cells<R>{(R*)(a.U[par] + o.u)}, Cells<R>{(R*)(a.U[par ^ 1] + o.u)},
-                                   a.Fx + o.fx, a.Fy + o.fy, a.Wx[par ^ 1] + o.wx, a.Wy[par ^ 1] + o.wy,
-                                   a.bad + o.bad, pass, step_dt<R>(c), i, j, bad);
-          if (pass == 1) {
-            a.bad[o.bad + (size_t)j * g.nx + i] = bad ? 1 : 0;
-            if (bad) {
-              atomicOr(&c->bad_found[0], 1);
-              atomicOr(&a.bar->any_bad[0], 1);
+#pragma unroll
+        for (int r = 0; r < kCellsPerThread; ++r) {
+          const int i = w.y + tid % a.cell_tw, j = w.z + tid / a.cell_tw + r * (kThreads / a.cell_tw);
+          if (i < g.nx && j < g.ny) {
+            bool bad;
+            const R iv = update_cell<R, TW>(g, Cells<R>{(R*)(a.U[par] + o.u)}, Cells<R>{(R*)(a.U[par ^ 1] + o.u)},
+                                            a.Fx + o.fx, a.Fy + o.fy, a.Wx[par ^ 1] + o.wx, a.Wy[par ^ 1] + o.wy,
+                                            a.bad + o.bad, pass, step_dt<R>(c), i, j, bad);
+            inv = fmax(inv, iv);
+            if (pass == 1) {
+              a.bad[o.bad + (size_t)j * g.nx + i] = bad ? 1 : 0;
+              if (bad) {
+                atomicOr(&c->bad_found[0], 1);
+                atomicOr(&a.bar->any_bad[0], 1);
+              }
+            } else if (pass == 2) {
+              if (bad) {
+                atomicOr(&c->bad_found[1], 1);
+                atomicOr(&a.bar->any_bad[1], 1);
+              }
+            } else if (bad && atomicCAS(&c->status, GKS_OK, GKS_ENONPHYSICAL) == GKS_OK) {
+              c->fail_step = c->steps;
             }
-          } else if (pass == 2) {
-            if (bad) {
-              atomicOr(&c->bad_found[1], 1);
-              atomicOr(&a.bar->any_bad[1], 1);
-            }
-          } else if (bad && atomicCAS(&c->status, GKS_OK, GKS_ENONPHYSICAL) == GKS_OK) {
-            c->fail_step = c->steps;
           }
         }
         block_bound_to<R>(inv, &c->dtb[pass - 1]);
       }
       if (!grid_barrier(a.bar)) return;
+      stamp(s, 2 + pass);
     }
   }
   for (int g = blockIdx.x * kThreads + tid; g < a.G; g += gridDim.x * kThreads)
@@ -291,8 +316,9 @@ struct gks_batch {
   double* staging;
   size_t staging_n;
   // launch configuration
-  int face_tw, cell_tw, blocks_per_sm, max_blocks_per_sm;
+  int face_tw[2], cell_tw, blocks_per_sm, max_blocks_per_sm;
   bool all_ns;  // every grid has mu > 0: the kernel with the Navier-Stokes face routine only
+  bool characteristic;  // reconstruction in characteristic variables (batch-wide option)
   double timeout_s;
   int skip_block;
   cudaGraphExec_t graph;
@@ -319,16 +345,22 @@ gks_status bfail(gks_batch* b, gks_status s, const std::string& m) {
 size_t wsize(const gks_batch* b) { return b->prec == GKS_FP64 ? 8 : 4; }
 
 gks_status build_items(gks_batch* b) {
+  // faces: every grid's x-face tiles first, then the y-face tiles, so that an SM runs one
+  // face body at a time (except around the switch)
   std::vector<int4> cell, face;
-  const int ch = kThreads / b->cell_tw, fh = kThreads / b->face_tw;
+  const int ch = kCellsPerThread * kThreads / b->cell_tw;
+  const int fwx = b->face_tw[0], fhx = kThreads / fwx, fwy = b->face_tw[1], fhy = kThreads / fwy;
   for (int g = 0; g < b->G; ++g) {
     const Geo& G = b->geo[g];
     for (int y = 0; y < G.ny; y += ch)
       for (int x = 0; x < G.nx; x += b->cell_tw) cell.push_back(make_int4(g, x, y, 0));
-    for (int y = 0; y < G.ny; y += fh)
-      for (int x = 0; x < G.nx + 1; x += b->face_tw) face.push_back(make_int4(g, x, y, 0));
-    for (int y = 0; y < G.ny + 1; y += fh)
-      for (int x = 0; x < G.nx; x += b->face_tw) face.push_back(make_int4(g, x, y, 1));
+    for (int y = 0; y < G.ny; y += fhx)
+      for (int x = 0; x < G.nx + 1; x += fwx) face.push_back(make_int4(g, x, y, 0));
+  }
+  for (int g = 0; g < b->G; ++g) {
+    const Geo& G = b->geo[g];
+    for (int y = 0; y < G.ny + 1; y += fhy)
+      for (int x = 0; x < G.nx; x += fwy) face.push_back(make_int4(g, x, y, 1));
   }
   cudaFree(b->d_cell);
   cudaFree(b->d_face);
@@ -364,15 +396,24 @@ Args<R, TW> make_args(gks_batch* b, double cfl) {
   a.n_cell = b->n_cell;
   a.n_face = b->n_face;
   a.cell_tw = b->cell_tw;
-  a.face_tw = b->face_tw;
+  a.face_tw[0] = b->face_tw[0];
+  a.face_tw[1] = b->face_tw[1];
   a.bar = b->d_bar;
   a.cfl = cfl;
+  a.stamps = nullptr;
   return a;
 }
 
 template <class R, class TW>
-gks_status launch(gks_batch* b, int nsteps, double cfl) {
+auto batch_kernel(const gks_batch* b) -> decltype(&k_batch<R, TW, 1, false>) {
+  if (b->characteristic) return b->all_ns ? &k_batch<R, TW, 1, true> : &k_batch<R, TW, -1, true>;
+  return b->all_ns ? &k_batch<R, TW, 1, false> : &k_batch<R, TW, -1, false>;
+}
+
+template <class R, class TW>
+gks_status launch(gks_batch* b, int nsteps, double cfl, unsigned long long* stamps = nullptr) {
   Args<R, TW> a = make_args<R, TW>(b, cfl);
+  a.stamps = stamps;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(b->sms * b->blocks_per_sm));
   cfg.blockDim = dim3(kThreads);
@@ -382,12 +423,13 @@ gks_status launch(gks_batch* b, int nsteps, double cfl) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  BCK(cudaLaunchKernelEx(&cfg, b->all_ns ? k_batch<R, TW, 1> : k_batch<R, TW, -1>, a, nsteps));
+  BCK(cudaLaunchKernelEx(&cfg, batch_kernel<R, TW>(b), a, nsteps));
   return GKS_OK;
 }
 
-gks_status launch_any(gks_batch* b, int nsteps, double cfl) {
-  return b->prec == GKS_FP64 ? launch<double, double>(b, nsteps, cfl) : launch<float, float>(b, nsteps, cfl);
+gks_status launch_any(gks_batch* b, int nsteps, double cfl, unsigned long long* stamps = nullptr) {
+  return b->prec == GKS_FP64 ? launch<double, double>(b, nsteps, cfl, stamps)
+                             : launch<float, float>(b, nsteps, cfl, stamps);
 }
 
 gks_status reset_barrier(gks_batch* b) {
@@ -409,11 +451,9 @@ void drop_graph(gks_batch* b) {
 int occupancy(gks_batch* b) {
   int n = 0;
   if (b->prec == GKS_FP64)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &n, b->all_ns ? k_batch<double, double, 1> : k_batch<double, double, -1>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<double, double>(b), kThreads, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, b->all_ns ? k_batch<float, float, 1> : k_batch<float, float, -1>,
-                                                  kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<float, float>(b), kThreads, 0);
   return n;
 }
 
@@ -433,10 +473,14 @@ gks_status gks_batch_create(int n, const gks_grid_desc* grids, const gks_options
   b->G = n;
   b->prec = o.precision;
   b->cell_tw = 32;
-  b->face_tw = 32;
+  // x-faces: nx + 1 per row, so narrow tall tiles waste least of the extra column;
+  // y-faces: ny + 1 rows, wide short tiles (the autotuner may pick others)
+  b->face_tw[0] = 8;
+  b->face_tw[1] = 32;
   b->timeout_s = 2.0;
   b->skip_block = -1;
   b->all_ns = true;
+  b->characteristic = o.characteristic != 0;
   size_t nu = 0, nwx = 0, nwy = 0, nc = 0, nfx = 0, nfy = 0, nbad = 0;
   b->cells = 0;
   for (int g = 0; g < n; ++g) {
@@ -698,24 +742,29 @@ gks_status gks_batch_grid_info(gks_batch* b, int g, double* t, long long* steps,
   return GKS_OK;
 }
 
-gks_status gks_batch_configure(gks_batch* b, int face_tile_width, int blocks_per_sm) {
+gks_status gks_batch_configure_tiles(gks_batch* b, int width_x, int width_y, int blocks_per_sm) {
   if (!b) return GKS_EINVAL;
-  if (face_tile_width != 16 && face_tile_width != 32 && face_tile_width != 64 && face_tile_width != 128)
-    return bfail(b, GKS_EINVAL, "face tile width must be 16, 32, 64 or 128");
+  auto ok = [](int w) { return w == 4 || w == 8 || w == 16 || w == 32 || w == 64 || w == 128; };
+  if (!ok(width_x) || !ok(width_y)) return bfail(b, GKS_EINVAL, "face tile widths must be 4, 8, 16, 32, 64 or 128");
   if (blocks_per_sm < 1 || blocks_per_sm > b->max_blocks_per_sm)
     return bfail(b, GKS_EINVAL, "blocks_per_sm must lie in [1, " + std::to_string(b->max_blocks_per_sm) + "]");
   BCK(cudaStreamSynchronize(b->stream));
   drop_graph(b);
   b->blocks_per_sm = blocks_per_sm;
-  if (face_tile_width != b->face_tw) {
-    b->face_tw = face_tile_width;
+  if (width_x != b->face_tw[0] || width_y != b->face_tw[1]) {
+    b->face_tw[0] = width_x;
+    b->face_tw[1] = width_y;
     return build_items(b);
   }
   return GKS_OK;
 }
 
-gks_status gks_batch_autotune(gks_batch* b, double CFL, int trial_steps, int* face_tile_width, int* blocks_per_sm,
-                              float* best_ms) {
+gks_status gks_batch_configure(gks_batch* b, int face_tile_width, int blocks_per_sm) {
+  return gks_batch_configure_tiles(b, face_tile_width, face_tile_width, blocks_per_sm);
+}
+
+gks_status gks_batch_autotune(gks_batch* b, double CFL, int trial_steps, int* face_tile_width_x,
+                              int* face_tile_width_y, int* blocks_per_sm, float* best_ms) {
   if (!b || !(CFL > 0) || trial_steps < 1) return bfail(b, GKS_EINVAL, "gks_batch_autotune: bad argument");
   BCK(cudaSetDevice(b->device));
   // the trials advance the batch; save and restore the state and control blocks
@@ -740,38 +789,80 @@ gks_status gks_batch_autotune(gks_batch* b, double CFL, int trial_steps, int* fa
     return GKS_OK;
   };
   gks_status st = snapshot(false);
-  const int widths[4] = {16, 32, 64, 128};
-  float best = 1e30f;
-  int bw = b->face_tw, bb = b->blocks_per_sm;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int wi = 0; wi < 4 && st == GKS_OK; ++wi)
-    for (int bps = 1; bps <= b->max_blocks_per_sm && st == GKS_OK; ++bps) {
-      st = gks_batch_configure(b, widths[wi], bps);
-      if (st != GKS_OK) break;
-      st = reset_barrier(b);
-      if (st == GKS_OK) st = launch_any(b, 1, CFL);  // warm-up
-      if (st == GKS_OK) st = reset_barrier(b);
-      cudaEventRecord(e0, b->stream);
-      if (st == GKS_OK) st = launch_any(b, trial_steps, CFL);
-      cudaEventRecord(e1, b->stream);
-      if (cudaEventSynchronize(e1) != cudaSuccess) st = bfail(b, GKS_ECUDA, "autotune trial failed");
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      BCK(cudaMemcpy(b->h_bar, b->d_bar, sizeof(Barrier), cudaMemcpyDeviceToHost));
-      if (st == GKS_OK && b->h_bar->error == 0 && ms < best) { best = ms; bw = widths[wi]; bb = bps; }
-      if (st == GKS_OK) st = snapshot(true);
-    }
+  // one timed trial of a configuration (state restored afterwards); +inf if it failed
+  auto trial = [&](int wx, int wy, int bps) -> float {
+    if (st != GKS_OK) return 1e30f;
+    st = gks_batch_configure_tiles(b, wx, wy, bps);
+    if (st == GKS_OK) st = reset_barrier(b);
+    if (st == GKS_OK) st = launch_any(b, 1, CFL);  // warm-up
+    if (st == GKS_OK) st = reset_barrier(b);
+    cudaEventRecord(e0, b->stream);
+    if (st == GKS_OK) st = launch_any(b, trial_steps, CFL);
+    cudaEventRecord(e1, b->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) st = bfail(b, GKS_ECUDA, "autotune trial failed");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (cudaMemcpy(b->h_bar, b->d_bar, sizeof(Barrier), cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = bfail(b, GKS_ECUDA, "autotune trial failed");
+    const bool good = st == GKS_OK && b->h_bar->error == 0;
+    if (st == GKS_OK) st = snapshot(true);
+    return good ? ms : 1e30f;
+  };
+  // coordinate search: the x-face tile width, then the y-face one, then the resident blocks
+  int bx = b->face_tw[0], by = b->face_tw[1], bb = b->max_blocks_per_sm;
+  float best = 1e30f;
+  for (int w : {4, 8, 16, 32}) {
+    const float ms = trial(w, by, bb);
+    if (ms < best) { best = ms; bx = w; }
+  }
+  for (int w : {16, 32, 64, 128}) {
+    if (w == by) continue;
+    const float ms = trial(bx, w, bb);
+    if (ms < best) { best = ms; by = w; }
+  }
+  for (int bps = 1; bps < b->max_blocks_per_sm; ++bps) {
+    const float ms = trial(bx, by, bps);
+    if (ms < best) { best = ms; bb = bps; }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (st == GKS_OK) st = gks_batch_configure(b, bw, bb);
+  if (st == GKS_OK) st = gks_batch_configure_tiles(b, bx, by, bb);
   cudaStreamSynchronize(b->stream);
   for (int k = 0; k < 4; ++k) cudaFree(save[k]);
   if (st != GKS_OK) return st;
-  if (face_tile_width) *face_tile_width = bw;
+  if (face_tile_width_x) *face_tile_width_x = bx;
+  if (face_tile_width_y) *face_tile_width_y = by;
   if (blocks_per_sm) *blocks_per_sm = bb;
   if (best_ms) *best_ms = best / trial_steps;
+  return GKS_OK;
+}
+
+gks_status gks_batch_profile(gks_batch* b, int nsteps, double CFL, double* ms) {
+  if (!b || nsteps < 1 || !(CFL > 0) || !ms) return bfail(b, GKS_EINVAL, "gks_batch_profile: bad argument");
+  BCK(cudaSetDevice(b->device));
+  unsigned long long* d = nullptr;
+  const size_t n = (size_t)nsteps * kPhases + 1;
+  BCK(cudaMalloc(&d, n * sizeof(unsigned long long)));
+  gks_status st = reset_barrier(b);
+  if (st == GKS_OK) st = launch_any(b, nsteps, CFL, d);
+  std::vector<unsigned long long> h(n);
+  if (st == GKS_OK && cudaMemcpyAsync(h.data(), d, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                      b->stream) != cudaSuccess)
+    st = bfail(b, GKS_ECUDA, "gks_batch_profile: copy");
+  if (st == GKS_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) st = bfail(b, GKS_ECUDA, "gks_batch_profile");
+  cudaFree(d);
+  if (st != GKS_OK) return st;
+  for (int p = 0; p < kPhases; ++p) ms[p] = 0.0;
+  unsigned long long prev = h[(size_t)nsteps * kPhases];
+  for (int s = 0; s < nsteps; ++s)
+    for (int p = 0; p < kPhases; ++p) {
+      const unsigned long long t = h[(size_t)s * kPhases + p];
+      ms[p] += (double)(t - prev) * 1e-6 / nsteps;
+      prev = t;
+    }
   return GKS_OK;
 }
 

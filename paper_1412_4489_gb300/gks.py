@@ -92,8 +92,12 @@ def load(path: str | None = None):
     L.gks_batch_sync.argtypes = [B, LL, LL]
     L.gks_batch_grid_info.argtypes = [B, ctypes.c_int, _dp, LL, ctypes.POINTER(ctypes.c_int)]
     L.gks_batch_configure.argtypes = [B, ctypes.c_int, ctypes.c_int]
+    L.gks_batch_profile.argtypes = [B, ctypes.c_int, D, _dp]
+    L.gks_batch_profile.restype = ctypes.c_int
     L.gks_batch_autotune.argtypes = [B, D, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                     ctypes.POINTER(ctypes.c_float)]
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
+    L.gks_batch_configure_tiles.argtypes = [B, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.gks_batch_configure_tiles.restype = ctypes.c_int
     L.gks_batch_set_wait_limit.argtypes = [B, D, ctypes.c_int]
     L.gks_batch_cells.argtypes = [B]
     L.gks_batch_cells.restype = ctypes.c_longlong
@@ -367,11 +371,26 @@ def gks_batch_configure(b, face_tile_width, blocks_per_sm):
     _bcheck(b, load().gks_batch_configure(b, int(face_tile_width), int(blocks_per_sm)))
 
 
+def gks_batch_configure_tiles(b, width_x, width_y, blocks_per_sm):
+    _bcheck(b, load().gks_batch_configure_tiles(b, int(width_x), int(width_y), int(blocks_per_sm)))
+
+
 def gks_batch_autotune(b, CFL, trial_steps=2):
-    w, k, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_float(0.0)
-    _bcheck(b, load().gks_batch_autotune(b, float(CFL), int(trial_steps), ctypes.byref(w), ctypes.byref(k),
-                                         ctypes.byref(ms)))
-    return w.value, k.value, ms.value
+    """Returns ((x-face tile width, y-face tile width), blocks per SM, ms per step)."""
+    wx, wy, k, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_float(0.0)
+    _bcheck(b, load().gks_batch_autotune(b, float(CFL), int(trial_steps), ctypes.byref(wx), ctypes.byref(wy),
+                                         ctypes.byref(k), ctypes.byref(ms)))
+    return (wx.value, wy.value), k.value, ms.value
+
+
+BATCH_PHASES = ["open", "recon", "faces", "update", "update2", "update3"]
+
+
+def gks_batch_profile(b, nsteps, CFL):
+    """Mean ms per step of each phase of the persistent batch kernel over nsteps steps."""
+    ms = (ctypes.c_double * len(BATCH_PHASES))()
+    _bcheck(b, load().gks_batch_profile(b, int(nsteps), float(CFL), ms))
+    return dict(zip(BATCH_PHASES, list(ms)))
 
 
 def gks_batch_set_wait_limit(b, seconds, test_skip_block=-1):

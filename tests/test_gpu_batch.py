@@ -71,8 +71,8 @@ def test_autotune_keeps_the_state():
     ps = _mixed_grids()[:3]
     b = gks.Batch(ps, gks.GKS_FP32_BULK)
     before = [b.state(g) for g in range(len(ps))]
-    w, k, ms = gks.gks_batch_autotune(b.b, 0.5, 1)
-    assert w in (16, 32, 64, 128) and k >= 1 and ms > 0
+    (wx, wy), k, ms = gks.gks_batch_autotune(b.b, 0.5, 1)
+    assert wx in (4, 8, 16, 32) and wy in (16, 32, 64, 128) and k >= 1 and ms > 0
     for g in range(len(ps)):
         after = b.state(g)
         for x, y in zip(before[g][:3], after[:3]):
