@@ -81,7 +81,10 @@ typedef enum {
   GKS_BC_OUTFLOW = 1,
   GKS_BC_SLIPWALL = 2,
   GKS_BC_NOSLIP_ISOTHERMAL = 3,
-  GKS_BC_NOSLIP_ADIABATIC = 4
+  GKS_BC_NOSLIP_ADIABATIC = 4,
+  GKS_BC_EXCHANGE = 5  /* y sides only: the handle is one row slab of a larger grid and the
+                          neighbouring slab's cells across this side are supplied by the
+                          caller (partitioned step, below) */
 } gks_bc_kind;
 
 typedef struct {
@@ -195,6 +198,60 @@ int gks_launches_per_step(const gks_handle* h);
  * (no work unless a cell needed it), end.
  * Synchronous; returns the status of the step. */
 gks_status gks_profile_step(gks_handle* h, double CFL, float* ms);
+
+/* ---- partitioned step: one grid split into row slabs (domain decomposition) ----
+ *
+ * A grid of nx by NY cells is split into row slabs, slab r holding global rows
+ * [j_r, j_r + ny_r).  Each slab is a handle of nx by ny_r cells on [0, Lx] x
+ * [0, ny_r dy] whose y-sides are GKS_BC_EXCHANGE where another slab lies beyond
+ * (on a periodic y-axis every y-side of every slab is; with a single slab its own
+ * copy), and the grid's own boundary condition where the grid ends.  Its state
+ * is the slab's rows of U and Wx and the ny_r + 1 rows of Wy from j_r to
+ * j_r + ny_r (both partition faces).  The scheme's step (Eq. finite over the whole
+ * grid) is then taken as:
+ *   1. bound_r = gks_part_bound(slab r); dt = min(CFL * min_r bound_r, dt_max)
+ *      (a min-reduction over all slabs);
+ *   2. gks_part_recon(slab r, dt) on every slab: the reconstruction of its cells;
+ *   3. the edge rows of reconstruction records (what = GKS_PART_RECORDS) go to
+ *      the neighbours: slab r's low edge (gks_part_get_edge(r, 2, ...)) becomes the
+ *      high halo of the slab below (gks_part_set_halo(r - 1, 3, ...)), its high
+ *      edge the low halo of the slab above;
+ *   4. gks_part_finish(slab r): the face evolution of its faces -- the partition
+ *      faces are evaluated by both slabs from the same inputs, so neither has to
+ *      send its fluxes -- and the update of its cells;
+ *   5. the edge rows of the new cell averages (what = GKS_PART_STATE) go to the
+ *      neighbours' halos in the same way (also once after gks_set_state, before
+ *      the first step).
+ * Every cell and face then sees exactly the inputs of the single-grid step, and
+ * the slabs' states equal the single-grid state bit for bit.  The positivity
+ * fallback is per slab: a step in which a cell next to a partition needs it
+ * differs from the single-grid step there (see the design notes).
+ * The edge and halo buffers hold raw compute-type data of gks_part_halo_bytes
+ * bytes (host or device memory: copies use cudaMemcpyDefault); the calls are
+ * synchronous.  Nothing here uses more than the handle's own GPU: the exchange
+ * between slabs is the caller's (copies, NCCL or a host transport). */
+#define GKS_PART_STATE 0
+#define GKS_PART_RECORDS 1
+
+/* Bytes of one edge row of averages (what = GKS_PART_STATE) or of reconstruction
+ * records (GKS_PART_RECORDS), ghost columns included. */
+gks_status gks_part_halo_bytes(const gks_handle* h, int what, size_t* bytes);
+
+/* CFL bound of the slab's current state (its cells' minimum; see gks_step). */
+gks_status gks_part_bound(gks_handle* h, double* bound);
+
+/* Opens a step of the given (global) dt and reconstructs the slab's cells. */
+gks_status gks_part_recon(gks_handle* h, double dt);
+
+/* Evolves the slab's faces and updates its cells; closes the step.  Returns
+ * GKS_ENONPHYSICAL (state kept) like gks_step. */
+gks_status gks_part_finish(gks_handle* h);
+
+/* Copies the slab's edge row on y-side `side` (2: low, 3: high) into dst, or the
+ * neighbour's row from src into the slab's halo on that side; `side` must be an
+ * exchange side. */
+gks_status gks_part_get_edge(gks_handle* h, int side, int what, void* dst);
+gks_status gks_part_set_halo(gks_handle* h, int side, int what, const void* src);
 
 /* ---- batched form: many independent grids in one persistent launch ----
  *

@@ -269,6 +269,15 @@ __global__ void k_to_double(const R* src, double* dst, size_t n) {
   if (k < n) dst[k] = (double)src[k];
 }
 
+// opens a step of the partitioned form with the dt the caller reduced over all slabs
+__global__ void k_part_begin(Ctrl* c, double dt) {
+  c->dt = dt;
+  c->dt_f = (float)dt;
+  c->skip = (c->status != GKS_OK || !(dt > 0.0)) ? 1 : 0;
+  c->dtb[0] = c->dtb[1] = c->dtb[2] = dbits(INFINITY);
+  c->bad_found[0] = c->bad_found[1] = 0;
+}
+
 __global__ void k_set_dt(Ctrl* c, double dt) {
   c->dt = dt;
   c->dt_f = (float)dt;
@@ -375,13 +384,13 @@ cudaError_t launch_recon(gks_handle* h, int force, int begin = 0, double cfl = 0
 // the ghost ring is refreshed first and the step is neither opened nor closed.
 template <class R, class TW>
 gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double t_end, bool with_begin_end,
-                               bool do_update, int force, cudaEvent_t* ev = nullptr) {
+                               bool do_update, int force, cudaEvent_t* ev = nullptr, bool do_recon = true) {
   const Geo& g = h->g;
   cudaStream_t s = h->stream;
   auto mark = [&](int k) {
     if (ev) cudaEventRecord(ev[k], s);
   };
-  if (!with_begin_end) launch_ghost<R>(h, force);
+  if (!with_begin_end && do_recon) launch_ghost<R>(h, force);
   // programmatic dependent launch between the step's kernels, except when events
   // are recorded between them (per-kernel timing)
   const bool pdl = ev == nullptr;
@@ -390,7 +399,7 @@ gks_status launch_step_kernels(gks_handle* h, double cfl, double dt_max, double 
     if (le == cudaSuccess) le = e;
   };
   mark(0);
-  keep(launch_recon<R, TW>(h, force, with_begin_end ? 1 : 0, cfl, dt_max, t_end, pdl));
+  if (do_recon) keep(launch_recon<R, TW>(h, force, with_begin_end ? 1 : 0, cfl, dt_max, t_end, pdl));
   mark(1);
   const dim3 b2(32, 8), bf(32, 4);
   // the x- and y-face evolutions are independent: without per-kernel timing the y-faces run
@@ -571,14 +580,16 @@ gks_status check_args(int nx, int ny, double Lx, double Ly, double gamma, double
   }
   if (bc) {
     for (int k = 0; k < 4; ++k) {
-      if (bc[k].kind < 0 || bc[k].kind > 4) { why = "unknown boundary kind"; return GKS_EINVAL; }
+      if (bc[k].kind < 0 || bc[k].kind > GKS_BC_EXCHANGE) { why = "unknown boundary kind"; return GKS_EINVAL; }
+      if (bc[k].kind == GKS_BC_EXCHANGE && k < 2) { why = "exchange sides are y sides"; return GKS_EINVAL; }
       if (bc[k].kind == GKS_BC_NOSLIP_ISOTHERMAL && !(bc[k].T_wall > 0)) { why = "T_wall must be > 0"; return GKS_EINVAL; }
     }
     if ((bc[0].kind == GKS_BC_PERIODIC) != (bc[1].kind == GKS_BC_PERIODIC) ||
         (bc[2].kind == GKS_BC_PERIODIC) != (bc[3].kind == GKS_BC_PERIODIC)) {
       why = "periodic must be set on both sides of an axis"; return GKS_EINVAL;
     }
-    if ((nx == 1 && bc[0].kind != GKS_BC_PERIODIC) || (ny == 1 && bc[2].kind != GKS_BC_PERIODIC)) {
+    if ((nx == 1 && bc[0].kind != GKS_BC_PERIODIC) ||
+        (ny == 1 && bc[2].kind != GKS_BC_PERIODIC && (bc[2].kind != GKS_BC_EXCHANGE || bc[3].kind != GKS_BC_EXCHANGE))) {
       why = "a single cell across needs periodic sides"; return GKS_EINVAL;
     }
   }
@@ -880,6 +891,105 @@ gks_status gks_debug_flux(gks_handle* h, double dt, double* Fx, double* Fy, doub
       k_to_double<float><<<(unsigned)((p.n + 255) / 256), 256, 0, h->stream>>>((const float*)p.src, h->staging, p.n);
     CK(cudaMemcpyAsync(p.dst, h->staging, p.n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   }
+  CK(cudaStreamSynchronize(h->stream));
+  return GKS_OK;
+}
+
+// ---- partitioned step (domain decomposition into row slabs) ----
+
+gks_status gks_part_halo_bytes(const gks_handle* h, int what, size_t* bytes) {
+  if (!h || !bytes || (what != GKS_PART_STATE && what != GKS_PART_RECORDS)) return GKS_EINVAL;
+  const Geo& g = h->g;
+  const size_t es = h->prec == GKS_FP64 ? sizeof(double) : sizeof(float);
+  // averages: 4 FP64 planes, or the 4 hi and 4 lo FP32 planes, nx + 2 values each
+  *bytes = what == GKS_PART_STATE ? (size_t)8 * sizeof(float) * (g.nx + 2) : (size_t)(g.nx + 2) * kRec * es;
+  return GKS_OK;
+}
+
+gks_status gks_part_bound(gks_handle* h, double* bound) {
+  if (!h || !bound) return GKS_EINVAL;
+  CK(cudaSetDevice(h->device));
+  gks_status st = read_ctrl(h);
+  if (st != GKS_OK) return st;
+  memcpy(bound, &h->hctrl->bound, sizeof(double));
+  if (h->hctrl->status != GKS_OK) return fail(h, (gks_status)h->hctrl->status, "the slab's state is not physical");
+  return GKS_OK;
+}
+
+gks_status gks_part_recon(gks_handle* h, double dt) {
+  if (!h || !(dt > 0)) return fail(h, GKS_EINVAL, "gks_part_recon: dt > 0 required");
+  CK(cudaSetDevice(h->device));
+  k_part_begin<<<1, 1, 0, h->stream>>>(h->ctrl, dt);
+  CK(cudaGetLastError());
+  const cudaError_t e = h->prec == GKS_FP64 ? launch_recon<double, double>(h, 0) : launch_recon<float, float>(h, 0);
+  CK(e);
+  return GKS_OK;
+}
+
+gks_status gks_part_finish(gks_handle* h) {
+  if (!h) return GKS_EINVAL;
+  CK(cudaSetDevice(h->device));
+  gks_status st = h->prec == GKS_FP64
+                      ? launch_step_kernels<double, double>(h, 0, 0, 0, true, true, 0, nullptr, false)
+                      : launch_step_kernels<float, float>(h, 0, 0, 0, true, true, 0, nullptr, false);
+  if (st != GKS_OK) return st;
+  st = read_ctrl(h);
+  if (st != GKS_OK) return st;
+  if (h->hctrl->status != GKS_OK) return fail(h, (gks_status)h->hctrl->status, "step produced a non-physical state; state kept");
+  return GKS_OK;
+}
+
+namespace {
+// one edge or halo row: (device address of its first byte, pitch between planes, planes,
+// bytes per plane row); row j of the current buffer
+gks_status part_row(gks_handle* h, int side, int what, bool halo, char** p, size_t* pitch, int* rows,
+                    size_t* width) {
+  if (side != 2 && side != 3) return fail(h, GKS_EINVAL, "side must be 2 (y low) or 3 (y high)");
+  if (h->g.bc.kind[side] != GKS_BC_EXCHANGE) return fail(h, GKS_EINVAL, "not an exchange side");
+  if (what != GKS_PART_STATE && what != GKS_PART_RECORDS) return fail(h, GKS_EINVAL, "what must be state or records");
+  gks_status st = read_ctrl(h);
+  if (st != GKS_OK) return st;
+  const Geo& g = h->g;
+  const int j = halo ? (side == 2 ? -1 : g.ny) : (side == 2 ? 0 : g.ny - 1);
+  const size_t es = h->prec == GKS_FP64 ? sizeof(double) : sizeof(float);
+  if (what == GKS_PART_STATE) {
+    const int par = (int)(h->hctrl->steps & 1);
+    *p = (char*)h->U[par] + ((size_t)(j + 1) * g.pitch) * es;
+    *pitch = g.plane * es;
+    *rows = h->prec == GKS_FP64 ? 4 : 8;
+    *width = (size_t)(g.nx + 2) * es;
+  } else {
+    *p = (char*)h->rec + ri(g, -1, j) * es;
+    *pitch = 0;
+    *rows = 1;
+    *width = (size_t)(g.nx + 2) * kRec * es;
+  }
+  return GKS_OK;
+}
+}  // namespace
+
+gks_status gks_part_get_edge(gks_handle* h, int side, int what, void* dst) {
+  if (!h || !dst) return GKS_EINVAL;
+  CK(cudaSetDevice(h->device));
+  char* p;
+  size_t pitch, width;
+  int rows;
+  gks_status st = part_row(h, side, what, false, &p, &pitch, &rows, &width);
+  if (st != GKS_OK) return st;
+  CK(cudaMemcpy2DAsync(dst, width, p, rows > 1 ? pitch : width, width, rows, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return GKS_OK;
+}
+
+gks_status gks_part_set_halo(gks_handle* h, int side, int what, const void* src) {
+  if (!h || !src) return GKS_EINVAL;
+  CK(cudaSetDevice(h->device));
+  char* p;
+  size_t pitch, width;
+  int rows;
+  gks_status st = part_row(h, side, what, true, &p, &pitch, &rows, &width);
+  if (st != GKS_OK) return st;
+  CK(cudaMemcpy2DAsync(p, rows > 1 ? pitch : width, src, width, width, rows, cudaMemcpyDefault, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return GKS_OK;
 }

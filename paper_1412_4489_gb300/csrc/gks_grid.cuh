@@ -342,9 +342,11 @@ __host__ __device__ __forceinline__ int perimeter(const Geo& g) { return 2 * (g.
 template <class Fn>
 __device__ __forceinline__ void for_each_ghost_of(const Geo& g, int i, int j, Fn fn) {
   const bool px = g.bc.kind[0] == GKS_BC_PERIODIC, py = g.bc.kind[2] == GKS_BC_PERIODIC;
-  // candidate x (y) coordinates: the cell's own, the low ghost, the high ghost
+  // candidate x (y) coordinates: the cell's own, the low ghost, the high ghost; across an
+  // exchange side the ghost row is the neighbouring slab's, supplied from outside
   const bool xl = i == (px ? g.nx - 1 : 0), xh = i == (px ? 0 : g.nx - 1);
-  const bool yl = j == (py ? g.ny - 1 : 0), yh = j == (py ? 0 : g.ny - 1);
+  const bool yl = j == (py ? g.ny - 1 : 0) && g.bc.kind[2] != GKS_BC_EXCHANGE;
+  const bool yh = j == (py ? 0 : g.ny - 1) && g.bc.kind[3] != GKS_BC_EXCHANGE;
   if (!(xl || xh || yl || yh)) return;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -370,8 +372,8 @@ template <class R>
 __device__ __forceinline__ void ghost_at(const Geo& g, Cells<R> U, int p) {
   const int row = g.nx + 2;
   int i, j;
-  if (p < row) { i = p - 1; j = -1; }
-  else if (p < 2 * row) { i = p - row - 1; j = g.ny; }
+  if (p < row) { i = p - 1; j = -1; if (g.bc.kind[2] == GKS_BC_EXCHANGE) return; }
+  else if (p < 2 * row) { i = p - row - 1; j = g.ny; if (g.bc.kind[3] == GKS_BC_EXCHANGE) return; }
   else if (p < 2 * row + g.ny) { i = -1; j = p - 2 * row; }
   else if (p < 2 * row + 2 * g.ny) { i = g.nx; j = p - 2 * row - g.ny; }
   else return;
@@ -707,16 +709,19 @@ __device__ __forceinline__ void flux_face(const Geo& g, const FaceConst<R>& C, c
   const int f = AX == 0 ? i : j;     // face index along the normal
   const int nf = AX == 0 ? nx : ny;  // faces 0 and nf are on the boundary
   const int lo_side = AX == 0 ? 0 : 2, hi_side = lo_side + 1;
+  // the two cells along the normal: across a periodic side the wrapped cell, across an
+  // exchange side the neighbouring slab's (its record in the halo row), across any other
+  // the image of the inside cell's polynomial
   src.cl = f - 1;
   src.cr = f;
   src.img_lo = src.img_hi = 0;
   if (f == 0) {
     if (g.bc.kind[lo_side] == GKS_BC_PERIODIC) src.cl = nf - 1;
-    else src.img_lo = g.bc.kind[lo_side];
+    else if (g.bc.kind[lo_side] != GKS_BC_EXCHANGE) src.img_lo = g.bc.kind[lo_side];
   }
   if (f == nf) {
     if (g.bc.kind[hi_side] == GKS_BC_PERIODIC) src.cr = 0;
-    else src.img_hi = g.bc.kind[hi_side];
+    else if (g.bc.kind[hi_side] != GKS_BC_EXCHANGE) src.img_hi = g.bc.kind[hi_side];
   }
   src.hn = C.dn;
   src.ht = C.dtan;
@@ -803,11 +808,11 @@ __device__ __forceinline__ void kfvs_face(const Geo& g, const R* U, R gm1, R K, 
   src.img_lo = src.img_hi = 0;
   if (f == 0) {
     if (g.bc.kind[lo_side] == GKS_BC_PERIODIC) src.cl = nf - 1;
-    else src.img_lo = g.bc.kind[lo_side];
+    else if (g.bc.kind[lo_side] != GKS_BC_EXCHANGE) src.img_lo = g.bc.kind[lo_side];
   }
   if (f == nf) {
     if (g.bc.kind[hi_side] == GKS_BC_PERIODIC) src.cr = 0;
-    else src.img_hi = g.bc.kind[hi_side];
+    else if (g.bc.kind[hi_side] != GKS_BC_EXCHANGE) src.img_hi = g.bc.kind[hi_side];
   }
   src.gamma = GeoR<R>::gamma(g);
   src.uwt_lo = GeoR<R>::uwt(g, lo_side);

@@ -17,6 +17,8 @@ from . import build as _build
 
 GKS_OK, GKS_EINVAL, GKS_ENOMEM, GKS_ECUDA, GKS_ENONPHYSICAL, GKS_ETIMEOUT, GKS_EUNSUPPORTED = range(7)
 GKS_BC_PERIODIC, GKS_BC_OUTFLOW, GKS_BC_SLIPWALL, GKS_BC_NOSLIP_ISOTHERMAL, GKS_BC_NOSLIP_ADIABATIC = range(5)
+GKS_BC_EXCHANGE = 5
+GKS_PART_STATE, GKS_PART_RECORDS = 0, 1
 GKS_FP64, GKS_FP32_BULK = 0, 1
 STATUS_NAMES = ["GKS_OK", "GKS_EINVAL", "GKS_ENOMEM", "GKS_ECUDA", "GKS_ENONPHYSICAL", "GKS_ETIMEOUT",
                 "GKS_EUNSUPPORTED"]
@@ -79,6 +81,15 @@ def load(path: str | None = None):
     L.gks_face_op_count.argtypes = [_dp, _dp, _dp, D, D, D, D, D, D, D, D, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_longlong)]
     L.gks_measure_alu_peak.argtypes = [ctypes.c_int, _dp]
+    L.gks_part_halo_bytes.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+    L.gks_part_bound.argtypes = [H, _dp]
+    L.gks_part_recon.argtypes = [H, D]
+    L.gks_part_finish.argtypes = [H]
+    L.gks_part_get_edge.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    L.gks_part_set_halo.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    for name in ("gks_part_halo_bytes", "gks_part_bound", "gks_part_recon", "gks_part_finish", "gks_part_get_edge",
+                 "gks_part_set_halo"):
+        getattr(L, name).restype = ctypes.c_int
     L.gks_step_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, D, D, D, D, D, ctypes.POINTER(gks_bc),
                                    ctypes.POINTER(gks_options), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, D, D,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _dp, ctypes.c_void_p]
@@ -137,6 +148,44 @@ def _dev(t):
 def _check(h, st):
     if st != GKS_OK:
         raise GKSError(st, load().gks_last_error(h).decode())
+
+
+def _buf(b):
+    """Address of a contiguous byte buffer: a numpy array (host) or a torch tensor (host or CUDA)."""
+    if isinstance(b, np.ndarray):
+        assert b.flags["C_CONTIGUOUS"]
+        return ctypes.c_void_p(b.ctypes.data)
+    assert b.is_contiguous()
+    return ctypes.c_void_p(b.data_ptr())
+
+
+# ---- partitioned step (row slabs of one grid; see gks.h) ----
+def gks_part_halo_bytes(h, what):
+    n = ctypes.c_size_t(0)
+    _check(h, load().gks_part_halo_bytes(h, int(what), ctypes.byref(n)))
+    return n.value
+
+
+def gks_part_bound(h):
+    b = ctypes.c_double(0.0)
+    _check(h, load().gks_part_bound(h, ctypes.byref(b)))
+    return b.value
+
+
+def gks_part_recon(h, dt):
+    _check(h, load().gks_part_recon(h, float(dt)))
+
+
+def gks_part_finish(h):
+    _check(h, load().gks_part_finish(h))
+
+
+def gks_part_get_edge(h, side, what, dst):
+    _check(h, load().gks_part_get_edge(h, int(side), int(what), _buf(dst)))
+
+
+def gks_part_set_halo(h, side, what, src):
+    _check(h, load().gks_part_set_halo(h, int(side), int(what), _buf(src)))
 
 
 def gks_default_options(precision=GKS_FP64, **kw) -> gks_options:
