@@ -62,6 +62,7 @@ struct Moments {
   R u[NU];
   R v[NV];
   R xi2, xi4;
+  R kap;  // <xi^4> - <xi^2>^2 = 2 K var^2
 };
 
 // kind: 0 full space, +1 over u > 0, -1 over u < 0; var = 1/(2 lam) = p/rho, formed
@@ -89,6 +90,7 @@ GKS_FN void moments(R U, R V, R lam, R var, R K, int kind, Moments<R, NU, NV>& m
   for (int n = 3; n < NV; ++n) m.v[n] = V * m.v[n - 1] + R(n - 1) * var * m.v[n - 2];
   m.xi2 = K * var;
   m.xi4 = K * (K + R(2)) * var * var;
+  m.kap = R(2) * K * var * var;
 }
 
 // The same half-space moments from their first two entries h = <u^0>, g = <u^1>
@@ -106,6 +108,7 @@ GKS_FN void moments_from(R U, R V, R var, R K, R h, R g, Moments<R, NU, NV>& m) 
   for (int n = 3; n < NV; ++n) m.v[n] = V * m.v[n - 1] + R(n - 1) * var * m.v[n - 2];
   m.xi2 = K * var;
   m.xi4 = K * (K + R(2)) * var * var;
+  m.kap = R(2) * K * var * var;
 }
 
 // <u^A v^B psi> and <xi^2 u^A v^B psi>, psi = (1, u, v, (u^2+v^2+xi^2)/2)
@@ -387,41 +390,51 @@ GKS_FN void poly_of(const Groups<R>& g, Poly<R>& P) {
 }
 
 // out += rho <u^SU P psi>, psi = (1, u, v, (u^2 + v^2 + xi^2) / 2); D / D1: the
-// degree of P in (u, v) for c = 0 / c = 1 (4 / 2, or 3 / 1 for the y-linear part)
+// degree of P in (u, v) for c = 0 / c = 1 (4 / 2, or 3 / 1 for the y-linear part).
+// <xi^2> is a number, so the xi^2 monomials fold into the others: with
+// q_ab = p0_ab + <xi^2> p1_ab, the first three components are sums of q_ab <u^a><v^b>;
+// the fourth's extra xi^2 weight, sum p0 <xi^2> + p1 <xi^4>, is <xi^2> o0 + kap T with
+// kap = <xi^4> - <xi^2>^2 and T = sum p1_ab <u^a><v^b> (u-moments shifted by SU).
 template <int SU, int D, int D1, class R, int NU, int NV>
 GKS_FN void poly_moments(const Poly<R>& P, const Moments<R, NU, NV>& m, R rho, R out[4]) {
   static_assert(D + SU + 2 < NU && D + 2 < NV, "moment table too short");
   R o0 = R(0), o1 = R(0), o2 = R(0), o3 = R(0);
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const int Dc = c == 0 ? D : D1;
+  for (int b = 0; b <= D; ++b) {
+    // sum_a q u^(a+SU), u^(a+SU+1), u^(a+SU+2) moments (the first term starts each sum)
+    R s0 = R(0), s1 = R(0), s2 = R(0);
 #pragma unroll
-    for (int b = 0; b <= Dc; ++b) {
-      // sum_a p u^(a+SU), u^(a+SU+1), u^(a+SU+2) moments (the first term starts each sum)
-      R s0 = R(0), s1 = R(0), s2 = R(0);
-#pragma unroll
-      for (int a = 0; a <= Dc - b; ++a) {
-        const R p = c == 0 ? P.c0[pidx0(a, b)] : P.c1[pidx1(a, b)];
-        s0 = a == 0 ? p * m.u[SU] : s0 + p * m.u[a + SU];
-        s1 = a == 0 ? p * m.u[SU + 1] : s1 + p * m.u[a + SU + 1];
-        s2 = a == 0 ? p * m.u[SU + 2] : s2 + p * m.u[a + SU + 2];
-      }
-      // <xi^2c v^b>, <xi^2c v^(b+1)>, <xi^2c v^(b+2)> + <xi^2(c+1) v^b> (v^0 = 1)
-      const R vb = c == 0 ? (b == 0 ? R(1) : m.v[b]) : (b == 0 ? m.xi2 : m.xi2 * m.v[b]);
-      const R vb1 = c == 0 ? m.v[b + 1] : m.xi2 * m.v[b + 1];
-      const R vb2 = c == 0 ? m.v[b + 2] + (b == 0 ? m.xi2 : m.xi2 * m.v[b])
-                           : m.xi2 * m.v[b + 2] + (b == 0 ? m.xi4 : m.xi4 * m.v[b]);
-      const bool first = c == 0 && b == 0;
-      o0 = first ? s0 * vb : o0 + s0 * vb;
-      o1 = first ? s1 * vb : o1 + s1 * vb;
-      o2 = first ? s0 * vb1 : o2 + s0 * vb1;
-      o3 = first ? s2 * vb + s0 * vb2 : o3 + s2 * vb + s0 * vb2;
+    for (int a = 0; a <= D - b; ++a) {
+      const R q = a + b <= D1 ? P.c0[pidx0(a, b)] + m.xi2 * P.c1[pidx1(a, b)] : P.c0[pidx0(a, b)];
+      s0 = a == 0 ? q * m.u[SU] : s0 + q * m.u[a + SU];
+      s1 = a == 0 ? q * m.u[SU + 1] : s1 + q * m.u[a + SU + 1];
+      s2 = a == 0 ? q * m.u[SU + 2] : s2 + q * m.u[a + SU + 2];
     }
+    // <v^b>, <v^(b+1)>, <v^(b+2)> (v^0 = 1)
+    if (b == 0) {
+      o0 = s0;
+      o1 = s1;
+      o2 = s0 * m.v[1];
+      o3 = s2 + s0 * m.v[2];
+    } else {
+      o0 = o0 + s0 * m.v[b];
+      o1 = o1 + s1 * m.v[b];
+      o2 = o2 + s0 * m.v[b + 1];
+      o3 = o3 + s2 * m.v[b] + s0 * m.v[b + 2];
+    }
+  }
+  R T = R(0);
+#pragma unroll
+  for (int b = 0; b <= D1; ++b) {
+    R t = R(0);
+#pragma unroll
+    for (int a = 0; a <= D1 - b; ++a) t = a == 0 ? P.c1[pidx1(a, b)] * m.u[SU] : t + P.c1[pidx1(a, b)] * m.u[a + SU];
+    T = b == 0 ? t : T + t * m.v[b];
   }
   out[0] += rho * o0;
   out[1] += rho * o1;
   out[2] += rho * o2;
-  out[3] += rho * (R(0.5) * o3);
+  out[3] += rho * (R(0.5) * (o3 + m.xi2 * o0 + m.kap * T));
 }
 
 template <class R, int NU, int NV>
