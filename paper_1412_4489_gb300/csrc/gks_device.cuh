@@ -751,6 +751,7 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
   }
 
   // ---- kinetic part, Eq. dis2, for both sides ----
+  const bool kin_point = tw.E[7] > R(0);  // e = exp(-dt/tau) >= 0 (the weights at t = dt are multiples of it)
 #pragma unroll 1
   for (int side = 0; side < 2; ++side) {
     // selects, not indexing: a dynamic index would put these arrays in local memory
@@ -775,34 +776,37 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
     Moments<R, 8, 7> mh;
     moments_from(U, V, var, C.K, side ? h0[1] : h0[0], side ? h1[1] : h1[0], mh);
     Groups<R> g;
-    R Y1[4], Yu[4], Yv[4];
-    if (ns) {
-      kinetic_groups<true>(c, tw.I, C.y2, tn, g);
-      add_flux(g, mh, rho, Fl);
-      if (C.prandtl) add_point(g, mh, rho, Mn);
-      kinetic_groups<true>(c, tw.E, C.y2, tn, g);
-      add_point(g, mh, rho, P0);
-      const R wy = -tn * tw.E[7] - tw.E[9];
+    if (ns) kinetic_groups<true>(c, tw.I, C.y2, tn, g);
+    else kinetic_groups<false>(c, tw.I, C.y2, tn, g);
+    add_flux(g, mh, rho, Fl);
+    if (C.prandtl) add_point(g, mh, rho, Mn);
+    // Every weight of the kinetic part at t = dt carries e = exp(-dt/tau), which underflows to
+    // exactly 0 once tau is a small enough fraction of dt (smooth Euler flow): the point
+    // values then get exactly nothing from this side
+    if (kin_point) {
+      R Y1[4], Yu[4], Yv[4];
+      if (ns) {
+        kinetic_groups<true>(c, tw.E, C.y2, tn, g);
+        add_point(g, mh, rho, P0);
+        const R wy = -tn * tw.E[7] - tw.E[9];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        Y1[k] = tw.E[7] * (c.a2[k] - tn * c.Aty[k]);
-        Yu[k] = wy * c.Axy[k];
-        Yv[k] = wy * c.Ayy[k];
-      }
-    } else {
-      kinetic_groups<false>(c, tw.I, C.y2, tn, g);
-      add_flux(g, mh, rho, Fl);
-      if (C.prandtl) add_point(g, mh, rho, Mn);
-      kinetic_groups<false>(c, tw.E, C.y2, tn, g);
-      add_point(g, mh, rho, P0);
+        for (int k = 0; k < 4; ++k) {
+          Y1[k] = tw.E[7] * (c.a2[k] - tn * c.Aty[k]);
+          Yu[k] = wy * c.Axy[k];
+          Yv[k] = wy * c.Ayy[k];
+        }
+      } else {
+        kinetic_groups<false>(c, tw.E, C.y2, tn, g);
+        add_point(g, mh, rho, P0);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        Y1[k] = tw.E[7] * c.a2[k];
-        Yu[k] = -tw.E[9] * c.Axy[k];
-        Yv[k] = -tw.E[9] * c.Ayy[k];
+        for (int k = 0; k < 4; ++k) {
+          Y1[k] = tw.E[7] * c.a2[k];
+          Yu[k] = -tw.E[9] * c.Axy[k];
+          Yv[k] = -tw.E[9] * c.Ayy[k];
+        }
       }
+      add_point_linear(Y1, Yu, Yv, mh, rho, P1);
     }
-    add_point_linear(Y1, Yu, Yv, mh, rho, P1);
   }
 
   // Prandtl-number fix: energy flux += (1/Pr - 1) q, q the time-integrated
