@@ -122,54 +122,6 @@ GKS_FN void psi_mom(const Moments<R, NU, NV>& m, R o[4]) {
   o[3] = R(0.5) * (m.u[A + 2] * m.v[B] + m.u[A] * m.v[B + 2] + ab * m.xi2);
 }
 
-// <X u psi> and <X v psi> for X = X0 + X1 u + X2 v + X3 (u^2+v^2+xi^2)/2 are
-// X0 T_A + X1 T_(A+u) + X2 T_(A+v) + X3 S_A with the psi-moment vectors T and
-// S_A = (<u^2 A psi> + <v^2 A psi> + <xi^2 A psi>)/2, A = u or v: a table formed
-// once per Maxwellian.
-template <class R>
-struct MomTab {
-  R Tu[4], Tuu[4], Tuv[4], Tv[4], Tvv[4], Su[4], Sv[4];
-};
-
-// <xi^2 u^A v^B psi>
-template <int A, int B, class R, int NU, int NV>
-GKS_FN void xi2_psi_mom(const Moments<R, NU, NV>& m, R o[4]) {
-  const R ab = m.u[A] * m.v[B];
-  o[0] = m.xi2 * ab;
-  o[1] = m.xi2 * (m.u[A + 1] * m.v[B]);
-  o[2] = m.xi2 * (m.u[A] * m.v[B + 1]);
-  o[3] = R(0.5) * (m.xi2 * (m.u[A + 2] * m.v[B] + m.u[A] * m.v[B + 2]) + m.xi4 * ab);
-}
-
-template <class R, int NU, int NV>
-GKS_FN void mom_tab(const Moments<R, NU, NV>& m, MomTab<R>& t) {
-  psi_mom<1, 0>(m, t.Tu);
-  psi_mom<2, 0>(m, t.Tuu);
-  psi_mom<1, 1>(m, t.Tuv);
-  psi_mom<0, 1>(m, t.Tv);
-  psi_mom<0, 2>(m, t.Tvv);
-  R a[4], b[4], c[4];
-  psi_mom<3, 0>(m, a);
-  psi_mom<1, 2>(m, b);
-  xi2_psi_mom<1, 0>(m, c);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) t.Su[k] = R(0.5) * (a[k] + b[k] + c[k]);
-  psi_mom<2, 1>(m, a);
-  psi_mom<0, 3>(m, b);
-  xi2_psi_mom<0, 1>(m, c);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) t.Sv[k] = R(0.5) * (a[k] + b[k] + c[k]);
-}
-
-// r = -(<X u psi> + <Y v psi>)
-template <class R>
-GKS_FN void neg_coef_mom(const MomTab<R>& t, const R X[4], const R Y[4], R r[4]) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    r[k] = -(X[0] * t.Tu[k] + X[1] * t.Tuu[k] + X[2] * t.Tuv[k] + X[3] * t.Su[k] +
-             Y[0] * t.Tv[k] + Y[1] * t.Tuv[k] + Y[2] * t.Tvv[k] + Y[3] * t.Sv[k]);
-}
-
 // ---------------------------------------------------------------------------
 // Section 2.2: <a> = rho r for a expanded in psi has a closed-form solution
 // (the moment matrix of a Maxwellian is block structured about (U, V)).  The
@@ -182,6 +134,8 @@ struct SolveK {
   R c4;  // 4 lam^2 / N, N = K + 2
   R s0;  // U^2 + V^2 - N / (2 lam)
   R s1;  // (U^2 + V^2) / 2 + N / (4 lam)
+  R hq;  // (U^2 + V^2) / 2
+  R kc;  // (N + 2) / (4 lam)
 };
 
 template <class R>
@@ -195,21 +149,12 @@ GKS_FN SolveK<R> solve_k(R U, R V, R lam, R var, R N, R iN) {
   k.c4 = R(4) * lam * lam * iN;
   k.s0 = q2 - nv;
   k.s1 = R(0.5) * (q2 + nv);
+  k.hq = R(0.5) * q2;
+  k.kc = R(0.5) * (nv + R(2) * var);
   return k;
 }
 
-template <class R>
-GKS_FN void solve(const SolveK<R>& k, const R r[4], R x[4]) {
-  const R x4 = k.c4 * (R(2) * (r[3] - k.U * r[1] - k.V * r[2]) + k.s0 * r[0]);
-  const R x3 = k.l2 * (r[2] - k.V * r[0]) - k.V * x4;
-  const R x2 = k.l2 * (r[1] - k.U * r[0]) - k.U * x4;
-  x[0] = r[0] - k.U * x2 - k.V * x3 - x4 * k.s1;
-  x[1] = x2;
-  x[2] = x3;
-  x[3] = x4;
-}
-
-// the same for <a> = rho r with r = ir d, ir = 1/rho folded into the factors:
+// <a> = rho r with r = ir d, ir = 1/rho folded into the factors:
 // c4i = c4 ir, l2i = l2 ir
 template <class R>
 GKS_FN void solve_scaled(const SolveK<R>& k, R c4i, R l2i, R ir, const R d[4], R x[4]) {
@@ -301,10 +246,43 @@ struct Coefs {
   R a1[4], a2[4], Axx[4], Axy[4], Ayy[4], A[4], Atx[4], Aty[4], Att[4];
 };
 
-// ir = 1/rho of the Maxwellian
-template <class R, int NU, int NV>
-GKS_FN void coef_systems(const Moments<R, NU, NV>& m, R ir, const SolveK<R>& sk, const R d[5][4],
-                         bool time_terms, bool second_time, Coefs<R>& c) {
+// A coefficient vector X about the Maxwellian's (U, V) in central coordinates: the
+// coefficients of 1, c, d, s = (c^2 + d^2 + xi^2) / 2 with c = u - U, d = v - V
+template <class R>
+GKS_FN void to_central(const SolveK<R>& k, const R X[4], R Y[4]) {
+  Y[0] = X[0] + k.U * X[1] + k.V * X[2] + k.hq * X[3];
+  Y[1] = X[1] + k.U * X[3];
+  Y[2] = X[2] + k.V * X[3];
+  Y[3] = X[3];
+}
+
+template <class R>
+GKS_FN void from_central(const SolveK<R>& k, const R Y[4], R X[4]) {
+  X[3] = Y[3];
+  X[1] = Y[1] - k.U * Y[3];
+  X[2] = Y[2] - k.V * Y[3];
+  X[0] = Y[0] - k.U * X[1] - k.V * X[2] - k.hq * Y[3];
+}
+
+// The time coefficient T of <(X u + Y v + T) psi g> = 0 (X, Y, T in central coordinates):
+// T = -P(u X + v Y), P the projection on span(psi) in the inner product weighted by the
+// Maxwellian.  u X = U X + c X, and the Maxwellian's central moments (<c^2> = 1/(2 lam),
+// <c^4> = 3 <c^2>^2, <xi^2> = K <c^2>) give P(c) = c, P(c^2) = (2/N) s, P(c d) = 0 and
+// P(c s) = kc c with kc = <c^2 s> / <c^2> = (N + 2) / (4 lam); likewise in d.
+template <class R>
+GKS_FN void time_coef(const SolveK<R>& k, R i2N, const R X[4], const R Y[4], R T[4]) {
+  T[0] = -(k.U * X[0] + k.V * Y[0]);
+  T[1] = -(k.U * X[1] + k.V * Y[1] + X[0] + k.kc * X[3]);
+  T[2] = -(k.U * X[2] + k.V * Y[2] + Y[0] + k.kc * Y[3]);
+  T[3] = -(k.U * X[3] + k.V * Y[3] + i2N * (X[1] + Y[2]));
+}
+
+// ir = 1/rho of the Maxwellian, i2N = 2 / N.  The spatial coefficients by the closed-form
+// solve; the time coefficients (the compatibility conditions of the system after Eq. dis3)
+// by the projection above, in central coordinates, mapped back to the psi basis.
+template <class R>
+GKS_FN void coef_systems(R ir, const SolveK<R>& sk, R i2N, const R d[5][4], bool time_terms, bool second_time,
+                         Coefs<R>& c) {
   const R c4i = sk.c4 * ir, l2i = sk.l2 * ir;
   solve_scaled(sk, c4i, l2i, ir, d[0], c.a1);
   solve_scaled(sk, c4i, l2i, ir, d[1], c.a2);
@@ -312,18 +290,21 @@ GKS_FN void coef_systems(const Moments<R, NU, NV>& m, R ir, const SolveK<R>& sk,
   solve_scaled(sk, c4i, l2i, ir, d[3], c.Axy);
   solve_scaled(sk, c4i, l2i, ir, d[4], c.Ayy);
   if (!time_terms) return;
-  R r[4];
-  MomTab<R> t;
-  mom_tab(m, t);
-  neg_coef_mom(t, c.a1, c.a2, r);  // <A + a1 u + a2 v> = 0
-  solve(sk, r, c.A);
-  neg_coef_mom(t, c.Axx, c.Axy, r);  // <Axx u + Axy v + Atx> = 0
-  solve(sk, r, c.Atx);
-  neg_coef_mom(t, c.Axy, c.Ayy, r);  // <Axy u + Ayy v + Aty> = 0
-  solve(sk, r, c.Aty);
+  R x[4], y[4], z[4], tx[4], ty[4], t[4];
+  to_central(sk, c.a1, x);
+  to_central(sk, c.a2, y);
+  time_coef(sk, i2N, x, y, t);  // <A + a1 u + a2 v> = 0
+  from_central(sk, t, c.A);
+  to_central(sk, c.Axx, x);
+  to_central(sk, c.Axy, y);
+  to_central(sk, c.Ayy, z);
+  time_coef(sk, i2N, x, y, tx);  // <Axx u + Axy v + Atx> = 0
+  time_coef(sk, i2N, y, z, ty);  // <Axy u + Ayy v + Aty> = 0
+  from_central(sk, tx, c.Atx);
+  from_central(sk, ty, c.Aty);
   if (!second_time) return;
-  neg_coef_mom(t, c.Atx, c.Aty, r);  // <Atx u + Aty v + Att> = 0
-  solve(sk, r, c.Att);
+  time_coef(sk, i2N, tx, ty, t);  // <Atx u + Aty v + Att> = 0
+  from_central(sk, t, c.Att);
 }
 
 // The interface distribution grouped by velocity monomial: f = sum over
@@ -451,6 +432,14 @@ GKS_FN void add_point(const Groups<R>& g, const Moments<R, NU, NV>& m, R rho, R 
   poly_moments<0, 4, 2>(P, m, rho, out);
 }
 
+// the same for groups whose u^2, u v, v^2 parts vanish
+template <class R, int NU, int NV>
+GKS_FN void add_point_first(const Groups<R>& g, const Moments<R, NU, NV>& m, R rho, R out[4]) {
+  Poly<R> P;
+  poly_of<false>(g, P);
+  poly_moments<0, 3, 1>(P, m, rho, out);
+}
+
 template <class R, int NU, int NV>
 GKS_FN void add_point_linear(const R Y1[4], const R Yu[4], const R Yv[4], const Moments<R, NU, NV>& m, R rho,
                              R out[4]) {
@@ -468,7 +457,8 @@ GKS_FN void add_point_linear(const R Y1[4], const R Yu[4], const R Yv[4], const 
 
 // Eq. dis1 grouped: weights W = I (flux, mean) or E (point); y2 = dtan^2/12 is both
 // the face mean of y^2 and y^2 at the Gauss points.
-template <class R>
+// SECOND = false: W[4] = 0, the groups of u^2, u v, v^2 vanish and are not formed.
+template <bool SECOND = true, class R>
 GKS_FN void hydro_groups(const Coefs<R>& c, const R* W, R y2, Groups<R>& g) {
   const R h5 = R(0.5) * W[5], hy = R(0.5) * y2 * W[1], h4 = R(0.5) * W[4];
 #pragma unroll
@@ -476,9 +466,11 @@ GKS_FN void hydro_groups(const Coefs<R>& c, const R* W, R y2, Groups<R>& g) {
     g.X1[k] = W[3] * c.A[k] + h5 * c.Att[k] + hy * c.Ayy[k];
     g.Xu[k] = W[2] * c.a1[k] + W[6] * c.Atx[k];
     g.Xv[k] = W[2] * c.a2[k] + W[6] * c.Aty[k];
-    g.Xuu[k] = h4 * c.Axx[k];
-    g.Xuv[k] = W[4] * c.Axy[k];
-    g.Xvv[k] = h4 * c.Ayy[k];
+    if (SECOND) {
+      g.Xuu[k] = h4 * c.Axx[k];
+      g.Xuv[k] = W[4] * c.Axy[k];
+      g.Xvv[k] = h4 * c.Ayy[k];
+    }
   }
   g.X1[0] += W[1];
 }
@@ -541,7 +533,7 @@ struct FaceParams {
 // Per-launch constants of the face routine in the compute type
 template <class R>
 struct FaceConst {
-  R gamma, gm1, K, N, iN, dn, dtan, y2, mu, pr_fix, tau_eps, tau_C;
+  R gamma, gm1, K, N, iN, i2N, dn, dtan, y2, mu, pr_fix, tau_eps, tau_C;
   R dn2_12, dt2_24;             // dn^2 / 12, dtan^2 / 24 (face values of the cell polynomial)
   R i4n, i4t, i8n2, i2nt, i2t2;  // 1/(4 dn), 1/(4 dt), 1/(8 dn^2), 1/(2 dn dt), 1/(2 dt^2)
   bool ns, prandtl;
@@ -555,6 +547,7 @@ GKS_FN FaceConst<R> face_const(const FaceParams& P) {
   c.K = R((4.0 - 2.0 * P.gamma) / (P.gamma - 1.0));  // internal degrees of freedom, Section 2.1
   c.N = R(2.0 / (P.gamma - 1.0));                     // K + 2
   c.iN = R(0.5 * (P.gamma - 1.0));
+  c.i2N = R(P.gamma - 1.0);  // 2 / N
   c.dn = R(P.dn);
   c.dtan = R(P.dtan);
   c.y2 = R(P.dtan * P.dtan / 12.0);
@@ -709,6 +702,9 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
 
   TimeW<R> tw;
   time_weights(dt, tau, tw);
+  // e = exp(-dt/tau) >= 0 underflows to exactly 0 once tau is a small enough fraction of dt
+  // (smooth Euler flow); the point-value terms whose weights carry it are then not formed
+  const bool kin_point = tw.E[7] > R(0);
 
   R Fl[4] = {0, 0, 0, 0}, P0[4] = {0, 0, 0, 0}, P1[4] = {0, 0, 0, 0}, Mn[4] = {0, 0, 0, 0};
 
@@ -733,13 +729,20 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
     Moments<R, 8, 7> m;
     moments(u0, v0, lam0, var0, C.K, 0, m);
     Coefs<R> c;
-    coef_systems(m, ir0, solve_k(u0, v0, lam0, var0, C.N, C.iN), d, true, true, c);
+    coef_systems(ir0, solve_k(u0, v0, lam0, var0, C.N, C.iN), C.i2N, d, true, true, c);
     Groups<R> g;
     hydro_groups(c, tw.I, C.y2, g);
     add_flux(g, m, r0, Fl);
     if (C.prandtl) add_point(g, m, r0, Mn);
-    hydro_groups(c, tw.E, C.y2, g);
-    add_point(g, m, r0, P0);
+    if (kin_point) {
+      hydro_groups(c, tw.E, C.y2, g);
+      add_point(g, m, r0, P0);
+    } else {
+      // e = exp(-dt/tau) = 0: the weight of the second-order groups at t = dt, -(dt^2 + 2 dt tau) e,
+      // is exactly 0
+      hydro_groups<false>(c, tw.E, C.y2, g);
+      add_point_first(g, m, r0, P0);
+    }
     R Y1[4], Yu[4], Yv[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -751,7 +754,6 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
   }
 
   // ---- kinetic part, Eq. dis2, for both sides ----
-  const bool kin_point = tw.E[7] > R(0);  // e = exp(-dt/tau) >= 0 (the weights at t = dt are multiples of it)
 #pragma unroll 1
   for (int side = 0; side < 2; ++side) {
     // selects, not indexing: a dynamic index would put these arrays in local memory
@@ -769,9 +771,8 @@ GKS_FN void face_evolution(const FaceConst<R>& C, const Src& src, R dt, R F[4], 
 #pragma unroll
           for (int k = 0; k < 4; ++k) d[q][k] = S.w[q + 1][k];
       }
-      Moments<R, 6, 6> mf;  // full-space moments fix the time coefficients of g_k (NS only)
-      if (ns) moments(U, V, lam, var, C.K, 0, mf);
-      coef_systems(mf, ir, solve_k(U, V, lam, var, C.N, C.iN), d, ns, false, c);
+      // the time coefficients of g_k (NS only)
+      coef_systems(ir, solve_k(U, V, lam, var, C.N, C.iN), C.i2N, d, ns, false, c);
     }
     Moments<R, 8, 7> mh;
     moments_from(U, V, var, C.K, side ? h0[1] : h0[0], side ? h1[1] : h1[0], mh);
