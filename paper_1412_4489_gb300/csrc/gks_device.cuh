@@ -20,6 +20,9 @@ namespace gks {
 
 template <class R> struct Prec;
 // series_below: x = dt/tau below which the time weights are summed from series;
+// series_terms: the sums stop before x^series_terms / series_terms!, at which the largest
+// relative truncation error over x < series_below is below the type's rounding (FP64: 17
+// terms reach it, FP32: 18);
 // tie: relative width within which two cross-derivative candidates count as equal.
 // FP64: far above its rounding noise, far below any real difference.  FP32: ~16
 // ulps, just above the rounding noise of the candidates; a wider band makes FP32
@@ -27,12 +30,12 @@ template <class R> struct Prec;
 // measured worse against the FP64 results on discontinuous data.
 template <> struct Prec<double> {
   static constexpr double series_below = 0.5;
-  static constexpr int series_terms = 22;
+  static constexpr int series_terms = 18;
   static constexpr double tie = 1e-8;
 };
 template <> struct Prec<float> {
   static constexpr float series_below = 2.0f;
-  static constexpr int series_terms = 24;
+  static constexpr int series_terms = 18;
   static constexpr float tie = 1e-6f;
 };
 
