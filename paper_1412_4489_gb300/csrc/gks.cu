@@ -64,8 +64,15 @@ __global__ void k_ghost(Geo g, Cells<R> U0, Cells<R> U1, const Ctrl* c, int forc
 // begin = 1: block 0 also opens the step (ctrl_begin); the other blocks then do
 // not look at the skip flag it sets (coefficients of a skipped step go unused).
 // CHAR: reconstruction in characteristic variables.
+// resident 256-thread blocks per SM the reconstruction is compiled for: FP32 conservative 4
+// (64 registers; the kernel is latency-bound, so occupancy pays), FP64 characteristic 1
+// (it needs more than 128 registers), the others 2 (128)
+template <class R, bool CHAR> struct ReconBlocks { static constexpr int value = 2; };
+template <> struct ReconBlocks<float, false> { static constexpr int value = 4; };
+template <> struct ReconBlocks<double, true> { static constexpr int value = 1; };
+
 template <class R, class TW, bool CHAR>
-__global__ void __launch_bounds__(256) k_recon(Geo g, const R* U0, const R* U1, const TW* Wx0, const TW* Wx1,
+__global__ void __launch_bounds__(256, ReconBlocks<R, CHAR>::value) k_recon(Geo g, const R* U0, const R* U1, const TW* Wx0, const TW* Wx1,
                                                const TW* Wy0, const TW* Wy1, R* __restrict__ rec, R dx, R dy,
                                                R weps, R wC, Ctrl* c, int force, int begin, double cfl,
                                                double dt_max, double t_end) {
@@ -103,8 +110,15 @@ __global__ void __launch_bounds__(128, FluxBlocks<R>::value) k_flux(Geo g, FaceC
                                                                     const Ctrl* c, int force) {
   pdl_enter();
   if (!force && c->skip) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (AX == 0 && (g.nx & 31) == 0 && blockIdx.x == gridDim.x - 1) {
+    // the column of blocks past a row of nx = 32 k x-faces holds only the last face of
+    // each row: it takes those faces 128 rows to a block, in whole warps, instead of one
+    // busy lane per warp
+    i = g.nx;
+    j = blockIdx.y * 128 + threadIdx.y * 32 + threadIdx.x;
+  }
   const int fx = AX == 0 ? g.nx + 1 : g.nx, fy = AX == 0 ? g.ny : g.ny + 1;
   if (i >= fx || j >= fy) return;
   const int par = (int)(c->steps & 1);

@@ -229,7 +229,9 @@ __global__ void __launch_bounds__(kThreads, BatchBlocks<R>::value) k_batch(Args<
             }
           }
         }
-        block_bound_to<R>(inv, &c->dtb[pass - 1]);
+        // per warp: a block barrier per tile would hold every warp of the block until the
+        // slowest one's loads return
+        warp_bound_to<R>(inv, &c->dtb[pass - 1]);
       }
       if (!grid_barrier(a.bar)) return;
       stamp(s, 2 + pass);

@@ -846,43 +846,52 @@ GKS_FN R minmod(R a, R b) {
 // Cell-size constants of the reconstruction, formed once per cell (not per variable)
 template <class R>
 struct ReconK {
-  R dx, dy, idx, idy, idx2, idy2, dx6, dy6, r3, dx2, dy2, dx2_12, dy2_12, dx4, dy4, dxy2, weps, I1;
+  R dx, dy, idx, idy;
+  R dx6, dy6;          // dx / 6, dy / 6
+  R r3;                // sqrt(3) / (dx dy)
+  R idx2, idy2;        // 1 / dx^2, 1 / dy^2
+  R dx2, dy2;          // smoothness indicator: weights of c2^2, c3^2,
+  R kc4, kc5, kc6;     //   c4^2 (13/12 dx^4), c5^2 (13/12 dy^4), c6^2 (7/6 dx^2 dy^2)
+  R dx2_12, dy2_12;    // dx^2 / 12, dy^2 / 12 (face values of the polynomial)
+  R weps, b1sq;        // eps and (eps + I(U1))^2, I(U1) = C dx dy
 };
 
+// idx, idy: 1/dx, 1/dy of the grid (formed once on the host)
 template <class R>
-GKS_FN ReconK<R> recon_k(R dx, R dy, R weps, R wC) {
+GKS_FN ReconK<R> recon_k(R dx, R dy, R idx, R idy, R weps, R wC) {
   ReconK<R> k;
   k.dx = dx;
   k.dy = dy;
-  k.idx = d_div(R(1), dx);
-  k.idy = d_div(R(1), dy);
-  k.idx2 = k.idx * k.idx;
-  k.idy2 = k.idy * k.idy;
+  k.idx = idx;
+  k.idy = idy;
+  k.idx2 = idx * idx;
+  k.idy2 = idy * idy;
   k.dx6 = dx * R(1.0 / 6.0);
   k.dy6 = dy * R(1.0 / 6.0);
-  k.r3 = R(1.7320508075688772) * k.idx * k.idy;  // sqrt(3) / (dx dy)
+  k.r3 = R(1.7320508075688772) * idx * idy;  // sqrt(3) / (dx dy)
   k.dx2 = dx * dx;
   k.dy2 = dy * dy;
+  k.kc4 = R(13.0 / 12.0) * k.dx2 * k.dx2;
+  k.kc5 = R(13.0 / 12.0) * k.dy2 * k.dy2;
+  k.kc6 = R(7.0 / 6.0) * k.dx2 * k.dy2;
   k.dx2_12 = k.dx2 * R(1.0 / 12.0);
   k.dy2_12 = k.dy2 * R(1.0 / 12.0);
-  k.dx4 = k.dx2 * k.dx2;
-  k.dy4 = k.dy2 * k.dy2;
-  k.dxy2 = k.dx2 * k.dy2;
   k.weps = weps;
-  k.I1 = wC * dx * dy;  // I(U1) = C dx dy
+  const R b1 = weps + wC * dx * dy;
+  k.b1sq = b1 * b1;
   return k;
 }
 
 template <class R>
 GKS_FN void recon_var(R c, R e, R w, R n, R s, R em, R ep, R wm, R wp, R nm, R np, R sm, R sp,
                       const ReconK<R>& K, R a[5]) {
-  // one-sided stencils: face Gauss mean S and neighbour average (Eq. over-sys)
-  const R Se = R(0.5) * (em + ep), Sw = R(0.5) * (wm + wp);
-  const R Sn = R(0.5) * (nm + np), Ss = R(0.5) * (sm + sp);
-  const R a4 = minmod(R(3) * (c + w - R(2) * Sw) * K.idx2, R(3) * (c + e - R(2) * Se) * K.idx2);
-  const R a2 = minmod(-R(2) * (Sw - c) * K.idx + a4 * K.dx6, R(2) * (Se - c) * K.idx - a4 * K.dx6);
-  const R a5 = minmod(R(3) * (c + s - R(2) * Ss) * K.idy2, R(3) * (c + n - R(2) * Sn) * K.idy2);
-  const R a3 = minmod(-R(2) * (Ss - c) * K.idy + a5 * K.dy6, R(2) * (Sn - c) * K.idy - a5 * K.dy6);
+  // one-sided stencils (Eq. over-sys) from each face's Gauss-point sum (twice its mean) and
+  // the neighbour average
+  const R se = em + ep, sw = wm + wp, sn = nm + np, ss = sm + sp;
+  const R a4 = minmod(R(3) * (c + w - sw) * K.idx2, R(3) * (c + e - se) * K.idx2);
+  const R a2 = minmod((R(2) * c - sw) * K.idx + a4 * K.dx6, (se - R(2) * c) * K.idx - a4 * K.dx6);
+  const R a5 = minmod(R(3) * (c + s - ss) * K.idy2, R(3) * (c + n - sn) * K.idy2);
+  const R a3 = minmod((R(2) * c - ss) * K.idy + a5 * K.dy6, (sn - R(2) * c) * K.idy - a5 * K.dy6);
   // cross derivative of the four one-sided stencils with limited a2, a3:
   // sx (sqrt3 Dx/(dx dy) - a3/dx) + sy (sqrt3 Dy/(dx dy) - a2/dy), smallest magnitude
   const R xe = K.r3 * (ep - em) - a3 * K.idx, xw = K.r3 * (wp - wm) - a3 * K.idx;
@@ -902,18 +911,18 @@ GKS_FN void recon_var(R c, R e, R w, R n, R s, R em, R ep, R wm, R wp, R nm, R n
   const R c2 = R(0.5) * (e - w) * K.idx, c4 = (e - R(2) * c + w) * K.idx2;
   const R c3 = R(0.5) * (n - s) * K.idy, c5 = (n - R(2) * c + s) * K.idy2;
   const R c6 = R(0.5) * K.r3 * ((ep - em) - (wp - wm) + (np - nm) - (sp - sm));
-  // Eq. average: alpha = 1/(eps + I)^2, I(U1) = C dx dy
-  const R I2 = K.dx2 * (c2 * c2 + c4 * c4 * K.dx2_12 + c6 * c6 * K.dy2_12) +
-               K.dy2 * (c3 * c3 + c5 * c5 * K.dy2_12 + c6 * c6 * K.dx2_12) + K.dx4 * c4 * c4 +
-               K.dxy2 * c6 * c6 + K.dy4 * c5 * c5;
-  const R b1 = K.weps + K.I1, b2 = K.weps + I2;
-  // w1 = (1/b1^2) / (1/b1^2 + 1/b2^2) = b2^2 / (b1^2 + b2^2)
-  const R w1 = d_div(b2 * b2, b1 * b1 + b2 * b2), w2 = R(1) - w1;
-  a[0] = w1 * a2 + w2 * c2;
-  a[1] = w1 * a3 + w2 * c3;
-  a[2] = w1 * a4 + w2 * c4;
-  a[3] = w1 * a5 + w2 * c5;
-  a[4] = w1 * a6 + w2 * c6;
+  // Eq. average: alpha = 1/(eps + I)^2, I(U1) = C dx dy; I(U2), the integral of the
+  // squared first and second derivatives of the central polynomial over the cell scaled
+  // by |Omega|, collected by coefficient
+  const R I2 = c2 * (K.dx2 * c2) + c3 * (K.dy2 * c3) + c4 * (K.kc4 * c4) + c5 * (K.kc5 * c5) + c6 * (K.kc6 * c6);
+  const R b2 = K.weps + I2, b2sq = b2 * b2;
+  // w1 = (1/b1^2) / (1/b1^2 + 1/b2^2) = b2^2 / (b1^2 + b2^2); a = c + w1 (a_one-sided - c)
+  const R w1 = d_div(b2sq, K.b1sq + b2sq);
+  a[0] = c2 + w1 * (a2 - c2);
+  a[1] = c3 + w1 * (a3 - c3);
+  a[2] = c4 + w1 * (a4 - c4);
+  a[3] = c5 + w1 * (a5 - c5);
+  a[4] = c6 + w1 * (a6 - c6);
 }
 
 }  // namespace gks

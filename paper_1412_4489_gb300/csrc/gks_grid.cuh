@@ -477,7 +477,7 @@ __device__ __forceinline__ void recon_cell(const Geo& g, const R* __restrict__ U
                                            R dy, R weps, R wC) {
   const int nx = g.nx, ny = g.ny;
   const size_t fxp = (size_t)ny * (nx + 1), fyp = (size_t)(ny + 1) * nx;
-  const ReconK<R> K = recon_k(dx, dy, weps, wC);
+  const ReconK<R> K = recon_k(dx, dy, GeoR<R>::idx(g), GeoR<R>::idy(g), weps, wC);
   R a[4][5], cbar[4];
   // stencil vector k of variable v: c, e, w, n, s; east face y-/y+, west y-/y+, north x-/x+,
   // south x-/x+
@@ -764,6 +764,16 @@ __device__ __forceinline__ R inv_bound(const Geo& g, const R w[4], bool& ok) {
   R inv = fmax((fabs(u) + c) * GeoR<R>::idx(g), (fabs(v) + c) * GeoR<R>::idy(g));
   if (g.visc_on) inv = fmax(inv, GeoR<R>::visc(g) * ir);
   return inv;
+}
+
+// warp maximum of inv, then the atomic minimum of the bound 1/inv (no block
+// barrier: the warps of a block go on independently).  Every lane of the warp must
+// call it.
+template <class R>
+__device__ __forceinline__ void warp_bound_to(R inv, unsigned long long* slot) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) inv = fmax(inv, __shfl_xor_sync(0xffffffffu, inv, o));
+  if ((threadIdx.x & 31) == 0 && inv > R(0)) atomicMin(slot, dbits(1.0 / (double)inv));
 }
 
 // block maximum of inv, then the atomic minimum of the bound 1/inv.  Every
