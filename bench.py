@@ -339,6 +339,7 @@ def run_ours(args):
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                          "peak_measured_fma": round(measured32, 2), "frac_of_measured_fma": round(achieved / measured32, 4),
                          "flops_per_face": flops_face, "faces_per_launch": nfaces,
+                         "faces_per_s": round(nfaces / (prof[dom] * 1e-3), 0),
                          "special_per_face": {k: ops[k] for k in ("sqrt", "rsqrt", "exp", "expm1", "erfc")},
                          "kernel_ms": round(prof[dom], 5), "traffic": traffic},
             "roofline_fp64": {"bound": "alu", "kernel": f"k_flux<{dom[-1]}> fp64", "achieved": round(achieved64, 4),
