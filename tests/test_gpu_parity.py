@@ -166,6 +166,30 @@ def test_advance_matches_step():
     assert np.array_equal(Ua, Ub) and np.array_equal(Wxa, Wxb) and np.array_equal(Wya, Wyb)
 
 
+@pytest.mark.parametrize("prec", [gks.GKS_FP64, gks.GKS_FP32_BULK])
+@pytest.mark.parametrize("nsteps", [6, 20])
+def test_advance_matches_step_through_the_fallback(prec, nsteps):
+    """On data where the positivity fallback fires (steps 3 and 5 in FP64) the replayed graphs
+    (one-step graphs; a 16-step graph and four one-step ones) equal gks_step bit for bit."""
+    quads = [(0.746, -0.312, 0.887, 0.312), (0.827, 0.438, -0.155, 0.861), (1.15, 0.953, 0.354, 0.494),
+             (0.228, -0.698, -0.347, 1.304)]
+    p = wl.riemann_2d(16, 80, quadrants=quads, mu=9.4e-4, Pr=0.72)
+    p.bc = [(wl.BC_PERIODIC, 0.0, 0.0, 1.0)] * 4
+    a = gks.Solver(p, prec)
+    b = gks.Solver(p, prec)
+    for _ in range(nsteps):
+        a.step(0.5)
+    b.advance(nsteps, 0.5)
+    t, n = b.sync()
+    assert n == nsteps
+    Ua, Wxa, Wya, ta = a.state()
+    Ub, Wxb, Wyb, tb = b.state()
+    a.close()
+    b.close()
+    assert ta == tb
+    assert np.array_equal(Ua, Ub) and np.array_equal(Wxa, Wxb) and np.array_equal(Wya, Wyb)
+
+
 def test_advance_stops_at_t_end():
     p = wl.smooth_wave_2d(16, seed=2)
     s = gks.Solver(p, tau_eps=0.0)
