@@ -870,24 +870,43 @@ __device__ __forceinline__ bool face_needs_fix(const Geo& g, const unsigned char
   return (c0 >= 0 && bad[c0]) || (c1 >= 0 && bad[c1]);
 }
 
+// state of one cell for the update, loaded before any arithmetic: FP64 values or FP32
+// (hi, lo) pairs
+template <class R> struct CellState;
+template <> struct CellState<double> { double w[4]; };
+template <> struct CellState<float> { float hi[4], lo[4]; };
+
+__device__ __forceinline__ void load_state(const Geo& g, Cells<double> U, int i, int j, CellState<double>& s) {
+#pragma unroll
+  for (int v = 0; v < 4; ++v) s.w[v] = U.p[ci(g, v, i, j)];
+}
+__device__ __forceinline__ void load_state(const Geo& g, Cells<float> U, int i, int j, CellState<float>& s) {
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const size_t o = ci(g, v, i, j);
+    s.hi[v] = U.p[o];
+    s.lo[v] = U.p[o + 4 * g.plane];
+  }
+}
+
 // Eq. finite for one variable: FP64 planes take the FP32 or FP64 fluxes in
 // FP64 (differences of FP32 numbers are exact there); the double-float pair
 // takes the FP32 fluxes one product at a time with error-free transformations.
 // Either way each face flux enters both neighbours with the same rounding, so
 // the sum over cells telescopes to roundoff of the accumulation type.
 template <class R>
-__device__ __forceinline__ R update_var(const Geo& g, Cells<double> U, Cells<double> Un, const R f[4][4], int v,
+__device__ __forceinline__ R update_var(const Geo& g, const CellState<double>& S, Cells<double> Un, const R f[4][4], int v,
                                         int i, int j, bool& finite) {
   const size_t o = ci(g, v, i, j);
-  const double w = U.p[o] + ((double)f[0][v] - (double)f[1][v]) * g.idx + ((double)f[2][v] - (double)f[3][v]) * g.idy;
+  const double w = S.w[v] + ((double)f[0][v] - (double)f[1][v]) * g.idx + ((double)f[2][v] - (double)f[3][v]) * g.idy;
   Un.p[o] = w;
   finite = isfinite(w);
   return R(w);
 }
-__device__ __forceinline__ float update_var(const Geo& g, Cells<float> U, Cells<float> Un, const float f[4][4],
+__device__ __forceinline__ float update_var(const Geo& g, const CellState<float>& S, Cells<float> Un, const float f[4][4],
                                             int v, int i, int j, bool& finite) {
   const size_t o = ci(g, v, i, j), lo_off = 4 * g.plane;
-  float hi = U.p[o], lo = U.p[o + lo_off];
+  float hi = S.hi[v], lo = S.lo[v];
   df_add_product(hi, lo, f[0][v], g.idx_hi, g.idx_lo);
   df_add_product(hi, lo, -f[1][v], g.idx_hi, g.idx_lo);
   df_add_product(hi, lo, f[2][v], g.idy_hi, g.idy_lo);
@@ -926,6 +945,8 @@ __device__ __forceinline__ R update_cell(const Geo& g, Cells<R> U, Cells<R> Un, 
     f[2][v] = Fy[v * nfy + (size_t)j * nx + i];
     f[3][v] = Fy[v * nfy + (size_t)(j + 1) * nx + i];
   }
+  CellState<R> S;
+  load_state(g, U, i, j, S);
   if (pass > 1) {
     const R gm1 = GeoR<R>::gm1(g), K = GeoR<R>::K(g);
 #pragma unroll 1
@@ -961,7 +982,7 @@ __device__ __forceinline__ R update_cell(const Geo& g, Cells<R> U, Cells<R> Un, 
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     bool fv;
-    wr[v] = update_var(g, U, Un, f, v, i, j, fv);
+    wr[v] = update_var(g, S, Un, f, v, i, j, fv);
     finite = finite && fv;
   }
   ghosts_of_cell<R>(g, Un, i, j);
