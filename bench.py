@@ -42,6 +42,7 @@ SEED = 2
 L2_FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per Blackwell SM
 SM_COUNT = 152
+ISSUE_PER_SM_CLK = 4      # warp instructions issued per SM per clock (four schedulers)
 SM_MAX_MHZ = 2070.0
 
 
@@ -114,22 +115,25 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
-def flux_traffic(precision_name):
-    """DRAM bytes per face of the x-face kernel from the committed ncu summary, or None when
-    it is missing or the kernel sources changed since it was taken."""
+def profile_figure(precision_name, key):
+    """A per-face figure of the x-face kernel (`key: value` line) from the committed ncu
+    summary, or None when it is missing or the kernel sources changed since it was taken."""
     path = os.path.join(ROOT, "profiles", f"step_kernels_{precision_name}_smooth_wave_2048.md")
     if not os.path.exists(path):
         return None, None
     h = source_hash()
-    traffic, scale, ok = None, None, False
+    value, ok = None, False
     for line in open(path):
         if line.startswith("source_sha1:"):
             ok = line.split(":", 1)[1].strip() == h
-        if line.startswith("traffic_bytes_per_face:"):
-            scale = float(line.split(":", 1)[1])
-    if ok and scale is not None:
-        traffic = scale
-    return traffic, path
+        if line.startswith(key + ":"):
+            value = float(line.split(":", 1)[1])
+    return (value if ok else None), path
+
+
+def flux_traffic(precision_name):
+    """DRAM bytes per face of the x-face kernel (ncu), or None (see profile_figure)."""
+    return profile_figure(precision_name, "traffic_bytes_per_face")
 
 
 def source_hash():
@@ -317,6 +321,11 @@ def run_ours(args):
     measured64 = gks.gks_measure_alu_peak(gks.GKS_FP64)
     traffic_face, traffic_src = flux_traffic("fp32")
     traffic = None if traffic_face is None else round(traffic_face * nfaces)
+    # the kernel is issue-bound: the share of the SMs' issue slots its instructions (ncu count
+    # per face at 2048^2, same source) take in this launch's measured time
+    instr_face, _ = profile_figure("fp32", "instructions_per_face")
+    issue_frac = None if instr_face is None else round(
+        instr_face * nfaces / 32 / (prof[dom] * 1e-3) / (SM_COUNT * ISSUE_PER_SM_CLK * SM_MAX_MHZ * 1e6), 4)
     flops64 = flops_face  # the same arithmetic in FP64
     achieved64 = flops64 * nfaces / (prof64[dom] * 1e-3) / 1e12
 
@@ -341,7 +350,9 @@ def run_ours(args):
                          "flops_per_face": flops_face, "faces_per_launch": nfaces,
                          "faces_per_s": round(nfaces / (prof[dom] * 1e-3), 0),
                          "special_per_face": {k: ops[k] for k in ("sqrt", "rsqrt", "exp", "expm1", "erfc")},
-                         "kernel_ms": round(prof[dom], 5), "traffic": traffic},
+                         "kernel_ms": round(prof[dom], 5), "traffic": traffic,
+                         "issue_slots": {"instructions_per_face": instr_face, "frac": issue_frac,
+                                         "peak": "152 SMs x 4 warp instructions per clock x 2070 MHz"}},
             "roofline_fp64": {"bound": "alu", "kernel": f"k_flux<{dom[-1]}> fp64", "achieved": round(achieved64, 4),
                               "peak": round(measured64, 3), "unit": "TFLOP/s", "frac": round(achieved64 / measured64, 4),
                               "peak_source": "measured FP64 FMA throughput (gks_measure_alu_peak)",
