@@ -108,6 +108,17 @@ def test_smooth_wave_100_steps():
         assert _rel_linf(a, b) < 1e-10
 
 
+@pytest.mark.parametrize("bcname", ["periodic", "noslip", "adiabatic"])
+def test_rows_of_whole_warps_of_x_faces(bcname):
+    """nx a multiple of 32: the last x-face of every row (a periodic seam or a wall face) is
+    evaluated by the extra column of blocks that takes it 128 rows at a time.  Every face and
+    cell against the oracle over 8 steps (ny = 200 spans two of those blocks)."""
+    p = _perturbed(64, 200, seed=11, bc=BCSETS[bcname], mu=1e-3, Pr=0.72)
+    g, o = _run_both(p, 8)
+    for a, b in zip(g, o):
+        assert _rel_linf(a, b) < 1e-10
+
+
 def test_riemann_ns_discontinuous():
     p = wl.riemann_2d(40, 36, seed=3, mu=1e-4, Pr=0.72)
     g, o = _run_both(p, 60)
