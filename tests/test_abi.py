@@ -49,3 +49,15 @@ def test_invalid_sizes_are_rejected_before_touching_the_device():
         with pytest.raises(gks.GKSError) as e:
             gks.gks_create(nx, ny, 1.0, 1.0, 1.4, 1.0, 0.0)
         assert e.value.status == gks.GKS_EINVAL
+
+
+def test_an_axis_one_cell_across_must_be_periodic():
+    """A wall or outflow side on an axis one cell across is rejected before any CUDA call."""
+    import pytest
+    from paper_1412_4489_gb300 import gks
+    walls = [gks.GKS_BC_SLIPWALL] * 4
+    for nx, ny in ((1, 5), (5, 1)):
+        with pytest.raises(gks.GKSError) as e:
+            gks.gks_create(nx, ny, 1.0, 1.0, 1.4, 1.0, 0.0, bc=walls)
+        assert e.value.status == gks.GKS_EINVAL
+        assert "periodic" in gks.gks_last_error(None)

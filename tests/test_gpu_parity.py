@@ -119,6 +119,38 @@ def test_rows_of_whole_warps_of_x_faces(bcname):
         assert _rel_linf(a, b) < 1e-10
 
 
+_TINY = [((1, 1), "periodic"), ((1, 7), "periodic"), ((7, 1), "periodic"), ((2, 2), "periodic"), ((3, 5), "periodic"),
+         ((2, 2), "outflow"), ((2, 7), "outflow"), ((7, 2), "slip"), ((3, 5), "slip"), ((2, 3), "noslip")]
+
+
+@pytest.mark.parametrize("shape,bcname", _TINY)
+def test_tiny_grids(shape, bcname):
+    """Grids of one to a few cells: every stencil reaches into the ghost ring or wraps onto
+    the cell itself (a 1 x 1 periodic grid is its own neighbour on all four sides; an axis one
+    cell across must be periodic).  GPU and oracle agree over 5 Navier-Stokes steps."""
+    nx, ny = shape
+    p = _perturbed(nx, ny, seed=4, bc=BCSETS[bcname], mu=1e-3, Pr=0.72)
+    g, o = _run_both(p, 5)
+    for a, b in zip(g, o):
+        assert _rel_linf(a, b) < 1e-10
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (2, 2), (3, 5)])
+def test_tiny_periodic_grids_fp32_bulk_conserve(shape):
+    """The FP32-bulk form on the same tiny periodic grids: finite states and totals kept to the
+    double-float pair's roundoff."""
+    nx, ny = shape
+    p = _perturbed(nx, ny, seed=4, mu=1e-3, Pr=0.72)
+    s = gks.Solver(p, gks.GKS_FP32_BULK)
+    for _ in range(20):
+        s.step(0.5)
+    U = s.state()[0]
+    s.close()
+    assert np.all(np.isfinite(U))
+    tot0, tot = p.U.sum(axis=(1, 2)), U.sum(axis=(1, 2))
+    assert np.max(np.abs(tot - tot0) / np.abs(tot0).max()) < 1e-12
+
+
 def test_riemann_ns_discontinuous():
     p = wl.riemann_2d(40, 36, seed=3, mu=1e-4, Pr=0.72)
     g, o = _run_both(p, 60)
